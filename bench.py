@@ -1,0 +1,338 @@
+"""TSQR benchmark on GB300: one JSON line.
+
+A step is one pass of the whole path over one synthetic matrix: tsqr_factor (leaves, flat
+chains, tree, root signs), tsqr_form_q (explicit thin Q) and tsqr_apply_qt on one right-hand
+side.  The workload: m = 2^22, n = 64, FP64, A = U Sigma V^T with Haar U, V and kappa = 1
+(seeded, synthetic).  The metric is GFLOP/s with LAPACK operation counts
+(factor 2mn^2 - 2n^3/3, thin Q 2mn^2 - 2n^3/3, Q^T b 4mn - 2n^2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (plain Householder QR + thin Q) on the host cores,
+on a bounded slice of the same workload.  Under torchrun each rank runs an independent replica
+(TSQR on one GPU needs no data-path collective); value is the sum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M_DEFAULT, N_DEFAULT = 1 << 22, 64
+METRIC = "TSQR GFLOP/s (factor + thin Q + Q^T b, FP64) at stated ||A-QR||, ||I-Q^TQ|| vs plain FP64"
+
+
+def flops(m, n, k=1):
+    f = 2.0 * m * n * n - 2.0 * n ** 3 / 3
+    return {"factor": f, "form_q": f, "apply_qt": 4.0 * m * n * k - 2.0 * n * n * k}
+
+
+def algorithmic_bytes(m, n, k=1):
+    # factor: read A, write V; thin Q: read V, write Q; Q^T b: read V, read+write b
+    return {"factor": 16.0 * m * n, "form_q": 16.0 * m * n, "apply_qt": 8.0 * m * n + 16.0 * m * k}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_input(m, n):
+    from paper_0809_2407_gb300 import inputs
+
+    return inputs.usv(m, n, 0.0, inputs.seed_for(2, 0))
+
+
+def cpu_oracle_sample(A_h, rows):
+    """Times the oracle (QR + thin Q) on the first `rows` rows; returns (GFLOP/s, seconds)."""
+    import oracle
+
+    oracle._load()
+    S = A_h[:rows].copy()
+    t0 = time.perf_counter()
+    oracle.qr(S, want_q=True)
+    dt = time.perf_counter() - t0
+    f = flops(rows, S.shape[1])
+    return (f["factor"] + f["form_q"]) / dt / 1e9, dt
+
+
+def run_reference(args, rank, world):
+    """The oracle on host cores, on bounded slices of the workload (rank 0 only)."""
+    if rank != 0:
+        return None
+    m, n = args.m, args.n
+    rows = args.ref_rows
+    from paper_0809_2407_gb300 import inputs
+
+    A_h = inputs.usv(rows, n, 0.0, inputs.seed_for(2, 0))
+    for _ in range(min(args.warmup, 1)):
+        cpu_oracle_sample(A_h, rows)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_sample(A_h, rows)
+        times.append(dt)
+    f = flops(rows, n)
+    per = f["factor"] + f["form_q"]
+    tot = sum(times)
+    value = per * len(times) / tot / 1e9
+    return {"metric": METRIC, "value": value, "unit": "GFLOP/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tsqr fp64 usv kappa=1, n=%d; oracle on a %d-row slice per step" % (n, rows),
+                       "m": m, "n": n},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": "oracle QR + thin Q of the first %d rows x %d columns, per step" % (rows, n)},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=M_DEFAULT)
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--ref-rows", type=int, default=1 << 15, help="oracle rows per reference-arm step")
+    ap.add_argument("--cpu-rows", type=int, default=1 << 17, help="oracle rows of the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_0809_2407_gb300 import build, tsqr
+
+    build.build()
+    tsqr.load()
+
+    m, n = args.m, args.n
+    A_h = make_input(m, n)
+    A_pin = torch.from_numpy(A_h).pin_memory()
+    A = A_pin.to(dev, non_blocking=False)
+    b_h = torch.from_numpy(np.random.default_rng(5).standard_normal((m, 1))).pin_memory()
+    b = b_h.to(dev)  # Q^T is applied to it in place every step; it stays a unit-scale vector
+    Q = torch.empty((m, n), dtype=torch.float64, device=dev)
+    R = torch.empty((n, n), dtype=torch.float64, device=dev)
+    opts = tsqr.Opts()
+    nbytes = tsqr.tsqr_workspace_size(tsqr.TSQR_F64, m, n, opts)
+    work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = tsqr.ctypes.c_void_p(stream.cuda_stream)
+
+    ev = {k: [] for k in ("factor", "form_q", "apply_qt")}
+
+    def step(record):
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+        if record:
+            marks[0].record(stream)
+        h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
+                             work.data_ptr(), nbytes, opts, sptr)
+        if record:
+            marks[1].record(stream)
+        tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
+        if record:
+            marks[2].record(stream)
+        tsqr.tsqr_apply_qt(h, 1, b.data_ptr(), 1, sptr)
+        if record:
+            marks[3].record(stream)
+        tsqr.tsqr_destroy(h)
+        return marks
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    all_marks = []
+    for _ in range(args.steps):
+        all_marks.append(step(True))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = t0.elapsed_time(t1)
+    for mk in all_marks:
+        ev["factor"].append(mk[0].elapsed_time(mk[1]))
+        ev["form_q"].append(mk[1].elapsed_time(mk[2]))
+        ev["apply_qt"].append(mk[2].elapsed_time(mk[3]))
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+
+    # accuracy of the last step
+    be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
+    orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Q.T @ Q).item()
+
+    fl = flops(m, n)
+    per_step = sum(fl.values())
+    ms_step = ms / args.steps
+    value = per_step * world / (ms_step / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the factorization): FP64-pipe bound
+    f_ms = statistics.mean(ev["factor"])
+    q_ms = statistics.mean(ev["form_q"])
+    a_ms = statistics.mean(ev["apply_qt"])
+    dom = "factor" if f_ms >= q_ms else "form_q"
+    dom_ms = f_ms if dom == "factor" else q_ms
+    achieved_tf = fl[dom] / (dom_ms / 1e3) / 1e12
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs")
+    ab = algorithmic_bytes(m, n)
+    roofline = {"bound": "alu", "kernel": dom + "_kernel", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe, 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "hbm_view": {"achieved_gbs": ab[dom] / (dom_ms / 1e3) / 1e9, "peak_gbs": hbm,
+                             "frac_of_measured": (ab[dom] / (dom_ms / 1e3) / 1e9 / hbm) if hbm else None}}
+
+    # end to end through the C-ABI with host buffers: H2D of A and b, D2H of R, Q and Q^T b
+    e2e = None
+    if not args.no_e2e:
+        R_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        Q_h = torch.empty((m, n), dtype=torch.float64).pin_memory()
+        bo_h = torch.empty((m, 1), dtype=torch.float64).pin_memory()
+        e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            A.copy_(A_pin, non_blocking=True)
+            b.copy_(b_h, non_blocking=True)
+            h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
+                                 work.data_ptr(), nbytes, opts, sptr)
+            tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
+            tsqr.tsqr_apply_qt(h, 1, b.data_ptr(), 1, sptr)
+            R_h.copy_(R, non_blocking=True)
+            Q_h.copy_(Q, non_blocking=True)
+            bo_h.copy_(b, non_blocking=True)
+            tsqr.tsqr_destroy(h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / e_steps
+        e2e = {"value": per_step * world / (e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": 8 * m * n + 8 * m, "d2h_bytes_per_step": 8 * n * n + 8 * m * n + 8 * m,
+               "ms_per_step": e_ms, "steps": e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = args.cpu_rows
+        gf, dt = cpu_oracle_sample(A_h, rows)
+        cpu = {"value": gf, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle QR + thin Q of the first %d rows of the same matrix (%.1f s)" % (rows, dt)}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "tsqr factor + form_q + apply_qt(k=1), fp64, m=%d n=%d, A=U S V^T kappa=1"
+                                      % (m, n), "m": m, "n": n, "k": 1, "leaf_h": None, "chain": "auto",
+                          "arity": 2, "l2": "inputs larger than L2 (A is %.1f GB)" % (8.0 * m * n / 1e9),
+                          "parallelism": "replicas" if world > 1 else "single-gpu"},
+               "backward_error": be, "orthogonality": orth,
+               "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": 3 * args.steps, "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,132 @@
+/*
+ * tsqr.h -- C-ABI of the GB300 TSQR library (libtsqr.so).
+ *
+ * TSQR is the communication-avoiding Householder QR of a tall-skinny m x n matrix A (m >= n)
+ * of Demmel, Grigori, Hoemmen and Langou, "Implementing Communication-Optimal Parallel and
+ * Sequential QR Factorizations".  A is split into a 1-D block-row layout of leaves (Sec. 2,
+ * Sec. 4.2).  Each leaf is factored by Householder QR; consecutive leaves owned by one thread
+ * block are combined by the sequential flat-tree step QR([R; A_k]) (Algorithm 2); the R factors
+ * of the thread blocks are then combined up an arity-q tree of structured QRs of stacked upper
+ * triangles (Algorithm 1, Sec. 3.1 eq. fact_2rs).  The final R is the R of A; Q stays implicit
+ * as the reified tree of Householder factors (Sec. 4.1) and is applied as Q^T B (a reduction)
+ * or Q B (a broadcast), or expanded to the explicit thin Q (Sec. 7.2).
+ *
+ * Conventions shared by every call:
+ *   - Matrices are FP64, row-major: element (i, j) of X with leading dimension ldx is
+ *     X[i * ldx + j].  Device pointers must be 16-byte aligned and, for A, lda must be even
+ *     (TMA row strides are multiples of 16 bytes).
+ *   - Reflectors are H = I - tau v v^T with v_0 = 1; beta = -sign(alpha) ||x||, sign(0) = +1.
+ *   - R is returned with a non-negative diagonal: D = diag(sign(R_jj)), R <- D R and the
+ *     thin Q <- Q D (the QR is unique only up to these signs, Sec. 2).
+ *   - The caller owns every buffer: A, R, B, Q and the workspace.  The library never allocates
+ *     device memory; a handle is a small host object that points into the workspace, which
+ *     must stay alive and untouched until tsqr_destroy.
+ *   - Every call is stream-ordered and asynchronous on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream).  No call synchronises the host except tsqr_status_poll.
+ *   - Errors are returned, never raised on the device: no device assert or trap.  Invalid
+ *     shapes, strides or alignment return TSQR_ERR_INVALID_ARG before anything is launched.
+ *     NaN and Inf in the input propagate to the outputs without being checked.
+ *   - tsqr_last_error() gives a human-readable reason for the last failing call on the
+ *     calling host thread.
+ */
+#ifndef TSQR_H_
+#define TSQR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsqr_handle_s* tsqr_handle_t; /* opaque; owns no device memory */
+typedef void* tsqr_stream_t;                  /* a cudaStream_t */
+
+typedef enum {
+  TSQR_OK = 0,
+  TSQR_ERR_INVALID_ARG = 1, /* bad shape, stride, pointer alignment or option */
+  TSQR_ERR_UNSUPPORTED = 2, /* a valid request this build does not implement (e.g. n > 128) */
+  TSQR_ERR_CUDA = 3,        /* a CUDA runtime or driver call failed */
+  TSQR_ERR_WORKSPACE = 4,   /* workspace missing or smaller than tsqr_workspace_size */
+  TSQR_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up (see tsqr_status_poll) */
+} tsqr_status_t;
+
+typedef enum { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype_t;
+typedef enum { TSQR_ROW_MAJOR = 0, TSQR_COL_MAJOR = 1 } tsqr_layout_t;
+
+/* Tuning knobs of the reduction tree (Sec. 2: TSQR works on any tree; Sec. 4.2: the leaf
+ * size follows from the fast-memory budget).  Zero means "choose automatically". */
+typedef struct {
+  int32_t leaf_h;    /* rows per leaf block: a multiple of 8, >= the padded n; 0 = auto */
+  int32_t chain;     /* leaves combined sequentially by one thread block (flat tree);
+                        1 = every leaf is its own tree leaf (pure arity-q tree); 0 = auto */
+  int32_t arity;     /* children per node of the tree over thread blocks, 2..8; 0 = 2 */
+  int32_t precision; /* 0 = native FP64 arithmetic everywhere (the only mode so far) */
+  int32_t inplace;   /* nonzero: the leaf reflectors overwrite A (Sec. 4.2 storage) and A's
+                        upper triangles hold intermediate R factors; zero: A is read only */
+} tsqr_opts_t;
+
+/* Plan and storage of a factorization, for inspection and tests.  The pointers are device
+ * pointers into the workspace (row-major FP64, np = n rounded up to a power of two >= 16). */
+typedef struct {
+  int64_t m, n, np;
+  int32_t leaf_h, chain, arity, depth; /* depth = levels of the tree above the chains */
+  int64_t leaves, chains, tree_nodes;
+  const double* v;        /* leaf reflectors, m x n with leading dimension ldv */
+  int64_t ldv;
+  const double* tau_leaf; /* leaves x np */
+  const double* t_leaf;   /* leaves x np x np, upper triangular T of each leaf (Q = I - V T V^T) */
+  const double* node_y;   /* tree_nodes x (arity-1) x np x np: the upper-triangular lower blocks
+                             of each tree node's reflectors (their top block is I, eq. fact_2rs) */
+  const double* node_tau; /* tree_nodes x np */
+  const double* node_t;   /* tree_nodes x np x np */
+  const double* signs;    /* np: D = diag(sign(R_jj)) of the root, sign(0) = +1 */
+} tsqr_info_t;
+
+/* Bytes of device workspace tsqr_factor needs for an m x n factorization with `opts`
+ * (NULL = all defaults).  Pure host computation. */
+tsqr_status_t tsqr_workspace_size(tsqr_dtype_t dtype, int64_t m, int64_t n, const tsqr_opts_t* opts,
+                                  size_t* bytes);
+
+/* Factors A (m x n, m >= n >= 1, device, leading dimension lda >= n, lda even) into R and
+ * an implicit Q (Algorithms 1 and 2, Sec. 3.1).
+ *   dR     : device, n x n with ldr >= n; receives R with diag(R) >= 0, strict lower zeroed.
+ *   dWork  : device workspace of at least tsqr_workspace_size bytes, 256-byte aligned.
+ *   out    : receives a new handle (free with tsqr_destroy).  The handle records A's pointer
+ *            when inplace is set; A must then outlive the handle.
+ * A is read once from HBM; with inplace it is overwritten by the leaf reflectors. */
+tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, int64_t n, void* dA,
+                          int64_t lda, void* dR, int64_t ldr, void* dWork, size_t work_bytes,
+                          const tsqr_opts_t* opts, tsqr_stream_t stream, tsqr_handle_t* out);
+
+/* B (m x k, device, ldb >= k) <- Q^T B with Q the full m x m orthogonal factor, signs
+ * normalised (Sec. 4.1: applying Q^T is a reduction up the tree; Sec. 3.2 gives the node
+ * update D = C0 + Y1^T C1, C0 -= T^T D, C1 -= Y1 T^T D).  Rows 0..n-1 of the result hold
+ * Q_thin^T B; the other rows hold B's coordinates in this TSQR's orthogonal complement. */
+tsqr_status_t tsqr_apply_qt(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, tsqr_stream_t stream);
+
+/* B (m x k, device, ldb >= k) <- Q B with the same full Q (Sec. 4.1: a broadcast down the
+ * tree).  tsqr_apply_q after tsqr_apply_qt returns B up to rounding. */
+tsqr_status_t tsqr_apply_q(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, tsqr_stream_t stream);
+
+/* Explicit thin Q (m x n, device, ldq >= n), signs normalised so that A = Q R (Sec. 2, the
+ * thin factor; Sec. 7.2 counts this conversion in the Q-and-R runtime). */
+tsqr_status_t tsqr_form_q(tsqr_handle_t h, void* dQ, int64_t ldq, tsqr_stream_t stream);
+
+/* Synchronises `stream` and reads the handle's device status word: TSQR_OK, or
+ * TSQR_ERR_TIMEOUT if any kernel of the handle's calls gave up a bounded wait. */
+tsqr_status_t tsqr_status_poll(tsqr_handle_t h, tsqr_stream_t stream);
+
+/* Fills *info with the plan and workspace pointers of h. */
+tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info);
+
+/* Frees the host handle (the workspace stays the caller's). NULL is a no-op. */
+tsqr_status_t tsqr_destroy(tsqr_handle_t h);
+
+const char* tsqr_status_string(tsqr_status_t s);
+const char* tsqr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSQR_H_ */

@@ -1,0 +1,339 @@
+// C-ABI of libtsqr.so: argument checks, the reduction-tree plan, the workspace layout, TMA
+// descriptors and the handle.  Declared in include/tsqr.h.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/tsqr.h"
+#include "factor_kernels.h"
+
+using tsqr::Plan;
+using tsqr::Store;
+
+struct tsqr_handle_s {
+  Plan P;
+  Store st;
+  CUtensorMap mapV;
+  int box_rows;
+  int inplace;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tsqr_status_t fail(tsqr_status_t s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+tsqr_status_t cuda_fail(cudaError_t e, const char* where) {
+  return fail(TSQR_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+constexpr size_t kSmemLimit = 232448;  // opt-in shared memory per block on GB300
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  return sms;
+}
+
+int default_leaf_h(int np) {
+  switch (np) {
+    case 16: return 512;
+    case 32: return 256;
+    default: return 128;
+  }
+}
+
+// Builds the plan of an m x n factorization; see Plan in common.cuh.
+tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P) {
+  tsqr_opts_t d{};
+  if (!o) o = &d;
+  if (n < 1 || m < n) return fail(TSQR_ERR_INVALID_ARG, "need m >= n >= 1");
+  int np = 16;
+  while (np < n) np *= 2;
+  if (np > 64) return fail(TSQR_ERR_UNSUPPORTED, "n > 64 is not supported by this build");
+  if (o->precision != 0) return fail(TSQR_ERR_UNSUPPORTED, "only precision 0 (native FP64) is implemented");
+  const int arity = o->arity ? o->arity : 2;
+  if (arity < 2 || arity > tsqr::kMaxArity) return fail(TSQR_ERR_INVALID_ARG, "arity must be in 2..8");
+  int h = o->leaf_h ? o->leaf_h : default_leaf_h(np);
+  if (h < np || h % 8 != 0 || (h > 256 && h % 256 != 0))
+    return fail(TSQR_ERR_INVALID_ARG, "leaf_h must be a multiple of 8, >= padded n, and a multiple of 256 above 256");
+  if (o->chain < 0) return fail(TSQR_ERR_INVALID_ARG, "chain must be >= 0");
+  std::memset(P, 0, sizeof(Plan));
+  P->m = m;
+  P->n = (int)n;
+  P->np = np;
+  P->h = h;
+  P->arity = arity;
+  P->leaves = (m + h - 1) / h;
+  int64_t chain = o->chain;
+  if (chain == 0) {
+    const int sms = device_sms();
+    chain = (P->leaves + sms - 1) / sms;
+  }
+  if (chain > P->leaves) chain = P->leaves;
+  int64_t chains = (P->leaves + chain - 1) / chain;
+  const int64_t rows_last = m - (P->leaves - 1) * h;
+  // a chain's first leaf must hold at least n real rows (its top block lives there)
+  if (chains > 1 && (P->leaves - 1) % chain == 0 && rows_last < n) chains -= 1;
+  if (chains > (int64_t)1 << 30) return fail(TSQR_ERR_UNSUPPORTED, "too many chains");
+  P->chain = (int)chain;
+  P->chains = (int)chains;
+  int count = P->chains, depth = 0, offset = 0;
+  P->level_count[0] = count;
+  P->level_offset[0] = 0;
+  offset = count;
+  while (count > 1) {
+    if (depth + 1 > tsqr::kMaxLevels) return fail(TSQR_ERR_UNSUPPORTED, "tree too deep");
+    count = (count + arity - 1) / arity;
+    ++depth;
+    P->level_count[depth] = count;
+    P->level_offset[depth] = offset;
+    offset += count;
+  }
+  P->depth = depth;
+  P->total_nodes = offset;
+  P->tree_nodes = offset - P->chains;
+  int rows_cap = np + h;
+  if (arity * np > rows_cap) rows_cap = arity * np;
+  P->rows_cap = (rows_cap + 7) / 8 * 8;
+  if (tsqr::factor_smem_bytes(*P) > kSmemLimit || tsqr::formq_smem_bytes(*P) > kSmemLimit ||
+      tsqr::apply_smem_bytes(*P, 32) > kSmemLimit)
+    return fail(TSQR_ERR_UNSUPPORTED, "leaf_h/arity too large for shared memory at this n");
+  return TSQR_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t v, tau_leaf, t_leaf, node_r, node_y, node_tau, node_t, signs, counters, status, total;
+  int64_t ldv;
+};
+
+Layout make_layout(const Plan& P, bool inplace) {
+  Layout L{};
+  const size_t np = (size_t)P.np, np2 = np * np;
+  L.ldv = (P.n + 1) / 2 * 2;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  L.v = take(inplace ? 0 : (size_t)P.m * L.ldv * 8);
+  L.tau_leaf = take((size_t)P.leaves * np * 8);
+  L.t_leaf = take((size_t)P.leaves * np2 * 8);
+  L.node_r = take((size_t)P.total_nodes * np2 * 8);
+  L.node_y = take((size_t)P.tree_nodes * (P.arity - 1) * np2 * 8);
+  L.node_tau = take((size_t)P.tree_nodes * np * 8);
+  L.node_t = take((size_t)P.tree_nodes * np2 * 8);
+  L.signs = take(np * 8);
+  L.counters = take((size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1) * tsqr::kMaxColBlocks * sizeof(int));
+  L.status = take(256);
+  L.total = off;
+  return L;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Row-major m x n FP64 matrix, boxes of 16 columns x box_rows rows, 128-byte swizzle,
+// zero fill outside the matrix.
+tsqr_status_t make_map(CUtensorMap* map, const void* ptr, int64_t m, int64_t n, int64_t ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return fail(TSQR_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+  cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TSQR_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+  return TSQR_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* tsqr_status_string(tsqr_status_t s) {
+  switch (s) {
+    case TSQR_OK: return "TSQR_OK";
+    case TSQR_ERR_INVALID_ARG: return "TSQR_ERR_INVALID_ARG";
+    case TSQR_ERR_UNSUPPORTED: return "TSQR_ERR_UNSUPPORTED";
+    case TSQR_ERR_CUDA: return "TSQR_ERR_CUDA";
+    case TSQR_ERR_WORKSPACE: return "TSQR_ERR_WORKSPACE";
+    case TSQR_ERR_TIMEOUT: return "TSQR_ERR_TIMEOUT";
+  }
+  return "TSQR_UNKNOWN_STATUS";
+}
+
+const char* tsqr_last_error(void) { return g_last_error.c_str(); }
+
+tsqr_status_t tsqr_workspace_size(tsqr_dtype_t dtype, int64_t m, int64_t n, const tsqr_opts_t* opts, size_t* bytes) {
+  if (!bytes) return fail(TSQR_ERR_INVALID_ARG, "bytes is NULL");
+  if (dtype != TSQR_F64) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_F64 is implemented");
+  Plan P;
+  tsqr_status_t s = make_plan(m, n, opts, &P);
+  if (s != TSQR_OK) return s;
+  *bytes = make_layout(P, opts && opts->inplace).total;
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, int64_t n, void* dA, int64_t lda,
+                          void* dR, int64_t ldr, void* dWork, size_t work_bytes, const tsqr_opts_t* opts,
+                          tsqr_stream_t stream, tsqr_handle_t* out) {
+  if (!out) return fail(TSQR_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (dtype != TSQR_F64) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_F64 is implemented");
+  if (layout != TSQR_ROW_MAJOR) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_ROW_MAJOR is implemented");
+  if (!dA || !dR) return fail(TSQR_ERR_INVALID_ARG, "A and R must be non-NULL");
+  if (n < 1 || m < n) return fail(TSQR_ERR_INVALID_ARG, "need m >= n >= 1");
+  if (lda < n || lda % 2 != 0) return fail(TSQR_ERR_INVALID_ARG, "lda must be >= n and even");
+  if (ldr < n) return fail(TSQR_ERR_INVALID_ARG, "ldr must be >= n");
+  if (!aligned16(dA)) return fail(TSQR_ERR_INVALID_ARG, "A must be 16-byte aligned");
+  Plan P;
+  tsqr_status_t s = make_plan(m, n, opts, &P);
+  if (s != TSQR_OK) return s;
+  const bool inplace = opts && opts->inplace;
+  const Layout L = make_layout(P, inplace);
+  if (!dWork || work_bytes < L.total)
+    return fail(TSQR_ERR_WORKSPACE, "workspace needs " + std::to_string(L.total) + " bytes");
+  if ((reinterpret_cast<uintptr_t>(dWork) & 255) != 0) return fail(TSQR_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  char* w = static_cast<char*>(dWork);
+  Store st;
+  st.v = inplace ? static_cast<double*>(dA) : reinterpret_cast<double*>(w + L.v);
+  st.ldv = inplace ? lda : L.ldv;
+  st.tau_leaf = reinterpret_cast<double*>(w + L.tau_leaf);
+  st.t_leaf = reinterpret_cast<double*>(w + L.t_leaf);
+  st.node_r = reinterpret_cast<double*>(w + L.node_r);
+  st.node_y = reinterpret_cast<double*>(w + L.node_y);
+  st.node_tau = reinterpret_cast<double*>(w + L.node_tau);
+  st.node_t = reinterpret_cast<double*>(w + L.node_t);
+  st.signs = reinterpret_cast<double*>(w + L.signs);
+  st.counters = reinterpret_cast<int*>(w + L.counters);
+  st.status = reinterpret_cast<int*>(w + L.status);
+  const int box_rows = P.h < 256 ? P.h : 256;
+  CUtensorMap mapA, mapV;
+  if ((s = make_map(&mapA, dA, m, n, lda, box_rows)) != TSQR_OK) return s;
+  if ((s = make_map(&mapV, st.v, m, n, st.ldv, box_rows)) != TSQR_OK) return s;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(st.status, 0, sizeof(int), cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  e = tsqr::launch_factor(mapA, mapV, P, st, static_cast<double*>(dR), ldr, box_rows, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "factor launch");
+  tsqr_handle_s* h = new (std::nothrow) tsqr_handle_s;
+  if (!h) return fail(TSQR_ERR_INVALID_ARG, "out of host memory");
+  h->P = P;
+  h->st = st;
+  h->mapV = mapV;
+  h->box_rows = box_rows;
+  h->inplace = inplace ? 1 : 0;
+  *out = h;
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_form_q(tsqr_handle_t h, void* dQ, int64_t ldq, tsqr_stream_t stream) {
+  if (!h) return fail(TSQR_ERR_INVALID_ARG, "handle is NULL");
+  if (!dQ || ldq < h->P.n) return fail(TSQR_ERR_INVALID_ARG, "Q must be non-NULL with ldq >= n");
+  cudaError_t e = tsqr::launch_form_q(h->mapV, h->P, h->st, static_cast<double*>(dQ), ldq, h->box_rows,
+                                      static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "form_q launch");
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_apply_qt(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, tsqr_stream_t stream) {
+  if (!h) return fail(TSQR_ERR_INVALID_ARG, "handle is NULL");
+  if (k < 0) return fail(TSQR_ERR_INVALID_ARG, "k must be >= 0");
+  if (k == 0) return TSQR_OK;
+  if (!dB || ldb < k) return fail(TSQR_ERR_INVALID_ARG, "B must be non-NULL with ldb >= k");
+  cudaError_t e = tsqr::launch_apply_qt(h->mapV, h->P, h->st, k, static_cast<double*>(dB), ldb, h->box_rows,
+                                        static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "apply_qt launch");
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_apply_q(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, tsqr_stream_t stream) {
+  if (!h) return fail(TSQR_ERR_INVALID_ARG, "handle is NULL");
+  if (k < 0) return fail(TSQR_ERR_INVALID_ARG, "k must be >= 0");
+  if (k == 0) return TSQR_OK;
+  if (!dB || ldb < k) return fail(TSQR_ERR_INVALID_ARG, "B must be non-NULL with ldb >= k");
+  cudaError_t e = tsqr::launch_apply_q(h->mapV, h->P, h->st, k, static_cast<double*>(dB), ldb, h->box_rows,
+                                       static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "apply_q launch");
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_status_poll(tsqr_handle_t h, tsqr_stream_t stream) {
+  if (!h) return fail(TSQR_ERR_INVALID_ARG, "handle is NULL");
+  int v = 0;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&v, h->st.status, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (v & tsqr::kStatusTimeout) return fail(TSQR_ERR_TIMEOUT, "a device-side bounded wait timed out");
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info) {
+  if (!h || !info) return fail(TSQR_ERR_INVALID_ARG, "NULL argument");
+  const Plan& P = h->P;
+  info->m = P.m;
+  info->n = P.n;
+  info->np = P.np;
+  info->leaf_h = P.h;
+  info->chain = P.chain;
+  info->arity = P.arity;
+  info->depth = P.depth;
+  info->leaves = P.leaves;
+  info->chains = P.chains;
+  info->tree_nodes = P.tree_nodes;
+  info->v = h->st.v;
+  info->ldv = h->st.ldv;
+  info->tau_leaf = h->st.tau_leaf;
+  info->t_leaf = h->st.t_leaf;
+  info->node_y = h->st.node_y;
+  info->node_tau = h->st.node_tau;
+  info->node_t = h->st.node_t;
+  info->signs = h->st.signs;
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_destroy(tsqr_handle_t h) {
+  delete h;
+  return TSQR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// TSQR factorization kernel: leaves, flat chains and the tree over thread blocks, in one launch.
+//
+// Block g owns chain g: leaves [g*chain, ...).  It factors its first leaf with a plain
+// Householder QR (Algorithm 1, first step) and each following leaf A_k with the flat-tree step
+// QR([R; A_k]) (Algorithm 2), keeping R in shared memory so that only one R per block leaves
+// the chip (Sec. 2: the flat tree minimises slow-memory traffic).  Every leaf's reflectors,
+// tau and T go to HBM (the reified tree, Sec. 4.1).
+//
+// The chains' R factors are then reduced up an arity-q tree (Algorithm 1, tree steps) without
+// any block waiting for another: each block publishes its R and bumps its parent's counter;
+// the block that arrives last stacks the q children's R factors in child order (Algorithm 1:
+// "by order of processor ids"), takes their structured QR (eq. fact_2rs) and climbs on.  The
+// block that finishes the root writes R with diag(R) >= 0 and the sign vector.
+#include "factor_kernels.h"
+#include "householder.cuh"
+
+namespace tsqr {
+
+struct FactorSmem {
+  Tile S;
+  double *T_s, *red, *dvec, *sc, *tau_s;
+  uint64_t* bar;
+  int* flag;
+  int ldt;
+};
+
+__device__ inline FactorSmem carve_factor(char* raw, const Plan& P) {
+  FactorSmem f;
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  f.S = Tile{base, P.rows_cap};
+  f.ldt = P.np + 1;
+  f.T_s = reinterpret_cast<double*>(base + (size_t)P.rows_cap * P.np * 8);
+  f.red = f.T_s + P.np * f.ldt;
+  f.dvec = f.red + kThreads;
+  f.sc = f.dvec + P.np;
+  f.tau_s = f.sc + 8;
+  f.bar = reinterpret_cast<uint64_t*>(f.tau_s + P.np);
+  f.flag = reinterpret_cast<int*>(f.bar + 1);
+  return f;
+}
+
+size_t factor_smem_bytes(const Plan& P) {
+  return 1024 + (size_t)P.rows_cap * P.np * 8 + (size_t)P.np * (P.np + 1) * 8 + kThreads * 8 + P.np * 8 + 8 * 8 +
+         P.np * 8 + 8 + 16;
+}
+
+__device__ inline void zero_smem(double* p, int count) {
+  for (int i = threadIdx.x; i < count; i += kThreads) p[i] = 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    factor_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, const Plan P,
+                  const Store st, double* __restrict__ R_out, int64_t ldr, int box_rows) {
+  extern __shared__ char smem_raw[];
+  FactorSmem f = carve_factor(smem_raw, P);
+  const Tile& S = f.S;
+  const int tid = threadIdx.x;
+  const int np = P.np, n = P.n, h = P.h;
+  const int g = blockIdx.x;
+  if (tid == 0) {
+    mbar_init(f.bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+
+  // ---- the chain: plain QR of the first leaf, then QR([R; A_k]) for each following leaf
+  const int64_t l0 = chain_first_leaf(P, g), l1 = chain_end_leaf(P, g);
+  for (int64_t leaf = l0; leaf < l1; ++leaf) {
+    const bool plain = (leaf == l0);
+    const int dst = plain ? 0 : np;
+    const int64_t row0 = leaf * h;
+    zero_smem(f.T_s, np * f.ldt);
+    if (!tile_load(S, &mapA, f.bar, phase, np, row0, h, dst, box_rows, st.status, f.flag)) {
+      if (tid == 0) tma_store_wait_all();
+      return;
+    }
+    stacked_qr(S, plain ? PLAIN : CHAIN, dst + h, np, n, f.tau_s, f.T_s, f.ldt, f.red, f.dvec, f.sc);
+    tile_store(S, &mapV, np, row0, h, dst, box_rows);
+    double* tau_g = st.tau_leaf + leaf * np;
+    double* T_g = st.t_leaf + leaf * np * np;
+    for (int i = tid; i < np; i += kThreads) tau_g[i] = f.tau_s[i];
+    for (int i = tid; i < np * np; i += kThreads) T_g[i] = f.T_s[(i / np) * f.ldt + (i % np)];
+    tile_store_drain();
+    if (plain) {  // rows 0..np-1 now carry R above the diagonal; clear the reflector part below
+      for (int i = tid; i < np * np; i += kThreads) {
+        const int r = i / np, c = i % np;
+        if (c < r) S(r, c) = 0.0;
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- publish the chain's R (level-0 node g); the reflector stores are complete first
+  if (tid == 0) tma_store_wait_all();
+  {
+    double* Rg = st.node_r + (size_t)g * np * np;
+    for (int i = tid; i < np * np; i += kThreads) {
+      const int r = i / np, c = i % np;
+      Rg[i] = (c >= r) ? S(r, c) : 0.0;
+    }
+  }
+
+  // ---- climb the tree while this block is the last child to arrive
+  int idx = g;
+  for (int level = 0; level < P.depth; ++level) {
+    const int parent = idx / P.arity;
+    const int first = parent * P.arity;
+    const int q = min(P.arity, P.level_count[level] - first);
+    const int pid = P.level_offset[level + 1] + parent;
+    const int tn = pid - P.chains;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const int prev = atomicAdd(&st.counters[tn], 1);
+      __threadfence();
+      *f.flag = (prev == q - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*f.flag == 0) return;
+    // stack the children's R factors in child order: child s at rows s*np..s*np+np-1
+    for (int s = 0; s < q; ++s) {
+      const double* Rc = st.node_r + (size_t)(P.level_offset[level] + first + s) * np * np;
+      for (int i = tid; i < np * np; i += kThreads) S(s * np + i / np, i % np) = __ldcg(Rc + i);
+    }
+    zero_smem(f.T_s, np * f.ldt);
+    __syncthreads();
+    stacked_qr(S, NODE, q * np, np, n, f.tau_s, f.T_s, f.ldt, f.red, f.dvec, f.sc);
+    double* Y = st.node_y + (size_t)tn * (P.arity - 1) * np * np;
+    for (int s = 1; s < P.arity; ++s) {
+      double* Ys = Y + (size_t)(s - 1) * np * np;
+      for (int i = tid; i < np * np; i += kThreads) {
+        const int r = i / np, c = i % np;
+        Ys[i] = (s < q && c >= r) ? S(s * np + r, c) : 0.0;
+      }
+    }
+    for (int i = tid; i < np; i += kThreads) st.node_tau[(size_t)tn * np + i] = f.tau_s[i];
+    double* Tn = st.node_t + (size_t)tn * np * np;
+    for (int i = tid; i < np * np; i += kThreads) Tn[i] = f.T_s[(i / np) * f.ldt + (i % np)];
+    double* Rp = st.node_r + (size_t)pid * np * np;
+    for (int i = tid; i < np * np; i += kThreads) {
+      const int r = i / np, c = i % np;
+      Rp[i] = (c >= r) ? S(r, c) : 0.0;
+    }
+    idx = parent;
+  }
+
+  // ---- root: R <- D R with D = diag(sign(R_jj)), sign(0) = +1
+  __syncthreads();
+  for (int j = tid; j < np; j += kThreads) st.signs[j] = (j < n && S(j, j) < 0.0) ? -1.0 : 1.0;
+  for (int i = tid; i < n * n; i += kThreads) {
+    const int r = i / n, c = i % n;
+    const double d = (S(r, r) < 0.0) ? -1.0 : 1.0;
+    R_out[(int64_t)r * ldr + c] = (c >= r) ? d * S(r, c) : 0.0;
+  }
+}
+
+cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
+                          double* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
+  const size_t smem = factor_smem_bytes(P);
+  cudaError_t e = cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(st.counters, 0, sizeof(int) * (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1), stream);
+  if (e != cudaSuccess) return e;
+  factor_kernel<<<P.chains, kThreads, smem, stream>>>(mapA, mapV, P, st, R_out, ldr, box_rows);
+  return cudaGetLastError();
+}
+
+}  // namespace tsqr

@@ -1,0 +1,21 @@
+// Host-side launchers of the TSQR kernels (internal to libtsqr.so).
+#pragma once
+
+#include "common.cuh"
+
+namespace tsqr {
+
+size_t factor_smem_bytes(const Plan& P);
+size_t formq_smem_bytes(const Plan& P);
+size_t apply_smem_bytes(const Plan& P, int kb);
+
+cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
+                          double* R_out, int64_t ldr, int box_rows, cudaStream_t stream);
+cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,
+                          int box_rows, cudaStream_t stream);
+cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+                            int64_t ldb, int box_rows, cudaStream_t stream);
+cudaError_t launch_apply_q(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+                           int64_t ldb, int box_rows, cudaStream_t stream);
+
+}  // namespace tsqr

@@ -1,0 +1,220 @@
+"""Python binding of libtsqr.so (include/tsqr.h): the same calls, marshalled through ctypes.
+
+Every step of TSQR runs in the library's CUDA kernels; this module only passes pointers,
+sizes and the current CUDA stream, and turns status codes into exceptions.  PyTorch provides
+device memory and streams.  If the library is missing the import fails loudly: there is no
+CPU or PyTorch fallback.
+
+Low level (same names as the C-ABI): ``tsqr_workspace_size``, ``tsqr_factor``,
+``tsqr_apply_qt``, ``tsqr_apply_q``, ``tsqr_form_q``, ``tsqr_status_poll``,
+``tsqr_handle_info``, ``tsqr_destroy``.  Convenience on torch tensors: ``Factorization`` and
+``qr``.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtsqr.so")
+
+TSQR_OK, TSQR_ERR_INVALID_ARG, TSQR_ERR_UNSUPPORTED, TSQR_ERR_CUDA, TSQR_ERR_WORKSPACE, TSQR_ERR_TIMEOUT = range(6)
+TSQR_F64, TSQR_F32 = 0, 1
+TSQR_ROW_MAJOR, TSQR_COL_MAJOR = 0, 1
+
+EXPORTED = ("tsqr_workspace_size", "tsqr_factor", "tsqr_apply_qt", "tsqr_apply_q", "tsqr_form_q",
+            "tsqr_status_poll", "tsqr_handle_info", "tsqr_destroy", "tsqr_status_string", "tsqr_last_error")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("leaf_h", ctypes.c_int32), ("chain", ctypes.c_int32), ("arity", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("inplace", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("np", ctypes.c_int64),
+                ("leaf_h", ctypes.c_int32), ("chain", ctypes.c_int32), ("arity", ctypes.c_int32),
+                ("depth", ctypes.c_int32),
+                ("leaves", ctypes.c_int64), ("chains", ctypes.c_int64), ("tree_nodes", ctypes.c_int64),
+                ("v", ctypes.c_void_p), ("ldv", ctypes.c_int64),
+                ("tau_leaf", ctypes.c_void_p), ("t_leaf", ctypes.c_void_p), ("node_y", ctypes.c_void_p),
+                ("node_tau", ctypes.c_void_p), ("node_t", ctypes.c_void_p), ("signs", ctypes.c_void_p)]
+
+
+class TsqrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_status_name(status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libtsqr.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libtsqr.so not found at %s: run __graft_entry__.build() first" % path)
+    lib = ctypes.CDLL(path)
+    i64, vp, sz = ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
+    lib.tsqr_workspace_size.argtypes = [ctypes.c_int, i64, i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+    lib.tsqr_factor.argtypes = [ctypes.c_int, ctypes.c_int, i64, i64, vp, i64, vp, i64, vp, sz,
+                                ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.tsqr_apply_qt.argtypes = [vp, i64, vp, i64, vp]
+    lib.tsqr_apply_q.argtypes = [vp, i64, vp, i64, vp]
+    lib.tsqr_form_q.argtypes = [vp, vp, i64, vp]
+    lib.tsqr_status_poll.argtypes = [vp, vp]
+    lib.tsqr_handle_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.tsqr_destroy.argtypes = [vp]
+    lib.tsqr_status_string.argtypes = [ctypes.c_int]
+    lib.tsqr_status_string.restype = ctypes.c_char_p
+    lib.tsqr_last_error.argtypes = []
+    lib.tsqr_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        f = getattr(lib, name)
+        if name not in ("tsqr_status_string", "tsqr_last_error"):
+            f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _status_name(s):
+    try:
+        return load().tsqr_status_string(s).decode()
+    except OSError:
+        return "status %d" % s
+
+
+def _check(status):
+    if status != TSQR_OK:
+        raise TsqrError(status, load().tsqr_last_error().decode())
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, Opts):
+        return ctypes.byref(opts)
+    return ctypes.byref(Opts(**opts))
+
+
+# ---------------------------------------------------------------- C-ABI, one to one
+def tsqr_workspace_size(dtype, m, n, opts=None):
+    out = ctypes.c_size_t(0)
+    _check(load().tsqr_workspace_size(dtype, m, n, _opts(opts), ctypes.byref(out)))
+    return out.value
+
+
+def tsqr_factor(dtype, layout, m, n, dA, lda, dR, ldr, dWork, work_bytes, opts, stream):
+    h = ctypes.c_void_p()
+    _check(load().tsqr_factor(dtype, layout, m, n, dA, lda, dR, ldr, dWork, work_bytes, _opts(opts), stream,
+                              ctypes.byref(h)))
+    return h
+
+
+def tsqr_apply_qt(h, k, dB, ldb, stream):
+    _check(load().tsqr_apply_qt(h, k, dB, ldb, stream))
+
+
+def tsqr_apply_q(h, k, dB, ldb, stream):
+    _check(load().tsqr_apply_q(h, k, dB, ldb, stream))
+
+
+def tsqr_form_q(h, dQ, ldq, stream):
+    _check(load().tsqr_form_q(h, dQ, ldq, stream))
+
+
+def tsqr_status_poll(h, stream):
+    return load().tsqr_status_poll(h, stream)
+
+
+def tsqr_handle_info(h):
+    info = Info()
+    _check(load().tsqr_handle_info(h, ctypes.byref(info)))
+    return info
+
+
+def tsqr_destroy(h):
+    load().tsqr_destroy(h)
+
+
+# ---------------------------------------------------------------- torch convenience layer
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check_matrix(X, name):
+    import torch
+
+    if not (X.is_cuda and X.dtype == torch.float64 and X.dim() == 2 and X.stride(1) == 1):
+        raise ValueError("%s must be a CUDA float64 matrix with unit column stride" % name)
+
+
+class Factorization:
+    """TSQR of a CUDA float64 matrix A (m x n, row-major).  Holds R, the workspace and the handle.
+
+    ``inplace=True`` lets the reflectors overwrite A (A must then stay alive).  Options:
+    leaf_h, chain, arity (see tsqr_opts_t).
+    """
+
+    def __init__(self, A, leaf_h=0, chain=0, arity=0, inplace=False):
+        import torch
+
+        _check_matrix(A, "A")
+        m, n = A.shape
+        self.m, self.n = m, n
+        self.opts = Opts(leaf_h=leaf_h, chain=chain, arity=arity, precision=0, inplace=1 if inplace else 0)
+        nbytes = tsqr_workspace_size(TSQR_F64, m, n, self.opts)
+        self.work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=A.device)
+        self.R = torch.empty((n, n), dtype=torch.float64, device=A.device)
+        self.A = A
+        self.handle = tsqr_factor(TSQR_F64, TSQR_ROW_MAJOR, m, n, A.data_ptr(), A.stride(0), self.R.data_ptr(), n,
+                                  self.work.data_ptr(), nbytes, self.opts, _stream())
+
+    def form_q(self, out=None):
+        import torch
+
+        Q = out if out is not None else torch.empty((self.m, self.n), dtype=torch.float64, device=self.R.device)
+        _check_matrix(Q, "Q")
+        tsqr_form_q(self.handle, Q.data_ptr(), Q.stride(0), _stream())
+        return Q
+
+    def apply_qt(self, B):
+        """B <- Q^T B in place (B: m x k CUDA float64, unit column stride)."""
+        _check_matrix(B, "B")
+        tsqr_apply_qt(self.handle, B.shape[1], B.data_ptr(), B.stride(0), _stream())
+        return B
+
+    def apply_q(self, B):
+        """B <- Q B in place."""
+        _check_matrix(B, "B")
+        tsqr_apply_q(self.handle, B.shape[1], B.data_ptr(), B.stride(0), _stream())
+        return B
+
+    def info(self):
+        return tsqr_handle_info(self.handle)
+
+    def status(self):
+        return tsqr_status_poll(self.handle, _stream())
+
+    def close(self):
+        if self.handle:
+            tsqr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qr(A, **opts):
+    """Thin QR of a CUDA float64 matrix by TSQR: returns (Q, R), diag(R) >= 0."""
+    f = Factorization(A, **opts)
+    Q = f.form_q()
+    R = f.R
+    f.close()
+    return Q, R

@@ -1,0 +1,88 @@
+"""Host-side checks of the C-ABI (no GPU): the library loads, exports every call the header
+declares, plans and sizes workspaces, and rejects bad arguments before launching anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0809_2407_gb300 import build, tsqr
+
+    build.build()
+    return tsqr
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "tsqr.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|tsqr_status_t)\s+(tsqr_\w+)\s*\(", text, re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 10
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for nm in names:
+        assert hasattr(so, nm), nm
+    assert set(names) == set(lib.EXPORTED)
+
+
+def test_status_strings(lib):
+    L = lib.load()
+    for s, nm in enumerate(["TSQR_OK", "TSQR_ERR_INVALID_ARG", "TSQR_ERR_UNSUPPORTED", "TSQR_ERR_CUDA",
+                            "TSQR_ERR_WORKSPACE", "TSQR_ERR_TIMEOUT"]):
+        assert L.tsqr_status_string(s).decode() == nm
+
+
+def test_workspace_size_grows_with_m(lib):
+    a = lib.tsqr_workspace_size(lib.TSQR_F64, 4096, 16, {"leaf_h": 256, "chain": 1, "arity": 2})
+    b = lib.tsqr_workspace_size(lib.TSQR_F64, 8192, 16, {"leaf_h": 256, "chain": 1, "arity": 2})
+    assert 0 < a < b
+    # in-place storage drops the m x n reflector copy
+    c = lib.tsqr_workspace_size(lib.TSQR_F64, 8192, 16, {"leaf_h": 256, "chain": 1, "arity": 2, "inplace": 1})
+    assert b - c >= 8192 * 16 * 8
+
+
+@pytest.mark.parametrize("m,n,opts,status", [
+    (10, 20, None, 1),                      # m < n
+    (100, 0, None, 1),                      # n < 1
+    (1000, 200, None, 2),                   # n > 64 not built yet
+    (1000, 16, {"arity": 1}, 1),
+    (1000, 16, {"arity": 9}, 1),
+    (1000, 16, {"leaf_h": 12}, 1),          # not a multiple of 8
+    (1000, 16, {"leaf_h": 8}, 1),           # below padded n
+    (1000, 16, {"leaf_h": 384}, 1),         # above 256 but not a multiple of 256
+    (1000, 16, {"precision": 3}, 2),
+])
+def test_invalid_plans(lib, m, n, opts, status):
+    with pytest.raises(lib.TsqrError) as ei:
+        lib.tsqr_workspace_size(lib.TSQR_F64, m, n, opts)
+    assert ei.value.status == status
+
+
+def test_factor_rejects_before_launch(lib):
+    L = lib.load()
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: every case fails validation first
+    # odd lda
+    assert L.tsqr_factor(0, 0, 100, 3, fake, 3, fake, 3, fake, 1 << 20, None, None, ctypes.byref(h)) == 1
+    # misaligned A
+    assert L.tsqr_factor(0, 0, 100, 4, ctypes.c_void_p(0x1008), 4, fake, 4, fake, 1 << 20, None, None,
+                         ctypes.byref(h)) == 1
+    # FP32 and column-major are not implemented
+    assert L.tsqr_factor(1, 0, 100, 4, fake, 4, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 2
+    assert L.tsqr_factor(0, 1, 100, 4, fake, 4, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 2
+    # workspace too small
+    assert L.tsqr_factor(0, 0, 100, 4, fake, 4, fake, 4, fake, 16, None, None, ctypes.byref(h)) == 4
+    assert h.value is None
+    assert b"workspace" in L.tsqr_last_error()
+    # NULL handle everywhere
+    assert L.tsqr_form_q(None, fake, 4, None) == 1
+    assert L.tsqr_apply_qt(None, 1, fake, 1, None) == 1
+    assert L.tsqr_apply_q(None, 1, fake, 1, None) == 1
+    assert L.tsqr_status_poll(None, None) == 1
+    assert L.tsqr_destroy(None) == 0

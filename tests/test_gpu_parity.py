@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA TSQR against the FP64 CPU oracle, through the C-ABI.
+
+Tolerances (FP64 path): backward error ||A - QR||_F/||A||_F <= 1e-12 and orthogonality
+||I - Q^T Q||_F <= 1e-12 everywhere; R within 1e-10 relative of the oracle's R when
+kappa(A) <= 1e6, where the sign-normalised thin QR is unique.  Q is compared elementwise with
+a bound from QR perturbation theory: two backward-stable factorizations differ in Q by about
+kappa(A) * n * eps, so the test allows 50 * kappa * n * eps (at least 1e-13).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0809_2407_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_BACK = 1e-12
+TOL_ORTH = 1e-12
+TOL_R = 1e-10
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0809_2407_gb300 import build, tsqr
+
+    build.build()
+    tsqr.load()
+    return tsqr
+
+
+def run(T, A_h, lda=None, **opts):
+    import torch
+
+    m, n = A_h.shape
+    if lda is not None and lda != n:
+        buf = torch.zeros((m, lda), dtype=torch.float64, device="cuda")
+        buf[:, :n] = torch.from_numpy(A_h).cuda()
+        A = buf[:, :n]
+    else:
+        A = torch.from_numpy(np.ascontiguousarray(A_h)).cuda()
+    f = T.Factorization(A, **opts)
+    Q = f.form_q()
+    torch.cuda.synchronize()
+    assert f.status() == T.TSQR_OK
+    return f, f.R.cpu().numpy(), Q.cpu().numpy()
+
+
+def check_against_oracle(A_h, R, Q, unique=True):
+    assert np.all(np.tril(R, -1) == 0.0)
+    assert np.all(np.diag(R) >= 0.0)
+    assert oracle.backward_error(A_h, Q, R) <= TOL_BACK
+    assert oracle.orthogonality(Q) <= TOL_ORTH
+    if unique:
+        ref = oracle.qr(A_h)
+        assert np.linalg.norm(R - ref["R"]) / np.linalg.norm(ref["R"]) <= TOL_R
+        kappa = np.linalg.cond(ref["R"])
+        n = A_h.shape[1]
+        assert np.abs(Q - ref["Q"]).max() <= max(1e-13, 50 * kappa * n * EPS)
+
+
+def test_config1_binary_tree(T):
+    """4096 x 16 N(0,1), leaf height 256, binary tree over 16 leaves."""
+    A_h = inputs.gaussian(4096, 16, inputs.seed_for(1, 0))
+    f, R, Q = run(T, A_h, leaf_h=256, chain=1, arity=2)
+    info = f.info()
+    assert (info.leaves, info.chains, info.depth) == (16, 16, 4)
+    check_against_oracle(A_h, R, Q)
+
+
+@pytest.mark.parametrize("chain,arity", [(1, 2), (1, 3), (1, 4), (1, 8), (2, 2), (3, 2), (5, 3), (0, 2), (1000, 2)])
+def test_tree_shapes(T, chain, arity):
+    """Any tree gives the QR of A (Sec. 2): binary, k-ary, flat chains, hybrids, single chain."""
+    A_h = inputs.gaussian(3000, 24, inputs.seed_for(2, chain * 10 + arity))
+    _, R, Q = run(T, A_h, leaf_h=128, chain=chain, arity=arity)
+    check_against_oracle(A_h, R, Q)
+
+
+@pytest.mark.parametrize("m,n,h", [(4096 + 77, 16, 256), (1000, 64, 128), (129, 64, 64), (65, 64, 64),
+                                   (130, 30, 64), (16, 16, 16), (1, 1, 16), (777, 1, 16), (5000, 5, 512),
+                                   (2000, 50, 128), (3333, 33, 128), (64 * 7 + 3, 64, 64)])
+def test_ragged_and_edge_shapes(T, m, n, h):
+    A_h = inputs.gaussian(m, n, inputs.seed_for(3, m + n + h))
+    lda = n + (n % 2)
+    _, R, Q = run(T, A_h, lda=lda, leaf_h=h, chain=0 if m > 1000 else 2, arity=2)
+    check_against_oracle(A_h, R, Q)
+
+
+def test_short_last_leaf_is_merged(T):
+    """A last leaf with fewer than n rows joins the previous chain instead of starting one."""
+    A_h = inputs.gaussian(64 * 4 + 5, 32, 77)
+    f, R, Q = run(T, A_h, leaf_h=64, chain=1, arity=2)
+    assert f.info().chains == 4
+    check_against_oracle(A_h, R, Q)
+
+
+def test_strided_and_inplace(T):
+    import torch
+
+    A_h = inputs.gaussian(2500, 20, 31)
+    _, R1, Q1 = run(T, A_h, lda=36, leaf_h=128, chain=3)
+    check_against_oracle(A_h, R1, Q1)
+    A = torch.from_numpy(A_h.copy()).cuda()
+    f = T.Factorization(A, leaf_h=128, chain=3, inplace=True)
+    Q2 = f.form_q().cpu().numpy()
+    assert np.array_equal(f.R.cpu().numpy(), R1)
+    assert np.array_equal(Q2, Q1)
+    # the reflectors now live in A
+    assert not np.array_equal(A.cpu().numpy(), A_h)
+
+
+@pytest.mark.parametrize("kind,k", [("usv", 0), ("usv", 6), ("usv", 12), ("krylov", None)])
+def test_conditioning(T, kind, k):
+    m, n = 1 << 14, 32
+    A_h = inputs.usv(m, n, k, 55 + (k or 0)) if kind == "usv" else inputs.krylov(m, n, 56)
+    _, R, Q = run(T, A_h, leaf_h=256)
+    check_against_oracle(A_h, R, Q, unique=(kind == "usv" and k <= 6))
+
+
+def test_apply_qt_apply_q(T):
+    import torch
+
+    m, n, k = 5000, 24, 7
+    A_h = inputs.gaussian(m, n, 91)
+    B_h = inputs.gaussian(m, k, 92)
+    f, R, Q = run(T, A_h, leaf_h=128, chain=4, arity=3)
+    B = torch.from_numpy(B_h.copy()).cuda()
+    f.apply_qt(B)
+    QtB = B.cpu().numpy()
+    # thin part against the oracle: D (H_{n-1} ... H_0 B)_{0:n}
+    assert np.abs(QtB[:n] - oracle.thin_qt(A_h, B_h)).max() <= 1e-11
+    # Q^T is orthogonal: norms of columns kept
+    assert np.allclose(np.linalg.norm(QtB, axis=0), np.linalg.norm(B_h, axis=0), rtol=1e-13)
+    # Q^T A = [R; 0]
+    Ad = torch.from_numpy(A_h.copy()).cuda()
+    f.apply_qt(Ad)
+    QtA = Ad.cpu().numpy()
+    assert np.abs(QtA[:n] - R).max() <= 1e-11 * np.abs(R).max()
+    assert np.abs(QtA[n:]).max() <= 1e-11 * np.abs(R).max()
+    # Q Q^T B = B
+    f.apply_q(B)
+    assert np.abs(B.cpu().numpy() - B_h).max() <= 1e-12
+    # form_q equals Q [I; 0]
+    E = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    E[:n] = torch.eye(n, dtype=torch.float64, device="cuda")
+    f.apply_q(E)
+    assert np.abs(E.cpu().numpy() - Q).max() <= 1e-13
+
+
+@pytest.mark.parametrize("k", [1, 2, 33, 64 * 32 + 5])
+def test_apply_column_counts(T, k):
+    import torch
+
+    m, n = 3000, 16
+    A_h = inputs.gaussian(m, n, 101)
+    B_h = inputs.gaussian(m, k, 102)
+    f, _, _ = run(T, A_h, leaf_h=256, chain=2)
+    B = torch.from_numpy(B_h.copy()).cuda()
+    f.apply_qt(B)
+    assert np.abs(B.cpu().numpy()[:n] - oracle.thin_qt(A_h, B_h)).max() <= 1e-11
+    f.apply_q(B)
+    assert np.abs(B.cpu().numpy() - B_h).max() <= 1e-12
+
+
+def test_node_structure_eq_fact_2rs(T):
+    """Tree-node reflectors: lower blocks upper triangular (eq. fact_2rs), T upper triangular."""
+    A_h = inputs.gaussian(2048, 16, 5)
+    f, R, Q = run(T, A_h, leaf_h=128, chain=1, arity=4)
+    info = f.info()
+    np_ = info.np
+    Y = workspace_view(f, info.node_y, info.tree_nodes * (info.arity - 1) * np_ * np_)
+    Y = Y.reshape(info.tree_nodes, info.arity - 1, np_, np_)
+    assert np.all(np.tril(Y, -1) == 0.0)
+    assert np.count_nonzero(np.triu(Y[:, :, :16, :16])) > 0
+    Tn = workspace_view(f, info.node_t, info.tree_nodes * np_ * np_).reshape(info.tree_nodes, np_, np_)
+    assert np.all(np.tril(Tn, -1) == 0.0)
+    tau = workspace_view(f, info.node_tau, info.tree_nodes * np_).reshape(info.tree_nodes, np_)
+    assert np.array_equal(np.diagonal(Tn, axis1=1, axis2=2), tau)
+
+
+def workspace_view(f, ptr, count):
+    """`count` doubles of the factorization's workspace starting at device pointer ptr."""
+    import torch
+
+    torch.cuda.synchronize()
+    off = ptr - f.work.data_ptr()
+    assert 0 <= off and off + 8 * count <= f.work.numel()
+    return f.work[off:off + 8 * count].view(torch.float64).cpu().numpy()
+
+
+def test_deterministic(T):
+    A_h = inputs.gaussian(20000, 32, 17)
+    _, R1, Q1 = run(T, A_h)
+    _, R2, Q2 = run(T, A_h)
+    assert np.array_equal(R1, R2) and np.array_equal(Q1, Q2)
+
+
+def test_virtual_ranks(T):
+    """Distributed TSQR algebra on one GPU: factor P row slabs separately, then the stacked R's."""
+    import torch
+
+    A_h = inputs.gaussian(8000, 16, 23)
+    _, R_one, _ = run(T, A_h)
+    Rs = []
+    for s in np.array_split(np.arange(8000), 4):
+        _, Rp, _ = run(T, A_h[s])
+        Rs.append(Rp)
+    _, R_two, _ = run(T, np.vstack(Rs), leaf_h=16, chain=1)
+    assert np.abs(R_two - R_one).max() <= 1e-12 * np.abs(R_one).max()
+
+
+def test_full_size_properties(T):
+    """m = 2^22, n = 64, A = U Sigma V^T with kappa = 1 (the benchmark's workload and launch
+    configuration).  At kappa = 1 the Cholesky factor of A^T A (a library routine on the Gram
+    matrix) equals R to ~eps, which pins R elementwise; A = QR and Q^T Q = I are checked with
+    FP64 GEMMs on the device."""
+    import torch
+
+    m, n = 1 << 22, 64
+    A_h = inputs.usv(m, n, 0.0, inputs.seed_for(2, 0))
+    A = torch.from_numpy(A_h).cuda()
+    f = T.Factorization(A)
+    Q = f.form_q()
+    torch.cuda.synchronize()
+    assert f.status() == T.TSQR_OK
+    R = f.R
+    G = A_h.T @ A_h
+    L = np.linalg.cholesky(G)
+    Rc = L.T
+    assert np.abs(R.cpu().numpy() - Rc).max() <= 1e-12
+    be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
+    orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device="cuda") - Q.T @ Q).item()
+    assert be <= TOL_BACK and orth <= TOL_ORTH
