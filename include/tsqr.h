@@ -120,6 +120,23 @@ tsqr_status_t tsqr_status_poll(tsqr_handle_t h, tsqr_stream_t stream);
 /* Fills *info with the plan and workspace pointers of h. */
 tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info);
 
+/* R only, with no workspace and no allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc or hand the library a workspace, such as code
+ * running while a stream is captured in global capture mode, code inside another runtime's
+ * allocator or callbacks, or C hosts without a device allocator.
+ *   A  : device, m x n (m >= n >= 1), lda >= n and even, 16-byte aligned; read only.
+ *   dR : device, n x n with ldr >= n; receives R with diag(R) >= 0, strict lower zeroed.
+ * Same tree as tsqr_factor, except that the number of chains is capped so the scratch fits.
+ * The scratch is a static 8 MiB device array inside libtsqr.so, held on every GPU that loads
+ * the library until the process exits.  A problem whose tree needs more returns
+ * TSQR_ERR_UNSUPPORTED.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress); make that first call before any stream capture starts.  Calls share
+ * the array: each clears what must start at zero, and calls that overlap on the GPU (on
+ * streams with no ordering between them) race and give wrong results.  The implicit Q is not
+ * kept, so there is no handle. */
+tsqr_status_t tsqr_factor_r_noalloc(int64_t m, int64_t n, const void* dA, int64_t lda, void* dR, int64_t ldr,
+                                    tsqr_stream_t stream);
+
 /* Frees the host handle (the workspace stays the caller's). NULL is a no-op. */
 tsqr_status_t tsqr_destroy(tsqr_handle_t h);
 

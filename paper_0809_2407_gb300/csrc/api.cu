@@ -337,3 +337,13 @@ tsqr_status_t tsqr_destroy(tsqr_handle_t h) {
 }
 
 }  // extern "C"
+
+namespace tsqr {
+tsqr_status_t internal_make_plan(int64_t m, int64_t n, const tsqr_opts_t* opts, Plan* P) {
+  return make_plan(m, n, opts, P);
+}
+tsqr_status_t internal_make_map(CUtensorMap* map, const void* ptr, int64_t m, int64_t n, int64_t ld, int box_rows) {
+  return make_map(map, ptr, m, n, ld, box_rows);
+}
+tsqr_status_t internal_fail(tsqr_status_t s, const char* msg) { return fail(s, msg); }
+}  // namespace tsqr

@@ -21,7 +21,8 @@ TSQR_F64, TSQR_F32 = 0, 1
 TSQR_ROW_MAJOR, TSQR_COL_MAJOR = 0, 1
 
 EXPORTED = ("tsqr_workspace_size", "tsqr_factor", "tsqr_apply_qt", "tsqr_apply_q", "tsqr_form_q",
-            "tsqr_status_poll", "tsqr_handle_info", "tsqr_destroy", "tsqr_status_string", "tsqr_last_error")
+            "tsqr_status_poll", "tsqr_handle_info", "tsqr_destroy", "tsqr_status_string", "tsqr_last_error",
+            "tsqr_factor_r_noalloc")
 
 
 class Opts(ctypes.Structure):
@@ -66,6 +67,7 @@ def load(path: str = LIB_PATH):
     lib.tsqr_status_poll.argtypes = [vp, vp]
     lib.tsqr_handle_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.tsqr_destroy.argtypes = [vp]
+    lib.tsqr_factor_r_noalloc.argtypes = [i64, i64, vp, i64, vp, i64, vp]
     lib.tsqr_status_string.argtypes = [ctypes.c_int]
     lib.tsqr_status_string.restype = ctypes.c_char_p
     lib.tsqr_last_error.argtypes = []
@@ -136,6 +138,11 @@ def tsqr_handle_info(h):
 
 def tsqr_destroy(h):
     load().tsqr_destroy(h)
+
+
+def tsqr_factor_r_noalloc(m, n, dA, lda, dR, ldr, stream):
+    """R only, using the library's static device scratch: for callers that cannot allocate."""
+    _check(load().tsqr_factor_r_noalloc(m, n, dA, lda, dR, ldr, stream))
 
 
 # ---------------------------------------------------------------- torch convenience layer
