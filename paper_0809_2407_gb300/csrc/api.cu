@@ -54,7 +54,7 @@ int default_leaf_h(int np) {
   switch (np) {
     case 16: return 512;
     case 32: return 256;
-    default: return 128;
+    default: return 96;  // np = 64: tile + packed T fit twice in one SM's shared memory
   }
 }
 
@@ -82,8 +82,8 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P) {
   P->leaves = (m + h - 1) / h;
   int64_t chain = o->chain;
   if (chain == 0) {
-    const int sms = device_sms();
-    chain = (P->leaves + sms - 1) / sms;
+    const int blocks = 2 * device_sms();  // two factor blocks per SM
+    chain = (P->leaves + blocks - 1) / blocks;
   }
   if (chain > P->leaves) chain = P->leaves;
   int64_t chains = (P->leaves + chain - 1) / chain;

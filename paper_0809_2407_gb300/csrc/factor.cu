@@ -21,16 +21,14 @@ struct FactorSmem {
   double *T_s, *red, *dvec, *sc, *tau_s;
   uint64_t* bar;
   int* flag;
-  int ldt;
 };
 
 __device__ inline FactorSmem carve_factor(char* raw, const Plan& P) {
   FactorSmem f;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   f.S = Tile{base, P.rows_cap};
-  f.ldt = P.np + 1;
   f.T_s = reinterpret_cast<double*>(base + (size_t)P.rows_cap * P.np * 8);
-  f.red = f.T_s + P.np * f.ldt;
+  f.red = f.T_s + tri_size(P.np);
   f.dvec = f.red + kThreads;
   f.sc = f.dvec + P.np;
   f.tau_s = f.sc + 8;
@@ -40,15 +38,11 @@ __device__ inline FactorSmem carve_factor(char* raw, const Plan& P) {
 }
 
 size_t factor_smem_bytes(const Plan& P) {
-  return 1024 + (size_t)P.rows_cap * P.np * 8 + (size_t)P.np * (P.np + 1) * 8 + kThreads * 8 + P.np * 8 + 8 * 8 +
+  return 1024 + (size_t)P.rows_cap * P.np * 8 + (size_t)tri_size(P.np) * 8 + kThreads * 8 + P.np * 8 + 8 * 8 +
          P.np * 8 + 8 + 16;
 }
 
-__device__ inline void zero_smem(double* p, int count) {
-  for (int i = threadIdx.x; i < count; i += kThreads) p[i] = 0.0;
-}
-
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     factor_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, const Plan P,
                   const Store st, double* __restrict__ R_out, int64_t ldr, int box_rows) {
   extern __shared__ char smem_raw[];
@@ -70,17 +64,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool plain = (leaf == l0);
     const int dst = plain ? 0 : np;
     const int64_t row0 = leaf * h;
-    zero_smem(f.T_s, np * f.ldt);
     if (!tile_load(S, &mapA, f.bar, phase, np, row0, h, dst, box_rows, st.status, f.flag)) {
       if (tid == 0) tma_store_wait_all();
       return;
     }
-    stacked_qr(S, plain ? PLAIN : CHAIN, dst + h, np, n, f.tau_s, f.T_s, f.ldt, f.red, f.dvec, f.sc);
+    stacked_qr(S, plain ? PLAIN : CHAIN, dst + h, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
     tile_store(S, &mapV, np, row0, h, dst, box_rows);
     double* tau_g = st.tau_leaf + leaf * np;
     double* T_g = st.t_leaf + leaf * np * np;
     for (int i = tid; i < np; i += kThreads) tau_g[i] = f.tau_s[i];
-    for (int i = tid; i < np * np; i += kThreads) T_g[i] = f.T_s[(i / np) * f.ldt + (i % np)];
+    for (int i = tid; i < np * np; i += kThreads) {
+      const int a = i / np, b = i % np;
+      T_g[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : 0.0;
+    }
     tile_store_drain();
     if (plain) {  // rows 0..np-1 now carry R above the diagonal; clear the reflector part below
       for (int i = tid; i < np * np; i += kThreads) {
@@ -123,9 +119,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double* Rc = st.node_r + (size_t)(P.level_offset[level] + first + s) * np * np;
       for (int i = tid; i < np * np; i += kThreads) S(s * np + i / np, i % np) = __ldcg(Rc + i);
     }
-    zero_smem(f.T_s, np * f.ldt);
     __syncthreads();
-    stacked_qr(S, NODE, q * np, np, n, f.tau_s, f.T_s, f.ldt, f.red, f.dvec, f.sc);
+    stacked_qr(S, NODE, q * np, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
     double* Y = st.node_y + (size_t)tn * (P.arity - 1) * np * np;
     for (int s = 1; s < P.arity; ++s) {
       double* Ys = Y + (size_t)(s - 1) * np * np;
@@ -136,7 +131,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = tid; i < np; i += kThreads) st.node_tau[(size_t)tn * np + i] = f.tau_s[i];
     double* Tn = st.node_t + (size_t)tn * np * np;
-    for (int i = tid; i < np * np; i += kThreads) Tn[i] = f.T_s[(i / np) * f.ldt + (i % np)];
+    for (int i = tid; i < np * np; i += kThreads) {
+      const int a = i / np, b = i % np;
+      Tn[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : 0.0;
+    }
     double* Rp = st.node_r + (size_t)pid * np * np;
     for (int i = tid; i < np * np; i += kThreads) {
       const int r = i / np, c = i % np;

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool plain = (leaf == l0);
     const int dst = plain ? 0 : np;
     if (!tile_load(S, &mapA, bar, phase, np, leaf * h, h, dst, box_rows, status, flag)) return;
-    stacked_qr(S, plain ? PLAIN : CHAIN, dst + h, np, n, tau_s, nullptr, 0, red, dvec, sc);
+    stacked_qr(S, plain ? PLAIN : CHAIN, dst + h, np, n, tau_s, nullptr, red, dvec, sc);
     if (plain) {
       for (int i = tid; i < np * np; i += kThreads) {
         const int r = i / np, c = i % np;
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int i = tid; i < np * np; i += kThreads) S(s * np + i / np, i % np) = __ldcg(Rc + i);
     }
     __syncthreads();
-    stacked_qr(S, NODE, q * np, np, n, tau_s, nullptr, 0, red, dvec, sc);
+    stacked_qr(S, NODE, q * np, np, n, tau_s, nullptr, red, dvec, sc);
     double* Rp = node_r + (size_t)pid * np * np;
     for (int i = tid; i < np * np; i += kThreads) {
       const int r = i / np, c = i % np;

@@ -93,13 +93,17 @@ __device__ inline void make_reflector(const Tile& S, int kind, int N, int np, in
   __syncthreads();
 }
 
+// Packed upper-triangular storage of T: row i holds T[i][i..np-1] starting at tri_off(i, np).
+__host__ __device__ __forceinline__ int tri_off(int i, int np) { return i * np - (i * (i - 1)) / 2; }
+__host__ __device__ __forceinline__ int tri_size(int np) { return np * (np + 1) / 2; }
+
 // QR of the stacked matrix S (rows 0..N-1, real columns 0..n-1 of np; np a power of two in
-// 16..128).  On return rows 0..n-1 hold R in their upper triangle and the reflectors' entries
+// 16..64).  On return rows 0..n-1 hold R in their upper triangle and the reflectors' entries
 // below their pivots sit where the zeros were created (for CHAIN/NODE the top block's strict
 // lower part stays zero; it must be zero on entry).  tau_s[0..np) receives tau (0 beyond n);
-// if T_s != nullptr, T (np x np, leading dimension ldt) must be zero on entry and receives T.
-// red needs kThreads doubles, dvec np doubles, sc 4 doubles.  All threads must call.
-__device__ inline void stacked_qr(const Tile& S, int kind, int N, int np, int n, double* tau_s, double* T_s, int ldt,
+// if T_s != nullptr it receives T packed by rows (tri_off; tri_size(np) doubles, any contents
+// on entry).  red needs kThreads doubles, dvec np doubles, sc 4 doubles.  All threads must call.
+__device__ inline void stacked_qr(const Tile& S, int kind, int N, int np, int n, double* tau_s, double* T_s,
                                   double* red, double* dvec, double* sc) {
   const int tid = threadIdx.x;
   const int G = kThreads / np;  // row groups of the (column, group) mapping
@@ -138,21 +142,32 @@ __device__ inline void stacked_qr(const Tile& S, int kind, int N, int np, int n,
       if (tid == 0) S(j, j) = beta;
       __syncthreads();
       if (T_s != nullptr && tid < j) {
+        const double* Ti = T_s + tri_off(tid, np) - tid;  // Ti[p] = T[tid][p]
         double s = 0.0;
-        for (int p = tid; p < j; ++p) s = fma(T_s[tid * ldt + p], dvec[p], s);
-        T_s[tid * ldt + j] = -tau * s;
+        for (int p = tid; p < j; ++p) s = fma(Ti[p], dvec[p], s);
+        T_s[tri_off(tid, np) + (j - tid)] = -tau * s;
       }
-      // trailing update S(r, c) -= tau d_c y_r
-      if (cown > j && cown < n) {
-        const double w = tau * dvec[cown];
-        for (int r = r_lo + gown; r < N; r += G) {
-          if (skip_row(kind, r, j, np)) continue;
-          S(r, cown) = fma(-w, S(r, j), S(r, cown));
+      // trailing update S(r, c) -= tau d_c y_r.  Only the ac = n-1-j columns right of j take
+      // part, so they are spread over all threads afresh for every j: an FP64 instruction costs
+      // the same whatever its active-lane count, and a fixed column-per-lane map would leave
+      // the lanes of finished columns idle.
+      const int ac = n - 1 - j;
+      if (ac > 0) {
+        const int Gu = kThreads / ac;
+        if (tid < Gu * ac) {
+          const int c = j + 1 + tid % ac;
+          const int gu = tid / ac;
+          const double w = tau * dvec[c];
+          for (int r = r_lo + gu; r < N; r += Gu) {
+            if (skip_row(kind, r, j, np)) continue;
+            S(r, c) = fma(-w, S(r, j), S(r, c));
+          }
         }
       }
     }
+    if (!active && T_s != nullptr && tid < j) T_s[tri_off(tid, np) + (j - tid)] = 0.0;
     if (tid == j) {
-      if (T_s != nullptr) T_s[j * ldt + j] = tau;
+      if (T_s != nullptr) T_s[tri_off(j, np)] = tau;
       tau_s[j] = tau;
     }
     __syncthreads();
