@@ -164,6 +164,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=1 << 17, help="oracle rows of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip timing the double-float precision form")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -201,63 +202,75 @@ def main():
     b = b_h.to(dev)  # Q^T is applied to it in place every step; it stays a unit-scale vector
     Q = torch.empty((m, n), dtype=torch.float64, device=dev)
     R = torch.empty((n, n), dtype=torch.float64, device=dev)
-    opts = tsqr.Opts()
-    nbytes = tsqr.tsqr_workspace_size(tsqr.TSQR_F64, m, n, opts)
-    work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sptr = tsqr.ctypes.c_void_p(stream.cuda_stream)
+    work_holder = {}
 
-    ev = {k: [] for k in ("factor", "form_q", "apply_qt")}
+    def run_mode(precision, steps, warmup, sample_clocks):
+        """Times `steps` full steps in one arithmetic mode; returns timings and accuracy."""
+        opts = tsqr.Opts(precision=precision)
+        nbytes = tsqr.tsqr_workspace_size(tsqr.TSQR_F64, m, n, opts)
+        if work_holder.get("bytes", 0) < nbytes:
+            work_holder.pop("t", None)
+            torch.cuda.empty_cache()
+            work_holder["t"] = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            work_holder["bytes"] = nbytes
+        work = work_holder["t"]
 
-    def step(record):
-        marks = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
-        if record:
-            marks[0].record(stream)
-        h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
-                             work.data_ptr(), nbytes, opts, sptr)
-        if record:
-            marks[1].record(stream)
-        tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
-        if record:
-            marks[2].record(stream)
-        tsqr.tsqr_apply_qt(h, 1, b.data_ptr(), 1, sptr)
-        if record:
-            marks[3].record(stream)
-        tsqr.tsqr_destroy(h)
-        return marks
+        def step(record):
+            marks = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+            if record:
+                marks[0].record(stream)
+            h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
+                                 work.data_ptr(), nbytes, opts, sptr)
+            if record:
+                marks[1].record(stream)
+            tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
+            if record:
+                marks[2].record(stream)
+            tsqr.tsqr_apply_qt(h, 1, b.data_ptr(), 1, sptr)
+            if record:
+                marks[3].record(stream)
+            tsqr.tsqr_destroy(h)
+            return marks
 
-    for _ in range(args.warmup):
-        step(False)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    sampler = ClockSampler(local) if rank == 0 else None
-    if sampler:
-        sampler.start()
-        time.sleep(0.3)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    t0.record(stream)
-    all_marks = []
-    for _ in range(args.steps):
-        all_marks.append(step(True))
-    t1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop() if sampler else None
-    ms = t0.elapsed_time(t1)
-    for mk in all_marks:
-        ev["factor"].append(mk[0].elapsed_time(mk[1]))
-        ev["form_q"].append(mk[1].elapsed_time(mk[2]))
-        ev["apply_qt"].append(mk[2].elapsed_time(mk[3]))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+        for _ in range(warmup):
+            step(False)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        sampler = ClockSampler(local) if (rank == 0 and sample_clocks) else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        all_marks = [step(True) for _ in range(steps)]
+        t1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms = t0.elapsed_time(t1)
+        ev = {"factor": [mk[0].elapsed_time(mk[1]) for mk in all_marks],
+              "form_q": [mk[1].elapsed_time(mk[2]) for mk in all_marks],
+              "apply_qt": [mk[2].elapsed_time(mk[3]) for mk in all_marks]}
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+        be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
+        orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Q.T @ Q).item()
+        return {"ms": ms, "ev": ev, "be": be, "orth": orth, "clocks": clocks, "opts": opts, "nbytes": nbytes}
 
-    # accuracy of the last step
-    be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
-    orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Q.T @ Q).item()
+    main_mode = run_mode(0, args.steps, args.warmup, True)
+    ms = main_mode["ms"]
+    ev = main_mode["ev"]
+    clocks = main_mode["clocks"]
+    be, orth = main_mode["be"], main_mode["orth"]
+    opts = main_mode["opts"]
+    nbytes = main_mode["nbytes"]
+    work = work_holder["t"]
 
     fl = flops(m, n)
     per_step = sum(fl.values())
@@ -279,6 +292,18 @@ def main():
                 "peak_source": "FP64 pipe, 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
                 "hbm_view": {"achieved_gbs": ab[dom] / (dom_ms / 1e3) / 1e9, "peak_gbs": hbm,
                              "frac_of_measured": (ab[dom] / (dom_ms / 1e3) / 1e9 / hbm) if hbm else None}}
+
+    # precision forms on the same workload (reported beside the plain FP64 line)
+    forms = {}
+    if not args.no_forms:
+        dfm = run_mode(1, args.steps, min(args.warmup, 3), False)
+        d_ms = dfm["ms"] / args.steps
+        forms["double_float"] = {
+            "precision": 1, "dtype": "f32x2", "value": per_step * world / (d_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+            "ms_per_step": d_ms, "speedup_vs_f64": ms_step / d_ms,
+            "kernel_ms": {k: statistics.mean(v) for k, v in dfm["ev"].items()},
+            "backward_error": dfm["be"], "orthogonality": dfm["orth"]}
+        opts = tsqr.Opts(precision=0)
 
     # end to end through the C-ABI with host buffers: H2D of A and b, D2H of R, Q and Q^T b
     e2e = None
@@ -326,7 +351,7 @@ def main():
                           "parallelism": "replicas" if world > 1 else "single-gpu"},
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roofline, "precision_forms": forms, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": 3 * args.steps, "clocks": clocks}
         print(json.dumps(out), flush=True)
     if dist:

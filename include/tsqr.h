@@ -61,7 +61,12 @@ typedef struct {
   int32_t chain;     /* leaves combined sequentially by one thread block (flat tree);
                         1 = every leaf is its own tree leaf (pure arity-q tree); 0 = auto */
   int32_t arity;     /* children per node of the tree over thread blocks, 2..8; 0 = 2 */
-  int32_t precision; /* 0 = native FP64 arithmetic everywhere (the only mode so far) */
+  int32_t precision; /* 0 = native FP64 arithmetic everywhere.
+                        1 = double-float: FP64 in and out, every operation of the path on pairs
+                            of FP32 numbers (about 48 significant bits, unit roundoff ~2^-46) on
+                            the FP32 pipe.  Magnitudes of A's and B's nonzero entries should lie
+                            in about [2^-100, 2^100]; the stored factors (and A, with inplace)
+                            then hold (hi, lo) FP32 pairs in each 8-byte slot. */
   int32_t inplace;   /* nonzero: the leaf reflectors overwrite A (Sec. 4.2 storage) and A's
                         upper triangles hold intermediate R factors; zero: A is read only */
 } tsqr_opts_t;

@@ -66,7 +66,8 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P) {
   int np = 16;
   while (np < n) np *= 2;
   if (np > 64) return fail(TSQR_ERR_UNSUPPORTED, "n > 64 is not supported by this build");
-  if (o->precision != 0) return fail(TSQR_ERR_UNSUPPORTED, "only precision 0 (native FP64) is implemented");
+  if (o->precision != 0 && o->precision != 1)
+    return fail(TSQR_ERR_UNSUPPORTED, "precision must be 0 (native FP64) or 1 (double-float)");
   const int arity = o->arity ? o->arity : 2;
   if (arity < 2 || arity > tsqr::kMaxArity) return fail(TSQR_ERR_INVALID_ARG, "arity must be in 2..8");
   int h = o->leaf_h ? o->leaf_h : default_leaf_h(np);
@@ -79,10 +80,15 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P) {
   P->np = np;
   P->h = h;
   P->arity = arity;
+  P->precision = o->precision;
   P->leaves = (m + h - 1) / h;
   int64_t chain = o->chain;
   if (chain == 0) {
-    const int blocks = 2 * device_sms();  // two factor blocks per SM
+    // Native FP64: two factor blocks per SM, one chain each.  Double-float: eight times as many
+    // shorter chains, because the loss of orthogonality grows with the number of reflectors on
+    // a row's path to the root (about sqrt(chain * n) units of roundoff), and the double-float
+    // unit roundoff is 2^-46.
+    const int blocks = (o->precision == 1 ? 16 : 2) * device_sms();
     chain = (P->leaves + blocks - 1) / blocks;
   }
   if (chain > P->leaves) chain = P->leaves;

@@ -6,52 +6,66 @@
 // root -> leaves (a broadcast) (Sec. 4.1).  Every local factor is applied in compact-WY form
 // (Sec. 3.2): with V = [I; Y] the node update is D = C0 + Y^T C1, C0 -= T^T D, C1 -= Y T^T D
 // for Q^T, and the same with T in place of T^T for Q.
+//
+// Every kernel is a template on the arithmetic policy (arith.cuh); the factors in the
+// workspace are in that policy's element format, B and Q are FP64 at the boundary.
+#include "arith.cuh"
 #include "factor_kernels.h"
 
 namespace tsqr {
 
-// ------------------------------------------------------------------------------------------
-// small dense helpers on row-major shared matrices (leading dimension given)
+template <class E>
+__device__ __forceinline__ E& tat(const Tile& S, int r, int c) {
+  return *reinterpret_cast<E*>(S.ptr(r, c));
+}
 
 // M (np x kb) = T * C (trans = false) or T^T * C (trans = true), T upper triangular n x n.
-__device__ inline void tri_mul(const double* T, int ldt, const double* C, int ldc, double* M, int ldm, int n, int np,
-                               int kb, bool trans) {
+template <class Ar>
+__device__ inline void tri_mul(const typename Ar::E* T, int ldt, const typename Ar::E* C, int ldc,
+                               typename Ar::E* M, int ldm, int n, int np, int kb, bool trans) {
+  using E = typename Ar::E;
   for (int o = threadIdx.x; o < np * kb; o += kThreads) {
     const int a = o / kb, b = o % kb;
-    double s = 0.0;
+    E s = Ar::zero();
     if (a < n) {
       if (!trans) {
-        for (int p = a; p < n; ++p) s = fma(T[a * ldt + p], C[p * ldc + b], s);
+        for (int p = a; p < n; ++p) Ar::fma_acc(s, T[a * ldt + p], C[p * ldc + b]);
       } else {
-        for (int p = 0; p <= a; ++p) s = fma(T[p * ldt + a], C[p * ldc + b], s);
+        for (int p = 0; p <= a; ++p) Ar::fma_acc(s, T[p * ldt + a], C[p * ldc + b]);
       }
     }
-    M[o / kb * ldm + b] = s;
+    M[a * ldm + b] = Ar::add(s, Ar::zero());
   }
 }
 
-// Copies an np x np row-major global matrix into shared memory with leading dimension ld.
-__device__ inline void load_square(const double* __restrict__ g, double* s, int np, int ld) {
-  for (int i = threadIdx.x; i < np * np; i += kThreads) s[(i / np) * ld + (i % np)] = __ldcg(g + i);
+// Copies an np x np row-major matrix of 8-byte elements into shared memory (leading dim ld).
+template <class E>
+__device__ inline void load_square(const double* __restrict__ g, E* s, int np, int ld) {
+  for (int i = threadIdx.x; i < np * np; i += kThreads) {
+    const double v = __ldcg(g + i);
+    s[(i / np) * ld + (i % np)] = *reinterpret_cast<const E*>(&v);
+  }
 }
 
 // ------------------------------------------------------------------------------------------
 // explicit thin Q
 
+template <class E>
 struct FormQSmem {
   Tile S;
-  double *C, *M, *T, *X;
+  E *C, *M, *T, *X;
   uint64_t* bar;
   int* flag;
   int ld;
 };
 
-__device__ inline FormQSmem carve_formq(char* raw, const Plan& P) {
-  FormQSmem f;
+template <class E>
+__device__ inline FormQSmem<E> carve_formq(char* raw, const Plan& P) {
+  FormQSmem<E> f;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   f.S = Tile{base, P.h};
   f.ld = P.np + 1;
-  f.C = reinterpret_cast<double*>(base + (size_t)P.h * P.np * 8);
+  f.C = reinterpret_cast<E*>(base + (size_t)P.h * P.np * 8);
   f.M = f.C + P.np * f.ld;
   f.T = f.M + P.np * f.ld;
   f.X = f.T + P.np * f.ld;
@@ -64,13 +78,67 @@ size_t formq_smem_bytes(const Plan& P) {
   return 1024 + (size_t)P.h * P.np * 8 + 4 * (size_t)P.np * (P.np + 1) * 8 + 8 + 16;
 }
 
-// Q rows of one leaf.  chain step (V = [I; Y]):  Q_rows = -Y M with M = T C, then C -= M.
-// first leaf (V unit lower trapezoidal): Q_rows = [C; 0] - V (T (V_top^T C)).
+// One level of the thin-Q broadcast (Sec. 4.1): node (level, idx) holds its block C of
+// Q_tree [D; 0] (the root's is D) and hands child s the block of Q_node [C; 0; ...; 0]:
+// C - T C for s = 0 and -Y_s T C for s >= 1 (V = [I; Y_1; ...], Sec. 3.2).  The blocks live in
+// the node_r slots, which the factorization no longer needs.
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 1)
+    formq_tree_kernel(const Plan P, const Store st, int level) {
+  using E = typename Ar::E;
+  extern __shared__ char smem_raw[];
+  FormQSmem<E> f = carve_formq<E>(smem_raw, P);
+  const int tid = threadIdx.x;
+  const int np = P.np, n = P.n, ld = f.ld;
+  const int node = blockIdx.x;
+  const int tn = P.level_offset[level] + node - P.chains;
+  E* blocks = reinterpret_cast<E*>(st.node_r);
+  const E* Cn = blocks + (size_t)(P.level_offset[level] + node) * np * np;
+  for (int i = tid; i < np * np; i += kThreads) {
+    const int a = i / np, b = i % np;
+    if (level == P.depth) {
+      f.C[a * ld + b] = (a == b && a < n) ? Ar::from_f64(__ldcg(st.signs + a)) : Ar::zero();
+    } else {
+      const double v = __ldcg(reinterpret_cast<const double*>(Cn) + i);
+      f.C[a * ld + b] = *reinterpret_cast<const E*>(&v);
+    }
+  }
+  load_square(st.node_t + (size_t)tn * np * np, f.T, np, ld);
+  __syncthreads();
+  tri_mul<Ar>(f.T, ld, f.C, ld, f.M, ld, n, np, np, false);
+  __syncthreads();
+  const int first = node * P.arity;
+  const int q = min(P.arity, P.level_count[level - 1] - first);
+  for (int s = 0; s < q; ++s) {
+    E* out = blocks + (size_t)(P.level_offset[level - 1] + first + s) * np * np;
+    if (s == 0) {
+      for (int i = tid; i < np * np; i += kThreads) {
+        const int o = (i / np) * ld + i % np;
+        out[i] = Ar::sub(f.C[o], f.M[o]);
+      }
+    } else {
+      load_square(st.node_y + ((size_t)tn * (P.arity - 1) + (s - 1)) * np * np, f.X, np, ld);
+      __syncthreads();
+      for (int i = tid; i < np * np; i += kThreads) {
+        const int a = i / np, b = i % np;
+        E v = Ar::zero();
+        for (int p = a; p < n; ++p) Ar::fma_acc(v, f.X[a * ld + p], f.M[p * ld + b]);
+        out[i] = Ar::neg(Ar::add(v, Ar::zero()));
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Q rows of chain g, last leaf first.  chain step (V = [I; Y]): Q_rows = -Y M with M = T C,
+// then C -= M.  first leaf (V unit lower trapezoidal): Q_rows = [C; 0] - V (T (V_top^T C)).
+template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1)
     formq_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
                  int64_t ldq, int box_rows) {
+  using E = typename Ar::E;
   extern __shared__ char smem_raw[];
-  FormQSmem f = carve_formq(smem_raw, P);
+  FormQSmem<E> f = carve_formq<E>(smem_raw, P);
   const Tile& S = f.S;
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, h = P.h, ld = f.ld;
@@ -79,40 +147,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(f.bar, 1);
     fence_mbar_init();
   }
-  // C = D (signs of the root)
-  for (int i = tid; i < np * np; i += kThreads) {
-    const int a = i / np, b = i % np;
-    f.C[a * ld + b] = (a == b && a < n) ? __ldcg(st.signs + a) : 0.0;
+  // C = this chain's block of Q_tree [D; 0], left by the tree levels (or D without a tree)
+  {
+    const double* Cg = st.node_r + (size_t)g * np * np;
+    for (int i = tid; i < np * np; i += kThreads) {
+      const int a = i / np, b = i % np;
+      if (P.depth == 0) {
+        f.C[a * ld + b] = (a == b && a < n) ? Ar::from_f64(__ldcg(st.signs + a)) : Ar::zero();
+      } else {
+        const double v = __ldcg(Cg + i);
+        f.C[a * ld + b] = *reinterpret_cast<const E*>(&v);
+      }
+    }
   }
   __syncthreads();
   uint32_t phase = 0;
-
-  // ---- walk the tree from the root down to chain g, keeping only this chain's block
-  for (int lev = P.depth; lev >= 1; --lev) {
-    int idx = g;
-    for (int l = 0; l < lev - 1; ++l) idx /= P.arity;
-    const int s = idx % P.arity;  // position of the level-(lev-1) ancestor among its siblings
-    const int node = idx / P.arity;
-    const int tn = P.level_offset[lev] + node - P.chains;
-    load_square(st.node_t + (size_t)tn * np * np, f.T, np, ld);
-    __syncthreads();
-    tri_mul(f.T, ld, f.C, ld, f.M, ld, n, np, np, false);
-    __syncthreads();
-    if (s == 0) {
-      for (int i = tid; i < np * np; i += kThreads) f.C[(i / np) * ld + i % np] -= f.M[(i / np) * ld + i % np];
-    } else {
-      load_square(st.node_y + ((size_t)tn * (P.arity - 1) + (s - 1)) * np * np, f.X, np, ld);
-      __syncthreads();
-      // C = -Y_s M, Y_s upper triangular
-      for (int o = tid; o < np * np; o += kThreads) {
-        const int a = o / np, b = o % np;
-        double v = 0.0;
-        for (int p = a; p < n; ++p) v = fma(f.X[a * ld + p], f.M[p * ld + b], v);
-        f.C[a * ld + b] = -v;
-      }
-    }
-    __syncthreads();
-  }
 
   // ---- unwind the chain from its last leaf to its first
   const int64_t l0 = chain_first_leaf(P, g), l1 = chain_end_leaf(P, g);
@@ -125,38 +174,45 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!tile_load(S, &mapV, f.bar, phase, np, row0, h, 0, box_rows, st.status, f.flag)) return;
     const int64_t rows_valid = (P.m - row0 < h) ? (P.m - row0) : h;
     if (!plain) {
-      tri_mul(f.T, ld, f.C, ld, f.M, ld, n, np, np, false);
+      tri_mul<Ar>(f.T, ld, f.C, ld, f.M, ld, n, np, np, false);
       __syncthreads();
       if (cown < n) {
         for (int r = gown; r < rows_valid; r += G) {
-          double v = 0.0;
-          for (int a = 0; a < n; ++a) v = fma(S(r, a), f.M[a * ld + cown], v);
-          Q[(row0 + r) * ldq + cown] = -v;
+          E v = Ar::zero();
+          for (int a = 0; a < n; ++a) Ar::fma_acc(v, tat<E>(S, r, a), f.M[a * ld + cown]);
+          Q[(row0 + r) * ldq + cown] = -Ar::to_f64(Ar::add(v, Ar::zero()));
         }
       }
-      for (int i = tid; i < np * np; i += kThreads) f.C[(i / np) * ld + i % np] -= f.M[(i / np) * ld + i % np];
+      for (int i = tid; i < np * np; i += kThreads) {
+        const int o = (i / np) * ld + i % np;
+        f.C[o] = Ar::sub(f.C[o], f.M[o]);
+      }
       __syncthreads();
     } else {
       // X = V_top^T C, V_top unit lower triangular (rows 0..n-1 of the leaf)
       for (int o = tid; o < np * np; o += kThreads) {
         const int a = o / np, b = o % np;
-        double v = 0.0;
+        E v = Ar::zero();
         if (a < n) {
           v = f.C[a * ld + b];
-          for (int r = a + 1; r < n; ++r) v = fma(S(r, a), f.C[r * ld + b], v);
+          for (int r = a + 1; r < n; ++r) Ar::fma_acc(v, tat<E>(S, r, a), f.C[r * ld + b]);
+          v = Ar::add(v, Ar::zero());
         }
         f.X[a * ld + b] = v;
       }
       __syncthreads();
-      tri_mul(f.T, ld, f.X, ld, f.M, ld, n, np, np, false);
+      tri_mul<Ar>(f.T, ld, f.X, ld, f.M, ld, n, np, np, false);
       __syncthreads();
       if (cown < n) {
         for (int r = gown; r < rows_valid; r += G) {
-          double v = (r < n) ? f.C[r * ld + cown] : 0.0;
+          // v = [C; 0]_r - sum_a V[r][a] M[a] with V's unit diagonal
+          E acc = Ar::zero();
           const int amax = (r < n) ? r : n;
-          for (int a = 0; a < amax; ++a) v = fma(-S(r, a), f.M[a * ld + cown], v);
-          if (r < n) v -= f.M[r * ld + cown];  // unit diagonal of V
-          Q[(row0 + r) * ldq + cown] = v;
+          for (int a = 0; a < amax; ++a) Ar::fma_acc(acc, tat<E>(S, r, a), f.M[a * ld + cown]);
+          if (r < n) Ar::fma_acc(acc, Ar::from_int(1), f.M[r * ld + cown]);
+          E v = Ar::neg(Ar::add(acc, Ar::zero()));
+          if (r < n) v = Ar::add(v, f.C[r * ld + cown]);
+          Q[(row0 + r) * ldq + cown] = Ar::to_f64(v);
         }
       }
       __syncthreads();
@@ -164,39 +220,32 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,
-                          int box_rows, cudaStream_t stream) {
-  const size_t smem = formq_smem_bytes(P);
-  cudaError_t e = cudaFuncSetAttribute(formq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  formq_kernel<<<P.chains, kThreads, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
-  return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------------------------------
 // Q^T B and Q B on column blocks of kb columns (kb a power of two <= 32)
 
+template <class E>
 struct ApplySmem {
-  Tile S;      // leaf reflectors, h rows
-  double* B;   // max(h, arity*np) x kb
-  double* C;   // np x kb: the chain's top block
-  double* W;   // np x kb
-  double* W2;  // np x kb
-  double* T;   // np x (np+1)
-  double* Y;   // np x (np+1): one tree-node block
-  double* red; // kThreads
+  Tile S;   // leaf reflectors, h rows
+  E* B;     // max(h, arity*np) x kb
+  E* C;     // np x kb: the chain's top block
+  E* W;     // np x kb
+  E* W2;    // np x kb
+  E* T;     // np x (np+1)
+  E* Y;     // np x (np+1): one tree-node block
+  E* red;   // kThreads
   uint64_t* bar;
   int* flag;
   int ldt, brows;
 };
 
-__device__ inline ApplySmem carve_apply(char* raw, const Plan& P, int kb) {
-  ApplySmem f;
+template <class E>
+__device__ inline ApplySmem<E> carve_apply(char* raw, const Plan& P, int kb) {
+  ApplySmem<E> f;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   f.S = Tile{base, P.h};
   f.brows = max(P.h, P.arity * P.np);
   f.ldt = P.np + 1;
-  f.B = reinterpret_cast<double*>(base + (size_t)P.h * P.np * 8);
+  f.B = reinterpret_cast<E*>(base + (size_t)P.h * P.np * 8);
   f.C = f.B + (size_t)f.brows * kb;
   f.W = f.C + P.np * kb;
   f.W2 = f.W + P.np * kb;
@@ -214,38 +263,40 @@ size_t apply_smem_bytes(const Plan& P, int kb) {
          kThreads * 8 + 8 + 16;
 }
 
-// W (np x kb) = Vsum, with the row sum split over thread groups when there are few outputs:
+// W (np x kb), with the row sum split over thread groups when there are few outputs:
 //   plain : W[a][b] = B[a][b] + sum_{r=a+1}^{h-1} V[r][a] B[r][b]       (V unit lower trapezoidal)
 //   chain : W[a][b] = C[a][b] + sum_{r=0}^{h-1}   Y[r][a] B[r][b]
-__device__ inline void wy_inner(const Tile& S, bool plain, int h, int n, int np, const double* B, const double* C,
-                                double* W, int kb, double* red) {
+template <class Ar>
+__device__ inline void wy_inner(const Tile& S, bool plain, int h, int n, int np, const typename Ar::E* B,
+                                const typename Ar::E* C, typename Ar::E* W, int kb, typename Ar::E* red) {
+  using E = typename Ar::E;
   const int OUT = np * kb;
   const int G = OUT >= kThreads ? 1 : kThreads / OUT;
   const int tid = threadIdx.x;
   for (int o0 = 0; o0 < OUT; o0 += kThreads / G) {
     const int o = o0 + tid % (kThreads / G);
     const int gg = tid / (kThreads / G);
-    double acc = 0.0;
+    E acc = Ar::zero();
     if (o < OUT) {
       const int a = o / kb, b = o % kb;
       if (a < n) {
         const int r0 = plain ? a + 1 : 0;
-        for (int r = r0 + gg; r < h; r += G) acc = fma(S(r, a), B[r * kb + b], acc);
+        for (int r = r0 + gg; r < h; r += G) Ar::fma_acc(acc, tat<E>(S, r, a), B[r * kb + b]);
       }
     }
     if (G == 1) {
       if (o < OUT) {
         const int a = o / kb, b = o % kb;
-        W[o] = (a < n) ? acc + (plain ? B[a * kb + b] : C[a * kb + b]) : 0.0;
+        W[o] = (a < n) ? Ar::add(acc, plain ? B[a * kb + b] : C[a * kb + b]) : Ar::zero();
       }
     } else {
       red[tid] = acc;
       __syncthreads();
       if (gg == 0 && o < OUT) {
-        double s = 0.0;
-        for (int q = 0; q < G; ++q) s += red[q * (kThreads / G) + tid];
+        E s = Ar::zero();
+        for (int q = 0; q < G; ++q) s = Ar::add(s, red[q * (kThreads / G) + tid]);
         const int a = o / kb, b = o % kb;
-        W[o] = (a < n) ? s + (plain ? B[a * kb + b] : C[a * kb + b]) : 0.0;
+        W[o] = (a < n) ? Ar::add(s, plain ? B[a * kb + b] : C[a * kb + b]) : Ar::zero();
       }
       __syncthreads();
     }
@@ -253,40 +304,47 @@ __device__ inline void wy_inner(const Tile& S, bool plain, int h, int n, int np,
 }
 
 // B -= V W2 (rows 0..h-1); plain: V unit lower trapezoidal; chain: V = [I; Y] so C -= W2 too.
-__device__ inline void wy_update(const Tile& S, bool plain, int h, int n, int np, double* B, double* C,
-                                 const double* W2, int kb) {
+template <class Ar>
+__device__ inline void wy_update(const Tile& S, bool plain, int h, int n, int np, typename Ar::E* B,
+                                 typename Ar::E* C, const typename Ar::E* W2, int kb) {
+  using E = typename Ar::E;
   for (int o = threadIdx.x; o < h * kb; o += kThreads) {
     const int r = o / kb, b = o % kb;
-    double v = B[o];
+    E acc = Ar::zero();
     const int amax = plain ? (r < n ? r : n) : n;
-    for (int a = 0; a < amax; ++a) v = fma(-S(r, a), W2[a * kb + b], v);
-    if (plain && r < n) v -= W2[r * kb + b];
-    B[o] = v;
+    for (int a = 0; a < amax; ++a) Ar::fma_acc(acc, tat<E>(S, r, a), W2[a * kb + b]);
+    if (plain && r < n) Ar::fma_acc(acc, Ar::from_int(1), W2[r * kb + b]);
+    B[o] = Ar::sub(B[o], Ar::add(acc, Ar::zero()));
   }
   if (!plain)
-    for (int o = threadIdx.x; o < np * kb; o += kThreads) C[o] -= W2[o];
+    for (int o = threadIdx.x; o < np * kb; o += kThreads) C[o] = Ar::sub(C[o], W2[o]);
 }
 
+template <class Ar>
 __device__ inline void load_b(const double* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k, int64_t row0,
-                              int rows, int64_t col0, int kb, double* Bs) {
+                              int rows, int64_t col0, int kb, typename Ar::E* Bs) {
   for (int o = threadIdx.x; o < rows * kb; o += kThreads) {
     const int r = o / kb, b = o % kb;
     const int64_t gr = row0 + r, gc = col0 + b;
-    Bs[o] = (gr < m && gc < k) ? __ldcg(Bg + gr * ldb + gc) : 0.0;
+    Bs[o] = Ar::from_f64((gr < m && gc < k) ? __ldcg(Bg + gr * ldb + gc) : 0.0);
   }
 }
+template <class Ar>
 __device__ inline void store_b(double* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k, int64_t row0, int r_begin,
-                               int rows, int64_t col0, int kb, const double* Bs) {
+                               int rows, int64_t col0, int kb, const typename Ar::E* Bs) {
   for (int o = threadIdx.x; o < (rows - r_begin) * kb; o += kThreads) {
     const int r = r_begin + o / kb, b = o % kb;
     const int64_t gr = row0 + r, gc = col0 + b;
-    if (gr < m && gc < k) Bg[gr * ldb + gc] = Bs[r * kb + b];
+    if (gr < m && gc < k) Bg[gr * ldb + gc] = Ar::to_f64(Bs[r * kb + b]);
   }
 }
 
-// Tree-node step on the stacked top blocks of the q children (child s's block at Bs rows
+// Tree-node step on the stacked top blocks of the q children (child s's block at B rows
 // s*np..s*np+n-1): D = C0 + sum_s Y_s^T C_s; W2 = T^T D (trans) or T D; C0 -= W2; C_s -= Y_s W2.
-__device__ inline void node_apply(ApplySmem& f, const Plan& P, const Store& st, int tn, int q, int kb, bool trans) {
+template <class Ar>
+__device__ inline void node_apply(ApplySmem<typename Ar::E>& f, const Plan& P, const Store& st, int tn, int q, int kb,
+                                  bool trans) {
+  using E = typename Ar::E;
   const int np = P.np, n = P.n, ld = f.ldt, tid = threadIdx.x;
   load_square(st.node_t + (size_t)tn * np * np, f.T, np, ld);
   for (int o = tid; o < np * kb; o += kThreads) f.W[o] = f.B[o];
@@ -294,27 +352,27 @@ __device__ inline void node_apply(ApplySmem& f, const Plan& P, const Store& st, 
   for (int s = 1; s < q; ++s) {
     load_square(st.node_y + ((size_t)tn * (P.arity - 1) + (s - 1)) * np * np, f.Y, np, ld);
     __syncthreads();
-    const double* Cs = f.B + (size_t)s * np * kb;
+    const E* Cs = f.B + (size_t)s * np * kb;
     for (int o = tid; o < np * kb; o += kThreads) {
       const int a = o / kb, b = o % kb;
-      double v = f.W[o];
-      for (int r = 0; r <= a && r < n; ++r) v = fma(f.Y[r * ld + a], Cs[r * kb + b], v);
-      f.W[o] = v;
+      E v = f.W[o];
+      for (int r = 0; r <= a && r < n; ++r) Ar::fma_acc(v, f.Y[r * ld + a], Cs[r * kb + b]);
+      f.W[o] = Ar::add(v, Ar::zero());
     }
     __syncthreads();
   }
-  tri_mul(f.T, ld, f.W, kb, f.W2, kb, n, np, kb, trans);
+  tri_mul<Ar>(f.T, ld, f.W, kb, f.W2, kb, n, np, kb, trans);
   __syncthreads();
-  for (int o = tid; o < np * kb; o += kThreads) f.B[o] -= f.W2[o];
+  for (int o = tid; o < np * kb; o += kThreads) f.B[o] = Ar::sub(f.B[o], f.W2[o]);
   for (int s = 1; s < q; ++s) {
     load_square(st.node_y + ((size_t)tn * (P.arity - 1) + (s - 1)) * np * np, f.Y, np, ld);
     __syncthreads();
-    double* Cs = f.B + (size_t)s * np * kb;
+    E* Cs = f.B + (size_t)s * np * kb;
     for (int o = tid; o < np * kb; o += kThreads) {
       const int a = o / kb, b = o % kb;
-      double v = Cs[o];
-      for (int p = a; p < n; ++p) v = fma(-f.Y[a * ld + p], f.W2[p * kb + b], v);
-      Cs[o] = v;
+      E acc = Ar::zero();
+      for (int p = a; p < n; ++p) Ar::fma_acc(acc, f.Y[a * ld + p], f.W2[p * kb + b]);
+      Cs[o] = Ar::sub(Cs[o], Ar::add(acc, Ar::zero()));
     }
     __syncthreads();
   }
@@ -330,11 +388,13 @@ __device__ inline int64_t node_top_row(const Plan& P, int level, int idx) {
 }
 
 // ---- Q^T B: chains leaves-first, then the tree bottom-up by last arrival, then D on the top.
+template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1)
     apply_qt_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, int64_t k,
                     double* __restrict__ Bg, int64_t ldb, int kb, int box_rows) {
+  using E = typename Ar::E;
   extern __shared__ char smem_raw[];
-  ApplySmem f = carve_apply(smem_raw, P, kb);
+  ApplySmem<E> f = carve_apply<E>(smem_raw, P, kb);
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, h = P.h;
   const int g = blockIdx.x, cb = blockIdx.y;
@@ -350,24 +410,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool plain = (leaf == l0);
     const int64_t row0 = leaf * h;
     load_square(st.t_leaf + leaf * np * np, f.T, np, f.ldt);
-    load_b(Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
+    load_b<Ar>(Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
     if (!tile_load(f.S, &mapV, f.bar, phase, np, row0, h, 0, box_rows, st.status, f.flag)) return;
-    wy_inner(f.S, plain, h, n, np, f.B, f.C, f.W, kb, f.red);
+    wy_inner<Ar>(f.S, plain, h, n, np, f.B, f.C, f.W, kb, f.red);
     __syncthreads();
-    tri_mul(f.T, f.ldt, f.W, kb, f.W2, kb, n, np, kb, true);
+    tri_mul<Ar>(f.T, f.ldt, f.W, kb, f.W2, kb, n, np, kb, true);
     __syncthreads();
-    wy_update(f.S, plain, h, n, np, f.B, f.C, f.W2, kb);
+    wy_update<Ar>(f.S, plain, h, n, np, f.B, f.C, f.W2, kb);
     __syncthreads();
     if (plain) {  // rows 0..n-1 become the chain's top block
-      for (int o = tid; o < np * kb; o += kThreads) f.C[o] = (o / kb < n) ? f.B[o] : 0.0;
-      store_b(Bg, ldb, P.m, k, row0, n, h, col0, kb, f.B);
+      for (int o = tid; o < np * kb; o += kThreads) f.C[o] = (o / kb < n) ? f.B[o] : Ar::zero();
+      store_b<Ar>(Bg, ldb, P.m, k, row0, n, h, col0, kb, f.B);
     } else {
-      store_b(Bg, ldb, P.m, k, row0, 0, h, col0, kb, f.B);
+      store_b<Ar>(Bg, ldb, P.m, k, row0, 0, h, col0, kb, f.B);
     }
     __syncthreads();
   }
   // publish the chain's top block
-  store_b(Bg, ldb, P.m, k, chain_top_row(P, g), 0, n, col0, kb, f.C);
+  store_b<Ar>(Bg, ldb, P.m, k, chain_top_row(P, g), 0, n, col0, kb, f.C);
   int idx = g;
   for (int level = 0; level < P.depth; ++level) {
     const int parent = idx / P.arity;
@@ -388,31 +448,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int o = tid; o < np * kb; o += kThreads) {
         const int a = o / kb, b = o % kb;
         const int64_t gc = col0 + b;
-        f.B[(size_t)s * np * kb + o] = (a < n && gc < k) ? __ldcg(Bg + (top + a) * ldb + gc) : 0.0;
+        f.B[(size_t)s * np * kb + o] = Ar::from_f64((a < n && gc < k) ? __ldcg(Bg + (top + a) * ldb + gc) : 0.0);
       }
     }
     __syncthreads();
-    node_apply(f, P, st, tn, q, kb, true);
+    node_apply<Ar>(f, P, st, tn, q, kb, true);
     __syncthreads();
     for (int s = 0; s < q; ++s)
-      store_b(Bg, ldb, P.m, k, node_top_row(P, level, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
+      store_b<Ar>(Bg, ldb, P.m, k, node_top_row(P, level, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
     idx = parent;
   }
   // root: the thin part gets the signs (the top block is C without a tree, else child 0's)
   __syncthreads();
-  const double* topblk = (P.depth == 0) ? f.C : f.B;
+  const E* topblk = (P.depth == 0) ? f.C : f.B;
   for (int o = tid; o < n * kb; o += kThreads) {
     const int a = o / kb, b = o % kb;
-    if (col0 + b < k) Bg[(int64_t)a * ldb + col0 + b] = __ldcg(st.signs + a) * topblk[o];
+    if (col0 + b < k) Bg[(int64_t)a * ldb + col0 + b] = __ldcg(st.signs + a) * Ar::to_f64(topblk[o]);
   }
 }
 
 // ---- Q B, tree part: one launch per level, top-down; the root level first applies D.
+template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1)
     apply_q_tree_kernel(const Plan P, const Store st, int level, int64_t k, double* __restrict__ Bg, int64_t ldb,
                         int kb) {
+  using E = typename Ar::E;
   extern __shared__ char smem_raw[];
-  ApplySmem f = carve_apply(smem_raw, P, kb);
+  ApplySmem<E> f = carve_apply<E>(smem_raw, P, kb);
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n;
   const int node = blockIdx.x, cb = blockIdx.y;
@@ -427,22 +489,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t gc = col0 + b;
       double v = (a < n && gc < k) ? Bg[(top + a) * ldb + gc] : 0.0;
       if (level == P.depth && s == 0 && a < n) v *= st.signs[a];
-      f.B[(size_t)s * np * kb + o] = v;
+      f.B[(size_t)s * np * kb + o] = Ar::from_f64(v);
     }
   }
   __syncthreads();
-  node_apply(f, P, st, tn, q, kb, false);
+  node_apply<Ar>(f, P, st, tn, q, kb, false);
   __syncthreads();
   for (int s = 0; s < q; ++s)
-    store_b(Bg, ldb, P.m, k, node_top_row(P, level - 1, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
+    store_b<Ar>(Bg, ldb, P.m, k, node_top_row(P, level - 1, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
 }
 
 // ---- Q B, chains: last leaf first, the first leaf last.
+template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1)
     apply_q_chain_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, int64_t k,
                          double* __restrict__ Bg, int64_t ldb, int kb, int box_rows) {
+  using E = typename Ar::E;
   extern __shared__ char smem_raw[];
-  ApplySmem f = carve_apply(smem_raw, P, kb);
+  ApplySmem<E> f = carve_apply<E>(smem_raw, P, kb);
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, h = P.h;
   const int g = blockIdx.x, cb = blockIdx.y;
@@ -457,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t gc = col0 + b;
     double v = (a < n && gc < k) ? Bg[(top + a) * ldb + gc] : 0.0;
     if (P.depth == 0 && a < n) v *= st.signs[a];
-    f.C[o] = v;
+    f.C[o] = Ar::from_f64(v);
   }
   __syncthreads();
   uint32_t phase = 0;
@@ -466,18 +530,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool plain = (leaf == l0);
     const int64_t row0 = leaf * h;
     load_square(st.t_leaf + leaf * np * np, f.T, np, f.ldt);
-    load_b(Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
+    load_b<Ar>(Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
     if (!tile_load(f.S, &mapV, f.bar, phase, np, row0, h, 0, box_rows, st.status, f.flag)) return;
     if (plain)
       for (int o = tid; o < n * kb; o += kThreads) f.B[o] = f.C[o];
     __syncthreads();
-    wy_inner(f.S, plain, h, n, np, f.B, f.C, f.W, kb, f.red);
+    wy_inner<Ar>(f.S, plain, h, n, np, f.B, f.C, f.W, kb, f.red);
     __syncthreads();
-    tri_mul(f.T, f.ldt, f.W, kb, f.W2, kb, n, np, kb, false);
+    tri_mul<Ar>(f.T, f.ldt, f.W, kb, f.W2, kb, n, np, kb, false);
     __syncthreads();
-    wy_update(f.S, plain, h, n, np, f.B, f.C, f.W2, kb);
+    wy_update<Ar>(f.S, plain, h, n, np, f.B, f.C, f.W2, kb);
     __syncthreads();
-    store_b(Bg, ldb, P.m, k, row0, 0, h, col0, kb, f.B);
+    store_b<Ar>(Bg, ldb, P.m, k, row0, 0, h, col0, kb, f.B);
     __syncthreads();
   }
 }
@@ -488,11 +552,35 @@ static int pick_kb(int64_t k) {
   return kb;
 }
 
-cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
-                            int64_t ldb, int box_rows, cudaStream_t stream) {
+template <class Ar>
+static cudaError_t launch_form_q_t(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,
+                                   int box_rows, cudaStream_t stream) {
+  const size_t smem = formq_smem_bytes(P);
+  cudaError_t e = cudaFuncSetAttribute(formq_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(formq_tree_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int level = P.depth; level >= 1; --level) {
+    formq_tree_kernel<Ar><<<P.level_count[level], kThreads, smem, stream>>>(P, st, level);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  formq_kernel<Ar><<<P.chains, kThreads, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,
+                          int box_rows, cudaStream_t stream) {
+  if (P.precision == 1) return launch_form_q_t<ArithDF>(mapV, P, st, Q, ldq, box_rows, stream);
+  return launch_form_q_t<ArithF64>(mapV, P, st, Q, ldq, box_rows, stream);
+}
+
+template <class Ar>
+static cudaError_t launch_apply_qt_t(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+                                     int64_t ldb, int box_rows, cudaStream_t stream) {
   const int kb = pick_kb(k);
   const size_t smem = apply_smem_bytes(P, kb);
-  cudaError_t e = cudaFuncSetAttribute(apply_qt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(apply_qt_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   for (int64_t c0 = 0; c0 < k; c0 += (int64_t)kb * kMaxColBlocks) {
     const int64_t kc = (k - c0 < (int64_t)kb * kMaxColBlocks) ? (k - c0) : (int64_t)kb * kMaxColBlocks;
@@ -500,7 +588,40 @@ cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store&
     e = cudaMemsetAsync(st.counters, 0, sizeof(int) * (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1) * kMaxColBlocks,
                         stream);
     if (e != cudaSuccess) return e;
-    apply_qt_kernel<<<dim3(P.chains, ncb), kThreads, smem, stream>>>(mapV, P, st, kc, B + c0, ldb, kb, box_rows);
+    apply_qt_kernel<Ar><<<dim3(P.chains, ncb), kThreads, smem, stream>>>(mapV, P, st, kc, B + c0, ldb, kb, box_rows);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+                            int64_t ldb, int box_rows, cudaStream_t stream) {
+  if (P.precision == 1) return launch_apply_qt_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
+  return launch_apply_qt_t<ArithF64>(mapV, P, st, k, B, ldb, box_rows, stream);
+}
+
+template <class Ar>
+static cudaError_t launch_apply_q_t(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+                                    int64_t ldb, int box_rows, cudaStream_t stream) {
+  const int kb = pick_kb(k);
+  const size_t smem = apply_smem_bytes(P, kb);
+  cudaError_t e =
+      cudaFuncSetAttribute(apply_q_tree_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(apply_q_chain_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t c0 = 0; c0 < k; c0 += (int64_t)kb * kMaxColBlocks) {
+    const int64_t kc = (k - c0 < (int64_t)kb * kMaxColBlocks) ? (k - c0) : (int64_t)kb * kMaxColBlocks;
+    const int ncb = (int)((kc + kb - 1) / kb);
+    for (int level = P.depth; level >= 1; --level) {
+      apply_q_tree_kernel<Ar><<<dim3(P.level_count[level], ncb), kThreads, smem, stream>>>(P, st, level, kc, B + c0,
+                                                                                            ldb, kb);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    apply_q_chain_kernel<Ar><<<dim3(P.chains, ncb), kThreads, smem, stream>>>(mapV, P, st, kc, B + c0, ldb, kb,
+                                                                               box_rows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -509,26 +630,8 @@ cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store&
 
 cudaError_t launch_apply_q(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
                            int64_t ldb, int box_rows, cudaStream_t stream) {
-  const int kb = pick_kb(k);
-  const size_t smem = apply_smem_bytes(P, kb);
-  cudaError_t e = cudaFuncSetAttribute(apply_q_tree_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(apply_q_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  for (int64_t c0 = 0; c0 < k; c0 += (int64_t)kb * kMaxColBlocks) {
-    const int64_t kc = (k - c0 < (int64_t)kb * kMaxColBlocks) ? (k - c0) : (int64_t)kb * kMaxColBlocks;
-    const int ncb = (int)((kc + kb - 1) / kb);
-    for (int level = P.depth; level >= 1; --level) {
-      apply_q_tree_kernel<<<dim3(P.level_count[level], ncb), kThreads, smem, stream>>>(P, st, level, kc, B + c0, ldb,
-                                                                                        kb);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-    }
-    apply_q_chain_kernel<<<dim3(P.chains, ncb), kThreads, smem, stream>>>(mapV, P, st, kc, B + c0, ldb, kb, box_rows);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  if (P.precision == 1) return launch_apply_q_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
+  return launch_apply_q_t<ArithF64>(mapV, P, st, k, B, ldb, box_rows, stream);
 }
 
 }  // namespace tsqr

@@ -32,7 +32,8 @@ struct Plan {
   int level_count[kMaxLevels + 1];
   int level_offset[kMaxLevels + 1];
   int total_nodes, tree_nodes;
-  int rows_cap;  // rows of the factor kernel's shared tile
+  int rows_cap;   // rows of the factor kernel's shared tile
+  int precision;  // 0: native FP64 arithmetic; 1: double-float (FP32 pairs), FP64 in and out
 };
 
 __host__ __device__ inline int64_t chain_first_leaf(const Plan& p, int g) { return (int64_t)g * p.chain; }

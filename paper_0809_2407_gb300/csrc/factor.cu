@@ -16,18 +16,20 @@
 
 namespace tsqr {
 
+template <class E>
 struct FactorSmem {
   Tile S;
-  double *T_s, *red, *dvec, *sc, *tau_s;
+  E *T_s, *red, *dvec, *sc, *tau_s;
   uint64_t* bar;
   int* flag;
 };
 
-__device__ inline FactorSmem carve_factor(char* raw, const Plan& P) {
-  FactorSmem f;
+template <class E>
+__device__ inline FactorSmem<E> carve_factor(char* raw, const Plan& P) {
+  FactorSmem<E> f;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   f.S = Tile{base, P.rows_cap};
-  f.T_s = reinterpret_cast<double*>(base + (size_t)P.rows_cap * P.np * 8);
+  f.T_s = reinterpret_cast<E*>(base + (size_t)P.rows_cap * P.np * 8);
   f.red = f.T_s + tri_size(P.np);
   f.dvec = f.red + kThreads;
   f.sc = f.dvec + P.np;
@@ -42,15 +44,33 @@ size_t factor_smem_bytes(const Plan& P) {
          P.np * 8 + 8 + 16;
 }
 
+// Rows [r0, r0 + rows) of the tile arrive from TMA as FP64; in double-float mode they are split
+// into (hi, lo) pairs in place.
+template <class Ar>
+__device__ inline void convert_rows_in(const Tile& S, int r0, int rows, int np) {
+  if constexpr (Ar::kPrecision != 0) {
+    for (int i = threadIdx.x; i < rows * np; i += kThreads) {
+      double* p = S.ptr(r0 + i / np, i % np);
+      *reinterpret_cast<typename Ar::E*>(p) = Ar::from_f64(*p);
+    }
+    __syncthreads();
+  }
+}
+
+template <class Ar>
 __global__ void __launch_bounds__(kThreads, 2)
     factor_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, const Plan P,
                   const Store st, double* __restrict__ R_out, int64_t ldr, int box_rows) {
+  using E = typename Ar::E;
   extern __shared__ char smem_raw[];
-  FactorSmem f = carve_factor(smem_raw, P);
+  FactorSmem<E> f = carve_factor<E>(smem_raw, P);
   const Tile& S = f.S;
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, h = P.h;
   const int g = blockIdx.x;
+  E* tau_leaf = reinterpret_cast<E*>(st.tau_leaf);
+  E* t_leaf = reinterpret_cast<E*>(st.t_leaf);
+  E* node_r = reinterpret_cast<E*>(st.node_r);
   if (tid == 0) {
     mbar_init(f.bar, 1);
     fence_mbar_init();
@@ -68,20 +88,21 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (tid == 0) tma_store_wait_all();
       return;
     }
-    stacked_qr(S, plain ? PLAIN : CHAIN, dst + h, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
+    convert_rows_in<Ar>(S, dst, h, np);
+    stacked_qr<Ar>(S, plain ? PLAIN : CHAIN, dst + h, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
     tile_store(S, &mapV, np, row0, h, dst, box_rows);
-    double* tau_g = st.tau_leaf + leaf * np;
-    double* T_g = st.t_leaf + leaf * np * np;
+    E* tau_g = tau_leaf + leaf * np;
+    E* T_g = t_leaf + leaf * np * np;
     for (int i = tid; i < np; i += kThreads) tau_g[i] = f.tau_s[i];
     for (int i = tid; i < np * np; i += kThreads) {
       const int a = i / np, b = i % np;
-      T_g[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : 0.0;
+      T_g[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
     }
     tile_store_drain();
     if (plain) {  // rows 0..np-1 now carry R above the diagonal; clear the reflector part below
       for (int i = tid; i < np * np; i += kThreads) {
         const int r = i / np, c = i % np;
-        if (c < r) S(r, c) = 0.0;
+        if (c < r) at<E>(S, r, c) = Ar::zero();
       }
       __syncthreads();
     }
@@ -90,10 +111,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   // ---- publish the chain's R (level-0 node g); the reflector stores are complete first
   if (tid == 0) tma_store_wait_all();
   {
-    double* Rg = st.node_r + (size_t)g * np * np;
+    E* Rg = node_r + (size_t)g * np * np;
     for (int i = tid; i < np * np; i += kThreads) {
       const int r = i / np, c = i % np;
-      Rg[i] = (c >= r) ? S(r, c) : 0.0;
+      Rg[i] = (c >= r) ? at<E>(S, r, c) : Ar::zero();
     }
   }
 
@@ -117,51 +138,58 @@ __global__ void __launch_bounds__(kThreads, 2)
     // stack the children's R factors in child order: child s at rows s*np..s*np+np-1
     for (int s = 0; s < q; ++s) {
       const double* Rc = st.node_r + (size_t)(P.level_offset[level] + first + s) * np * np;
-      for (int i = tid; i < np * np; i += kThreads) S(s * np + i / np, i % np) = __ldcg(Rc + i);
+      for (int i = tid; i < np * np; i += kThreads) *S.ptr(s * np + i / np, i % np) = __ldcg(Rc + i);
     }
     __syncthreads();
-    stacked_qr(S, NODE, q * np, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
-    double* Y = st.node_y + (size_t)tn * (P.arity - 1) * np * np;
+    stacked_qr<Ar>(S, NODE, q * np, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
+    E* Y = reinterpret_cast<E*>(st.node_y) + (size_t)tn * (P.arity - 1) * np * np;
     for (int s = 1; s < P.arity; ++s) {
-      double* Ys = Y + (size_t)(s - 1) * np * np;
+      E* Ys = Y + (size_t)(s - 1) * np * np;
       for (int i = tid; i < np * np; i += kThreads) {
         const int r = i / np, c = i % np;
-        Ys[i] = (s < q && c >= r) ? S(s * np + r, c) : 0.0;
+        Ys[i] = (s < q && c >= r) ? at<E>(S, s * np + r, c) : Ar::zero();
       }
     }
-    for (int i = tid; i < np; i += kThreads) st.node_tau[(size_t)tn * np + i] = f.tau_s[i];
-    double* Tn = st.node_t + (size_t)tn * np * np;
+    for (int i = tid; i < np; i += kThreads) reinterpret_cast<E*>(st.node_tau)[(size_t)tn * np + i] = f.tau_s[i];
+    E* Tn = reinterpret_cast<E*>(st.node_t) + (size_t)tn * np * np;
     for (int i = tid; i < np * np; i += kThreads) {
       const int a = i / np, b = i % np;
-      Tn[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : 0.0;
+      Tn[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
     }
-    double* Rp = st.node_r + (size_t)pid * np * np;
+    E* Rp = node_r + (size_t)pid * np * np;
     for (int i = tid; i < np * np; i += kThreads) {
       const int r = i / np, c = i % np;
-      Rp[i] = (c >= r) ? S(r, c) : 0.0;
+      Rp[i] = (c >= r) ? at<E>(S, r, c) : Ar::zero();
     }
     idx = parent;
   }
 
   // ---- root: R <- D R with D = diag(sign(R_jj)), sign(0) = +1
   __syncthreads();
-  for (int j = tid; j < np; j += kThreads) st.signs[j] = (j < n && S(j, j) < 0.0) ? -1.0 : 1.0;
+  for (int j = tid; j < np; j += kThreads) st.signs[j] = (j < n && Ar::is_neg(at<E>(S, j, j))) ? -1.0 : 1.0;
   for (int i = tid; i < n * n; i += kThreads) {
     const int r = i / n, c = i % n;
-    const double d = (S(r, r) < 0.0) ? -1.0 : 1.0;
-    R_out[(int64_t)r * ldr + c] = (c >= r) ? d * S(r, c) : 0.0;
+    const double d = Ar::is_neg(at<E>(S, r, r)) ? -1.0 : 1.0;
+    R_out[(int64_t)r * ldr + c] = (c >= r) ? d * Ar::to_f64(at<E>(S, r, c)) : 0.0;
   }
+}
+
+template <class Ar>
+static cudaError_t launch_factor_t(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
+                                   double* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
+  const size_t smem = factor_smem_bytes(P);
+  cudaError_t e = cudaFuncSetAttribute(factor_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(st.counters, 0, sizeof(int) * (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1), stream);
+  if (e != cudaSuccess) return e;
+  factor_kernel<Ar><<<P.chains, kThreads, smem, stream>>>(mapA, mapV, P, st, R_out, ldr, box_rows);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                           double* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
-  const size_t smem = factor_smem_bytes(P);
-  cudaError_t e = cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(st.counters, 0, sizeof(int) * (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1), stream);
-  if (e != cudaSuccess) return e;
-  factor_kernel<<<P.chains, kThreads, smem, stream>>>(mapA, mapV, P, st, R_out, ldr, box_rows);
-  return cudaGetLastError();
+  if (P.precision == 1) return launch_factor_t<ArithDF>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
+  return launch_factor_t<ArithF64>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
 }
 
 }  // namespace tsqr

@@ -96,11 +96,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool plain = (leaf == l0);
     const int dst = plain ? 0 : np;
     if (!tile_load(S, &mapA, bar, phase, np, leaf * h, h, dst, box_rows, status, flag)) return;
-    stacked_qr(S, plain ? PLAIN : CHAIN, dst + h, np, n, tau_s, nullptr, red, dvec, sc);
+    stacked_qr<ArithF64>(S, plain ? PLAIN : CHAIN, dst + h, np, n, tau_s, nullptr, red, dvec, sc);
     if (plain) {
       for (int i = tid; i < np * np; i += kThreads) {
         const int r = i / np, c = i % np;
-        if (c < r) S(r, c) = 0.0;
+        if (c < r) *S.ptr(r, c) = 0.0;
       }
     }
     __syncthreads();
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   double* Rg = node_r + (size_t)g * np * np;
   for (int i = tid; i < np * np; i += kThreads) {
     const int r = i / np, c = i % np;
-    Rg[i] = (c >= r) ? S(r, c) : 0.0;
+    Rg[i] = (c >= r) ? *S.ptr(r, c) : 0.0;
   }
   int idx = g;
   for (int level = 0; level < P.depth; ++level) {
@@ -127,22 +127,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (*flag == 0) return;
     for (int s = 0; s < q; ++s) {
       const double* Rc = node_r + (size_t)(P.level_offset[level] + first + s) * np * np;
-      for (int i = tid; i < np * np; i += kThreads) S(s * np + i / np, i % np) = __ldcg(Rc + i);
+      for (int i = tid; i < np * np; i += kThreads) *S.ptr(s * np + i / np, i % np) = __ldcg(Rc + i);
     }
     __syncthreads();
-    stacked_qr(S, NODE, q * np, np, n, tau_s, nullptr, red, dvec, sc);
+    stacked_qr<ArithF64>(S, NODE, q * np, np, n, tau_s, nullptr, red, dvec, sc);
     double* Rp = node_r + (size_t)pid * np * np;
     for (int i = tid; i < np * np; i += kThreads) {
       const int r = i / np, c = i % np;
-      Rp[i] = (c >= r) ? S(r, c) : 0.0;
+      Rp[i] = (c >= r) ? *S.ptr(r, c) : 0.0;
     }
     idx = parent;
   }
   __syncthreads();
   for (int i = tid; i < n * n; i += kThreads) {
     const int r = i / n, c = i % n;
-    const double d = (S(r, r) < 0.0) ? -1.0 : 1.0;
-    R_out[(int64_t)r * ldr + c] = (c >= r) ? d * S(r, c) : 0.0;
+    const double d = (*S.ptr(r, r) < 0.0) ? -1.0 : 1.0;
+    R_out[(int64_t)r * ldr + c] = (c >= r) ? d * *S.ptr(r, c) : 0.0;
   }
 }
 

@@ -1,5 +1,6 @@
-// Householder QR of a stacked matrix held in a shared-memory Tile, in FP64, by one thread
-// block.  One routine serves the three shapes TSQR factors (Kind in common.cuh):
+// Householder QR of a stacked matrix held in a shared-memory Tile, by one thread block, in the
+// arithmetic of policy Ar (arith.cuh).  One routine serves the three shapes TSQR factors
+// (Kind in common.cuh):
 //   PLAIN  a leaf block A_i                          (Algorithm 1, first step)
 //   CHAIN  [R; A_k], triangle atop a full block      (Algorithm 2, loop body; Sec. 3.1)
 //   NODE   [R_0; R_1; ...; R_{q-1}], q triangles      (Algorithm 1, tree step; eq. fact_2rs)
@@ -15,9 +16,15 @@
 // pattern.
 #pragma once
 
+#include "arith.cuh"
 #include "common.cuh"
 
 namespace tsqr {
+
+template <class E>
+__device__ __forceinline__ E& at(const Tile& S, int r, int c) {
+  return *reinterpret_cast<E*>(S.ptr(r, c));
+}
 
 // Rows of column j's reflector other than the pivot row j start at r_lo; NODE skips rows whose
 // position inside their triangle is below the diagonal.
@@ -27,24 +34,28 @@ __device__ __forceinline__ bool skip_row(int kind, int r, int j, int np) {
 }
 
 // Reflector of column j (x = S(j, j) and the column's rows >= r_lo), written to sc[]:
-//   sc[0] = beta (new S(j, j)), sc[1] = tau, sc[2] = 1/(alpha - beta), sc[3] = 1 if H != I.
+//   sc[0] = beta (new S(j, j)), sc[1] = tau, sc[2] = 1/(alpha - beta), sc[3] != 0 if H != I.
 // beta = -sign(alpha) ||x||, sign(0) = +1; tau = (beta - alpha)/beta; tau = 0 when the rows
-// below the pivot are all zero.  ||x|| is taken from the plain sum of squares unless that sum
-// leaves [2^-900, 2^900], in which case it is recomputed with every entry scaled by the
-// largest magnitude.  Warp 0 computes; ends with a block barrier.
-__device__ inline void make_reflector(const Tile& S, int kind, int N, int np, int j, double* sc) {
+// below the pivot are all zero.  Warp 0 computes; ends with a block barrier.
+template <class Ar>
+__device__ inline void make_reflector(const Tile& S, int kind, int N, int np, int j, typename Ar::E* sc);
+
+// Native FP64: ||x|| from the plain sum of squares unless that sum leaves [2^-900, 2^900], in
+// which case every entry is rescaled by the largest magnitude first.
+template <>
+__device__ inline void make_reflector<ArithF64>(const Tile& S, int kind, int N, int np, int j, double* sc) {
   const int lane = threadIdx.x;
   if (lane < 32) {
     const int r_lo = first_row(kind, j, np);
     double ss = 0.0;
     for (int r = r_lo + lane; r < N; r += 32) {
       if (skip_row(kind, r, j, np)) continue;
-      const double x = S(r, j);
+      const double x = at<double>(S, r, j);
       ss = fma(x, x, ss);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    const double alpha = S(j, j);
+    const double alpha = at<double>(S, j, j);
     double beta = alpha, tau = 0.0, inv = 0.0;
     const bool active = !(ss == 0.0);
     if (active) {
@@ -56,7 +67,7 @@ __device__ inline void make_reflector(const Tile& S, int kind, int N, int np, in
         double mx = fabs(alpha);
         for (int r = r_lo + lane; r < N; r += 32) {
           if (skip_row(kind, r, j, np)) continue;
-          const double a = fabs(S(r, j));
+          const double a = fabs(at<double>(S, r, j));
           if (!(a <= mx)) mx = a;  // keeps NaN
         }
 #pragma unroll
@@ -71,7 +82,7 @@ __device__ inline void make_reflector(const Tile& S, int kind, int N, int np, in
           double s = 0.0;
           for (int r = r_lo + lane; r < N; r += 32) {
             if (skip_row(kind, r, j, np)) continue;
-            const double t = S(r, j) / mx;
+            const double t = at<double>(S, r, j) / mx;
             s = fma(t, t, s);
           }
 #pragma unroll
@@ -93,6 +104,55 @@ __device__ inline void make_reflector(const Tile& S, int kind, int N, int np, in
   __syncthreads();
 }
 
+// Double-float: the column is rescaled by 2^k, with k set from its largest |hi|, before the
+// squares are summed, so the sum stays inside the FP32 exponent range; the square root and the
+// two divisions are double-float operations.
+template <>
+__device__ inline void make_reflector<ArithDF>(const Tile& S, int kind, int N, int np, int j, f32x2* sc) {
+  using E = f32x2;
+  const int lane = threadIdx.x;
+  if (lane < 32) {
+    const int r_lo = first_row(kind, j, np);
+    float tmx = 0.f;
+    for (int r = r_lo + lane; r < N; r += 32) {
+      if (skip_row(kind, r, j, np)) continue;
+      tmx = fmaxf(tmx, fabsf(at<E>(S, r, j).hi));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tmx = fmaxf(tmx, __shfl_xor_sync(0xffffffffu, tmx, o));
+    const E alpha = at<E>(S, j, j);
+    E beta = alpha, tau = ArithDF::zero(), inv = ArithDF::zero();
+    const bool active = tmx != 0.f;
+    if (active) {
+      const float mx = fmaxf(tmx, fabsf(alpha.hi));
+      int bexp = (__float_as_int(mx) >> 23) & 0xff;  // biased exponent of the largest |hi|
+      int k = 126 - bexp;                             // mx * 2^k in [0.5, 1)
+      k = k < -126 ? -126 : (k > 126 ? 126 : k);
+      E ss = ArithDF::zero();
+      for (int r = r_lo + lane; r < N; r += 32) {
+        if (skip_row(kind, r, j, np)) continue;
+        const E x = ArithDF::ldexp(at<E>(S, r, j), k);
+        ArithDF::fma_acc(ss, x, x);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss = ArithDF::add(ss, ArithDF::shfl_xor(ss, o));
+      const E as = ArithDF::ldexp(alpha, k);
+      ArithDF::fma_acc(ss, as, as);
+      const E nrm = ArithDF::ldexp(ArithDF::sqrt_df(ArithDF::norm(ss)), -k);
+      beta = ArithDF::is_neg(alpha) ? nrm : ArithDF::neg(nrm);
+      tau = ArithDF::div_df(ArithDF::sub(beta, alpha), beta);
+      inv = ArithDF::div_df(ArithDF::from_int(1), ArithDF::sub(alpha, beta));
+    }
+    if (lane == 0) {
+      sc[0] = beta;
+      sc[1] = tau;
+      sc[2] = inv;
+      sc[3] = active ? ArithDF::from_int(1) : ArithDF::zero();
+    }
+  }
+  __syncthreads();
+}
+
 // Packed upper-triangular storage of T: row i holds T[i][i..np-1] starting at tri_off(i, np).
 __host__ __device__ __forceinline__ int tri_off(int i, int np) { return i * np - (i * (i - 1)) / 2; }
 __host__ __device__ __forceinline__ int tri_size(int np) { return np * (np + 1) / 2; }
@@ -101,51 +161,55 @@ __host__ __device__ __forceinline__ int tri_size(int np) { return np * (np + 1) 
 // 16..64).  On return rows 0..n-1 hold R in their upper triangle and the reflectors' entries
 // below their pivots sit where the zeros were created (for CHAIN/NODE the top block's strict
 // lower part stays zero; it must be zero on entry).  tau_s[0..np) receives tau (0 beyond n);
-// if T_s != nullptr it receives T packed by rows (tri_off; tri_size(np) doubles, any contents
-// on entry).  red needs kThreads doubles, dvec np doubles, sc 4 doubles.  All threads must call.
-__device__ inline void stacked_qr(const Tile& S, int kind, int N, int np, int n, double* tau_s, double* T_s,
-                                  double* red, double* dvec, double* sc) {
+// if T_s != nullptr it receives T packed by rows (tri_off; tri_size(np) elements, any contents
+// on entry).  red needs kThreads elements, dvec np, sc 4.  All threads must call.
+template <class Ar>
+__device__ inline void stacked_qr(const Tile& S, int kind, int N, int np, int n, typename Ar::E* tau_s,
+                                  typename Ar::E* T_s, typename Ar::E* red, typename Ar::E* dvec,
+                                  typename Ar::E* sc) {
+  using E = typename Ar::E;
   const int tid = threadIdx.x;
-  const int G = kThreads / np;  // row groups of the (column, group) mapping
+  const int G = kThreads / np;  // row groups of the (column, group) mapping of the dot products
   const int cown = tid & (np - 1);
   const int gown = tid / np;
-  for (int j = tid + n; j < np; j += kThreads) tau_s[j] = 0.0;
+  for (int j = tid + n; j < np; j += kThreads) tau_s[j] = Ar::zero();
   for (int j = 0; j < n; ++j) {
-    make_reflector(S, kind, N, np, j, sc);
-    const double beta = sc[0], tau = sc[1], inv = sc[2];
-    const bool active = sc[3] != 0.0;
+    make_reflector<Ar>(S, kind, N, np, j, sc);
+    const E beta = sc[0], tau = sc[1], inv = sc[2];
+    const bool active = !Ar::is_zero(sc[3]);
     const int r_lo = first_row(kind, j, np);
     if (active) {
       // y = x / (alpha - beta) below the pivot
       for (int r = r_lo + tid; r < N; r += kThreads) {
         if (skip_row(kind, r, j, np)) continue;
-        S(r, j) *= inv;
+        E& x = at<E>(S, r, j);
+        x = Ar::mul(x, inv);
       }
       __syncthreads();
       // d_c = S(j, c) + sum_r y_r S(r, c) for every other column: c > j gives the update's
       // inner product, c < j the Gram entry v_c^T v_j for T.
       if (cown < n && cown != j) {
-        double acc = 0.0;
+        E acc = Ar::zero();
         for (int r = r_lo + gown; r < N; r += G) {
           if (skip_row(kind, r, j, np)) continue;
-          acc = fma(S(r, j), S(r, cown), acc);
+          Ar::fma_acc(acc, at<E>(S, r, j), at<E>(S, r, cown));
         }
         red[gown * np + cown] = acc;
       }
       __syncthreads();
       if (tid < n && tid != j) {
-        double d = S(j, tid);
-        for (int g = 0; g < G; ++g) d += red[g * np + tid];
+        E d = at<E>(S, j, tid);
+        for (int g = 0; g < G; ++g) d = Ar::add(d, red[g * np + tid]);
         dvec[tid] = d;
-        if (tid > j) S(j, tid) = fma(-tau, d, S(j, tid));
+        if (tid > j) at<E>(S, j, tid) = Ar::axpy(at<E>(S, j, tid), tau, d);
       }
-      if (tid == 0) S(j, j) = beta;
+      if (tid == 0) at<E>(S, j, j) = beta;
       __syncthreads();
       if (T_s != nullptr && tid < j) {
-        const double* Ti = T_s + tri_off(tid, np) - tid;  // Ti[p] = T[tid][p]
-        double s = 0.0;
-        for (int p = tid; p < j; ++p) s = fma(Ti[p], dvec[p], s);
-        T_s[tri_off(tid, np) + (j - tid)] = -tau * s;
+        const E* Ti = T_s + tri_off(tid, np) - tid;  // Ti[p] = T[tid][p]
+        E s = Ar::zero();
+        for (int p = tid; p < j; ++p) Ar::fma_acc(s, Ti[p], dvec[p]);
+        T_s[tri_off(tid, np) + (j - tid)] = Ar::neg(Ar::mul(tau, Ar::add(s, Ar::zero())));
       }
       // trailing update S(r, c) -= tau d_c y_r.  Only the ac = n-1-j columns right of j take
       // part, so they are spread over all threads afresh for every j: an FP64 instruction costs
@@ -157,15 +221,16 @@ __device__ inline void stacked_qr(const Tile& S, int kind, int N, int np, int n,
         if (tid < Gu * ac) {
           const int c = j + 1 + tid % ac;
           const int gu = tid / ac;
-          const double w = tau * dvec[c];
+          const E w = Ar::mul(tau, dvec[c]);
           for (int r = r_lo + gu; r < N; r += Gu) {
             if (skip_row(kind, r, j, np)) continue;
-            S(r, c) = fma(-w, S(r, j), S(r, c));
+            E& a = at<E>(S, r, c);
+            a = Ar::axpy(a, w, at<E>(S, r, j));
           }
         }
       }
     }
-    if (!active && T_s != nullptr && tid < j) T_s[tri_off(tid, np) + (j - tid)] = 0.0;
+    if (!active && T_s != nullptr && tid < j) T_s[tri_off(tid, np) + (j - tid)] = Ar::zero();
     if (tid == j) {
       if (T_s != nullptr) T_s[tri_off(j, np)] = tau;
       tau_s[j] = tau;

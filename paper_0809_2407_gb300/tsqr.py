@@ -163,16 +163,16 @@ class Factorization:
     """TSQR of a CUDA float64 matrix A (m x n, row-major).  Holds R, the workspace and the handle.
 
     ``inplace=True`` lets the reflectors overwrite A (A must then stay alive).  Options:
-    leaf_h, chain, arity (see tsqr_opts_t).
+    leaf_h, chain, arity, precision (0 native FP64, 1 double-float; see tsqr_opts_t).
     """
 
-    def __init__(self, A, leaf_h=0, chain=0, arity=0, inplace=False):
+    def __init__(self, A, leaf_h=0, chain=0, arity=0, inplace=False, precision=0):
         import torch
 
         _check_matrix(A, "A")
         m, n = A.shape
         self.m, self.n = m, n
-        self.opts = Opts(leaf_h=leaf_h, chain=chain, arity=arity, precision=0, inplace=1 if inplace else 0)
+        self.opts = Opts(leaf_h=leaf_h, chain=chain, arity=arity, precision=precision, inplace=1 if inplace else 0)
         nbytes = tsqr_workspace_size(TSQR_F64, m, n, self.opts)
         self.work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=A.device)
         self.R = torch.empty((n, n), dtype=torch.float64, device=A.device)
