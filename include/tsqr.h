@@ -13,8 +13,8 @@
  *
  * Conventions shared by every call:
  *   - Matrices are FP64, row-major: element (i, j) of X with leading dimension ldx is
- *     X[i * ldx + j].  Device pointers must be 16-byte aligned and, for A, lda must be even
- *     (TMA row strides are multiples of 16 bytes).
+ *     X[i * ldx + j], 8-byte aligned.  A is read by TMA, which needs a 16-byte aligned base
+ *     and an even lda; any other A is first copied into the workspace by a staging kernel.
  *   - Reflectors are H = I - tau v v^T with v_0 = 1; beta = -sign(alpha) ||x||, sign(0) = +1.
  *   - R is returned with a non-negative diagonal: D = diag(sign(R_jj)), R <- D R and the
  *     thin Q <- Q D (the QR is unique only up to these signs, Sec. 2).
@@ -93,8 +93,8 @@ typedef struct {
 tsqr_status_t tsqr_workspace_size(tsqr_dtype_t dtype, int64_t m, int64_t n, const tsqr_opts_t* opts,
                                   size_t* bytes);
 
-/* Factors A (m x n, m >= n >= 1, device, leading dimension lda >= n, lda even) into R and
- * an implicit Q (Algorithms 1 and 2, Sec. 3.1).
+/* Factors A (m x n, m >= n >= 1, device, leading dimension lda >= n) into R and an implicit
+ * Q (Algorithms 1 and 2, Sec. 3.1).  With inplace, lda must be even and A 16-byte aligned.
  *   dR     : device, n x n with ldr >= n; receives R with diag(R) >= 0, strict lower zeroed.
  *   dWork  : device workspace of at least tsqr_workspace_size bytes, 256-byte aligned.
  *   out    : receives a new handle (free with tsqr_destroy).  The handle records A's pointer

@@ -227,13 +227,18 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
   if (layout != TSQR_ROW_MAJOR) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_ROW_MAJOR is implemented");
   if (!dA || !dR) return fail(TSQR_ERR_INVALID_ARG, "A and R must be non-NULL");
   if (n < 1 || m < n) return fail(TSQR_ERR_INVALID_ARG, "need m >= n >= 1");
-  if (lda < n || lda % 2 != 0) return fail(TSQR_ERR_INVALID_ARG, "lda must be >= n and even");
+  if (lda < n) return fail(TSQR_ERR_INVALID_ARG, "lda must be >= n");
   if (ldr < n) return fail(TSQR_ERR_INVALID_ARG, "ldr must be >= n");
-  if (!aligned16(dA)) return fail(TSQR_ERR_INVALID_ARG, "A must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(dA) & 7) != 0) return fail(TSQR_ERR_INVALID_ARG, "A must be 8-byte aligned");
   Plan P;
   tsqr_status_t s = make_plan(m, n, opts, &P);
   if (s != TSQR_OK) return s;
   const bool inplace = opts && opts->inplace;
+  // TMA needs a 16-byte aligned base and a row stride that is a multiple of 16 bytes; any other A
+  // is first copied into the reflector storage of the workspace (which then holds V as usual).
+  const bool stage = (lda % 2 != 0) || !aligned16(dA);
+  if (stage && inplace)
+    return fail(TSQR_ERR_INVALID_ARG, "inplace needs an even lda and a 16-byte aligned A");
   const Layout L = make_layout(P, inplace);
   if (!dWork || work_bytes < L.total)
     return fail(TSQR_ERR_WORKSPACE, "workspace needs " + std::to_string(L.total) + " bytes");
@@ -253,11 +258,19 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
   st.status = reinterpret_cast<int*>(w + L.status);
   const int box_rows = P.h < 256 ? P.h : 256;
   CUtensorMap mapA, mapV;
-  if ((s = make_map(&mapA, dA, m, n, lda, box_rows)) != TSQR_OK) return s;
   if ((s = make_map(&mapV, st.v, m, n, st.ldv, box_rows)) != TSQR_OK) return s;
+  if (stage) {
+    mapA = mapV;
+  } else if ((s = make_map(&mapA, dA, m, n, lda, box_rows)) != TSQR_OK) {
+    return s;
+  }
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(st.status, 0, sizeof(int), cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (stage) {
+    e = tsqr::launch_stage_copy(static_cast<const double*>(dA), lda, st.v, st.ldv, m, (int)n, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "staging copy launch");
+  }
   e = tsqr::launch_factor(mapA, mapV, P, st, static_cast<double*>(dR), ldr, box_rows, cs);
   if (e != cudaSuccess) return cuda_fail(e, "factor launch");
   tsqr_handle_s* h = new (std::nothrow) tsqr_handle_s;

@@ -1,0 +1,211 @@
+// The flat-tree step QR([R; A_k]) (Algorithm 2, loop body; Sec. 3.1: triangle atop a full
+// block) for the default leaf shapes, scheduled for GB300.
+//
+// Same mathematics as stacked_qr(CHAIN): for each column j the reflector of the pivot R_jj and
+// the h rows of A_k, applied to the columns right of j, with the compact-WY T.  The schedule
+// differs in four ways, all aimed at the issue slots and barriers that bound this step:
+//   * shapes are compile-time and the h bottom rows are walked in blocks of 8 whose swizzled
+//     shared-memory offsets are precomputed per column, so inner loops do no address math;
+//   * look-ahead: while warps 1..7 apply reflector j to columns j+2.., warp 0 applies it to
+//     column j+1 and builds reflector j+1, so the serial norm/sqrt/division work overlaps the
+//     trailing update (three barriers per column instead of five);
+//   * the reflector column is left unscaled (x instead of v = x/(alpha-beta)) while the leaf
+//     is factored; products with it carry the factor inv_j = 1/(alpha-beta) instead, and the
+//     whole leaf is scaled once at the end;
+//   * T is assembled after the leaf from the Gram entries g_pj = v_p^T v_j by the blocked
+//     Schreiber-Van Loan merge T = [T1, -T1 G12 T2; 0, T2], in parallel, instead of a
+//     column recurrence on the critical path of every reflector.
+#pragma once
+
+#include "householder.cuh"
+
+namespace tsqr {
+
+// Shapes with a specialised chain step: (np, h) of the default plans.
+template <int NP>
+struct ChainShape;
+template <>
+struct ChainShape<64> {
+  static constexpr int H = 96;
+};
+template <>
+struct ChainShape<32> {
+  static constexpr int H = 256;
+};
+template <>
+struct ChainShape<16> {
+  static constexpr int H = 512;
+};
+
+// Byte offset of element (r, c) in a Tile with rows_cap rows (the layout of Tile::ptr).
+__device__ __forceinline__ uint32_t tile_off(int rows_cap, int r, int c) {
+  return (uint32_t)(c >> 4) * (uint32_t)rows_cap * 128u + (uint32_t)r * 128u +
+         (((((uint32_t)c & 15u) >> 1) ^ ((uint32_t)r & 7u)) << 4) + (((uint32_t)c & 1u) << 3);
+}
+
+// Offsets of column c in the 8 rows of a block that starts at a row multiple of 8.
+__device__ __forceinline__ void block_offsets(int rows_cap, int c, uint32_t off[8]) {
+#pragma unroll
+  for (int t = 0; t < 8; ++t) off[t] = tile_off(rows_cap, t, c);
+}
+
+// Scratch of chain_qr, in shared memory: red (kThreads), dvec, wvec, invs (NP each),
+// sc (4), X (NP/2 * NP/2) for the T merges.
+template <class Ar, int NP>
+struct ChainScratch {
+  typename Ar::E *red, *dvec, *wvec, *invs, *sc, *X;
+};
+
+// QR of [R; A_k] held in tile rows 0..NP-1 (R, strict lower part zero) and NP..NP+H-1 (A_k).
+// Leaves R in rows 0..n-1, the scaled reflectors in rows NP.., tau in tau_s and T packed by
+// rows in T_s (tri_off).  All threads call.
+template <class Ar, int NP>
+__device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename Ar::E* T_s,
+                         const ChainScratch<Ar, NP>& w) {
+  using E = typename Ar::E;
+  constexpr int H = ChainShape<NP>::H;
+  constexpr int NB = H / 8;            // row blocks of the bottom part
+  constexpr int G = kThreads / NP;     // row groups of the dot products
+  constexpr int NBG = NB / G;          // blocks per group
+  static_assert(NB % G == 0, "row blocks must divide among the groups");
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int rc = S.rows_cap;
+  char* const bottom = S.base + (size_t)NP * 128;  // row NP starts block 0
+  E* sc = w.sc;
+
+  // reflector of column 0 before the loop
+  if (warp == 0) chain_reflector<Ar>(S, NP, H, 0, sc, w.invs);
+  for (int j = tid + n; j < NP; j += kThreads) tau_s[j] = Ar::zero();
+  __syncthreads();
+
+  const int cown = tid & (NP - 1);
+  const int gown = tid / NP;
+  uint32_t oc[8];
+  block_offsets(rc, cown, oc);
+
+  for (int j = 0; j < n; ++j) {
+    const E tau = sc[1];
+    const E inv = sc[2];
+    const bool active = !Ar::is_zero(sc[3]);
+    if (tid == j) tau_s[j] = tau;
+    if (tid == j) T_s[tri_off(j, NP)] = tau;
+    if (active) {
+      // ---- A: D_c = sum_r x_r a_rc over the bottom rows, every column c != j
+      uint32_t oj[8];
+      block_offsets(rc, j, oj);
+      if (cown < n && cown != j) {
+        // four independent partial sums so consecutive multiply-adds do not wait on each other
+        E acc[4] = {Ar::zero(), Ar::zero(), Ar::zero(), Ar::zero()};
+#pragma unroll
+        for (int bb = 0; bb < NBG; ++bb) {
+          const char* pb = bottom + (size_t)(gown + bb * G) * 1024;
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const E x = *reinterpret_cast<const E*>(pb + oj[t]);
+            const E a = *reinterpret_cast<const E*>(pb + oc[t]);
+            Ar::fma_acc(acc[t & 3], x, a);
+          }
+        }
+        w.red[gown * NP + cown] = Ar::add(Ar::add(acc[0], acc[1]), Ar::add(acc[2], acc[3]));
+      }
+      __syncthreads();
+      // ---- B: d_c = S(j,c) + inv D_c (c > j): pivot-row update and the update weight;
+      //         g_cj = inv_c inv D_c (c < j): Gram entries for T
+      if (tid < n && tid != j) {
+        E D = w.red[tid];
+#pragma unroll
+        for (int g = 1; g < G; ++g) D = Ar::add(D, w.red[g * NP + tid]);
+        if (tid > j) {
+          E& pr = at<E>(S, j, tid);
+          const E d = Ar::add(pr, Ar::mul(inv, D));
+          pr = Ar::axpy(pr, tau, d);
+          w.wvec[tid] = Ar::mul(Ar::mul(tau, d), inv);  // weight on the unscaled x
+        } else {
+          T_s[tri_off(tid, NP) + (j - tid)] = Ar::mul(Ar::mul(w.invs[tid], inv), D);
+        }
+      }
+      if (tid == 0) at<E>(S, j, j) = sc[0];
+      __syncthreads();
+      // ---- C: trailing update a_rc -= w_c x_r; warp 0 takes column j+1 and then builds
+      //         reflector j+1, warps 1..7 take columns j+2..n-1
+      if (warp == 0) {
+        if (j + 1 < n) {
+          const int c = j + 1;
+          const E wc = w.wvec[c];
+          for (int r = NP + lane; r < NP + H; r += 32) {
+            E& a = at<E>(S, r, c);
+            a = Ar::axpy(a, wc, at<E>(S, r, j));
+          }
+          __syncwarp();
+          chain_reflector<Ar>(S, NP, H, j + 1, sc, w.invs);
+        }
+      } else {
+        const int ac = n - j - 2;
+        if (ac > 0) {
+          const int t2 = tid - 32;
+          const int Gu = (kThreads - 32) / ac;
+          const int gu = t2 / ac;
+          if (gu < Gu) {
+            const int c = j + 2 + t2 % ac;
+            const E wc = w.wvec[c];
+            uint32_t oa[8];
+            block_offsets(rc, c, oa);
+            for (int b = gu; b < NB; b += Gu) {
+              char* pb = bottom + (size_t)b * 1024;
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                E& a = *reinterpret_cast<E*>(pb + oa[t]);
+                a = Ar::axpy(a, wc, *reinterpret_cast<const E*>(pb + oj[t]));
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+    } else {
+      // H_j = I: no update; Gram entries with column j are zero; build reflector j+1
+      if (tid < j) T_s[tri_off(tid, NP) + (j - tid)] = Ar::zero();
+      if (warp == 0 && j + 1 < n) chain_reflector<Ar>(S, NP, H, j + 1, sc, w.invs);
+      __syncthreads();
+    }
+  }
+
+  // ---- scale the reflector columns: v = x * inv_c
+  for (int i = tid; i < H * n; i += kThreads) {
+    const int r = NP + i / n, c = i % n;
+    E& x = at<E>(S, r, c);
+    x = Ar::mul(x, w.invs[c]);
+  }
+  // ---- T from the Gram entries by blocked merges (sizes 1, 2, 4, ... NP/2)
+  for (int b = 1; b < n; b <<= 1) {
+    const int pairs = (n + 2 * b - 1) / (2 * b);
+    // X = G12 * T2 for every pair (G12 at rows blk1, cols blk2 of T_s; T2 upper)
+    for (int o = tid; o < pairs * b * b; o += kThreads) {
+      const int k = o / (b * b), i = (o / b) % b, q = o % b;
+      const int r1 = 2 * b * k + i, c2 = 2 * b * k + b + q;
+      E v = Ar::zero();
+      if (r1 < n && c2 < n) {
+        for (int p = 2 * b * k + b; p <= c2; ++p)
+          Ar::fma_acc(v, T_s[tri_off(r1, NP) + (p - r1)], T_s[tri_off(p, NP) + (c2 - p)]);
+      }
+      w.X[o] = Ar::add(v, Ar::zero());
+    }
+    __syncthreads();
+    // T12 = -T1 * X
+    for (int o = tid; o < pairs * b * b; o += kThreads) {
+      const int k = o / (b * b), i = (o / b) % b, q = o % b;
+      const int r1 = 2 * b * k + i, c2 = 2 * b * k + b + q;
+      if (r1 < n && c2 < n) {
+        E v = Ar::zero();
+        for (int p = r1; p < 2 * b * k + b; ++p)
+          Ar::fma_acc(v, T_s[tri_off(r1, NP) + (p - r1)], w.X[(k * b + (p - 2 * b * k)) * b + q]);
+        T_s[tri_off(r1, NP) + (c2 - r1)] = Ar::neg(Ar::add(v, Ar::zero()));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace tsqr

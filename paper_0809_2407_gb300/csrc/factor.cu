@@ -12,14 +12,14 @@
 // "by order of processor ids"), takes their structured QR (eq. fact_2rs) and climbs on.  The
 // block that finishes the root writes R with diag(R) >= 0 and the sign vector.
 #include "factor_kernels.h"
-#include "householder.cuh"
+#include "chain_qr.cuh"
 
 namespace tsqr {
 
 template <class E>
 struct FactorSmem {
   Tile S;
-  E *T_s, *red, *dvec, *sc, *tau_s;
+  E *T_s, *red, *dvec, *sc, *tau_s, *wvec, *invs, *X;
   uint64_t* bar;
   int* flag;
 };
@@ -34,14 +34,33 @@ __device__ inline FactorSmem<E> carve_factor(char* raw, const Plan& P) {
   f.dvec = f.red + kThreads;
   f.sc = f.dvec + P.np;
   f.tau_s = f.sc + 8;
-  f.bar = reinterpret_cast<uint64_t*>(f.tau_s + P.np);
+  f.wvec = f.tau_s + P.np;
+  f.invs = f.wvec + P.np;
+  f.X = f.invs + P.np;
+  f.bar = reinterpret_cast<uint64_t*>(f.X + P.np * P.np / 4);
   f.flag = reinterpret_cast<int*>(f.bar + 1);
   return f;
 }
 
 size_t factor_smem_bytes(const Plan& P) {
   return 1024 + (size_t)P.rows_cap * P.np * 8 + (size_t)tri_size(P.np) * 8 + kThreads * 8 + P.np * 8 + 8 * 8 +
-         P.np * 8 + 8 + 16;
+         P.np * 8 + 2 * P.np * 8 + (size_t)P.np * P.np / 4 * 8 + 8 + 16;
+}
+
+// The flat-tree step on the tile: the scheduled chain_qr for the default shapes, the generic
+// stacked_qr otherwise.
+template <class Ar>
+__device__ inline void chain_step(const FactorSmem<typename Ar::E>& f, const Plan& P) {
+  const int np = P.np, n = P.n, h = P.h;
+  if (np == 64 && h == ChainShape<64>::H) {
+    chain_qr<Ar, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 64>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+  } else if (np == 32 && h == ChainShape<32>::H) {
+    chain_qr<Ar, 32>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 32>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+  } else if (np == 16 && h == ChainShape<16>::H) {
+    chain_qr<Ar, 16>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 16>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+  } else {
+    stacked_qr<Ar>(f.S, CHAIN, np + h, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
+  }
 }
 
 // Rows [r0, r0 + rows) of the tile arrive from TMA as FP64; in double-float mode they are split
@@ -89,7 +108,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       return;
     }
     convert_rows_in<Ar>(S, dst, h, np);
-    stacked_qr<Ar>(S, plain ? PLAIN : CHAIN, dst + h, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
+    if (plain)
+      stacked_qr<Ar>(S, PLAIN, h, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
+    else
+      chain_step<Ar>(f, P);
     tile_store(S, &mapV, np, row0, h, dst, box_rows);
     E* tau_g = tau_leaf + leaf * np;
     E* T_g = t_leaf + leaf * np * np;
@@ -183,6 +205,24 @@ static cudaError_t launch_factor_t(const CUtensorMap& mapA, const CUtensorMap& m
   e = cudaMemsetAsync(st.counters, 0, sizeof(int) * (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1), stream);
   if (e != cudaSuccess) return e;
   factor_kernel<Ar><<<P.chains, kThreads, smem, stream>>>(mapA, mapV, P, st, R_out, ldr, box_rows);
+  return cudaGetLastError();
+}
+
+// Copies A (m x n, leading dimension lda) into V (leading dimension ldv): the staging step for
+// an A whose row stride or address TMA cannot take (odd lda, or not 16-byte aligned).
+__global__ void stage_copy_kernel(const double* __restrict__ A, int64_t lda, double* __restrict__ V, int64_t ldv,
+                                  int64_t m, int n) {
+  const int64_t total = m * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n;
+    const int c = (int)(i - r * n);
+    V[r * ldv + c] = A[r * lda + c];
+  }
+}
+
+cudaError_t launch_stage_copy(const double* A, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
+                              cudaStream_t stream) {
+  stage_copy_kernel<<<152 * 8, 256, 0, stream>>>(A, lda, V, ldv, m, n);
   return cudaGetLastError();
 }
 

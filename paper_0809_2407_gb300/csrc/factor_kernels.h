@@ -9,6 +9,8 @@ size_t factor_smem_bytes(const Plan& P);
 size_t formq_smem_bytes(const Plan& P);
 size_t apply_smem_bytes(const Plan& P, int kb);
 
+cudaError_t launch_stage_copy(const double* A, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
+                              cudaStream_t stream);
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                           double* R_out, int64_t ldr, int box_rows, cudaStream_t stream);
 cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,

@@ -33,19 +33,19 @@ __device__ __forceinline__ bool skip_row(int kind, int r, int j, int np) {
   return kind == NODE && (r & (np - 1)) > j;
 }
 
-// Reflector of column j (x = S(j, j) and the column's rows >= r_lo), written to sc[]:
+// Reflector of column j (x = S(j, j) and the column's rows >= r_lo), written to sc[] by lane 0:
 //   sc[0] = beta (new S(j, j)), sc[1] = tau, sc[2] = 1/(alpha - beta), sc[3] != 0 if H != I.
 // beta = -sign(alpha) ||x||, sign(0) = +1; tau = (beta - alpha)/beta; tau = 0 when the rows
-// below the pivot are all zero.  Warp 0 computes; ends with a block barrier.
+// below the pivot are all zero.  Called by all 32 lanes of one warp; no block barrier.
 template <class Ar>
-__device__ inline void make_reflector(const Tile& S, int kind, int N, int np, int j, typename Ar::E* sc);
+__device__ inline void reflector_warp(const Tile& S, int kind, int N, int np, int j, typename Ar::E* sc);
 
 // Native FP64: ||x|| from the plain sum of squares unless that sum leaves [2^-900, 2^900], in
 // which case every entry is rescaled by the largest magnitude first.
 template <>
-__device__ inline void make_reflector<ArithF64>(const Tile& S, int kind, int N, int np, int j, double* sc) {
-  const int lane = threadIdx.x;
-  if (lane < 32) {
+__device__ inline void reflector_warp<ArithF64>(const Tile& S, int kind, int N, int np, int j, double* sc) {
+  const int lane = threadIdx.x & 31;
+  {
     const int r_lo = first_row(kind, j, np);
     double ss = 0.0;
     for (int r = r_lo + lane; r < N; r += 32) {
@@ -101,17 +101,16 @@ __device__ inline void make_reflector<ArithF64>(const Tile& S, int kind, int N, 
       sc[3] = active ? 1.0 : 0.0;
     }
   }
-  __syncthreads();
 }
 
 // Double-float: the column is rescaled by 2^k, with k set from its largest |hi|, before the
 // squares are summed, so the sum stays inside the FP32 exponent range; the square root and the
 // two divisions are double-float operations.
 template <>
-__device__ inline void make_reflector<ArithDF>(const Tile& S, int kind, int N, int np, int j, f32x2* sc) {
+__device__ inline void reflector_warp<ArithDF>(const Tile& S, int kind, int N, int np, int j, f32x2* sc) {
   using E = f32x2;
-  const int lane = threadIdx.x;
-  if (lane < 32) {
+  const int lane = threadIdx.x & 31;
+  {
     const int r_lo = first_row(kind, j, np);
     float tmx = 0.f;
     for (int r = r_lo + lane; r < N; r += 32) {
@@ -150,7 +149,23 @@ __device__ inline void make_reflector<ArithDF>(const Tile& S, int kind, int N, i
       sc[3] = active ? ArithDF::from_int(1) : ArithDF::zero();
     }
   }
+}
+
+// Warp 0 builds the reflector of column j, then the block synchronises.
+template <class Ar>
+__device__ inline void make_reflector(const Tile& S, int kind, int N, int np, int j, typename Ar::E* sc) {
+  if (threadIdx.x < 32) reflector_warp<Ar>(S, kind, N, np, j, sc);
   __syncthreads();
+}
+
+// The reflector of column j of the stacked [R; A_k] held in rows 0..np-1 and np..np+h-1
+// (one warp), also recording inv = 1/(alpha - beta) in invs[j] (zero when H = I).
+template <class Ar>
+__device__ inline void chain_reflector(const Tile& S, int np, int h, int j, typename Ar::E* sc,
+                                       typename Ar::E* invs) {
+  reflector_warp<Ar>(S, CHAIN, np + h, np, j, sc);
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) invs[j] = Ar::is_zero(sc[3]) ? Ar::zero() : sc[2];
 }
 
 // Packed upper-triangular storage of T: row i holds T[i][i..np-1] starting at tri_off(i, np).

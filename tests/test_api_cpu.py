@@ -68,11 +68,17 @@ def test_factor_rejects_before_launch(lib):
     L = lib.load()
     h = ctypes.c_void_p()
     fake = ctypes.c_void_p(0x1000)  # never dereferenced: every case fails validation first
-    # odd lda
-    assert L.tsqr_factor(0, 0, 100, 3, fake, 3, fake, 3, fake, 1 << 20, None, None, ctypes.byref(h)) == 1
-    # misaligned A
-    assert L.tsqr_factor(0, 0, 100, 4, ctypes.c_void_p(0x1008), 4, fake, 4, fake, 1 << 20, None, None,
+    # lda < n
+    assert L.tsqr_factor(0, 0, 100, 3, fake, 2, fake, 3, fake, 1 << 20, None, None, ctypes.byref(h)) == 1
+    # A not even 8-byte aligned
+    assert L.tsqr_factor(0, 0, 100, 4, ctypes.c_void_p(0x1004), 4, fake, 4, fake, 1 << 20, None, None,
                          ctypes.byref(h)) == 1
+    # in place needs a TMA-compatible A (even lda, 16-byte aligned)
+    inpl = lib.Opts(inplace=1)
+    assert L.tsqr_factor(0, 0, 100, 3, fake, 3, fake, 3, fake, 1 << 20, ctypes.byref(inpl), None,
+                         ctypes.byref(h)) == 1
+    assert L.tsqr_factor(0, 0, 100, 4, ctypes.c_void_p(0x1008), 4, fake, 4, fake, 1 << 20, ctypes.byref(inpl),
+                         None, ctypes.byref(h)) == 1
     # FP32 and column-major are not implemented
     assert L.tsqr_factor(1, 0, 100, 4, fake, 4, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 2
     assert L.tsqr_factor(0, 1, 100, 4, fake, 4, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 2

@@ -100,12 +100,41 @@ def test_ragged_and_edge_shapes(T, m, n, h, prec):
     check_against_oracle(A_h, R, Q, precision=prec)
 
 
+@pytest.mark.parametrize("m,n", [(40000 + 13, 64), (30000, 50), (60000 + 7, 32), (50000, 33), (100000 + 3, 16),
+                                 (70000, 17), (9000, 64)])
+def test_default_plan_shapes(T, m, n, prec):
+    """The default plans (leaf height 96/256/512 for n up to 64/32/16) run the scheduled chain step."""
+    A_h = inputs.gaussian(m, n, inputs.seed_for(3, m + n))
+    f, R, Q = run(T, A_h, precision=prec)
+    assert f.info().leaf_h == {64: 96, 32: 256, 16: 512}[f.info().np]
+    check_against_oracle(A_h, R, Q, precision=prec)
+
+
 def test_short_last_leaf_is_merged(T):
     """A last leaf with fewer than n rows joins the previous chain instead of starting one."""
     A_h = inputs.gaussian(64 * 4 + 5, 32, 77)
     f, R, Q = run(T, A_h, leaf_h=64, chain=1, arity=2)
     assert f.info().chains == 4
     check_against_oracle(A_h, R, Q)
+
+
+@pytest.mark.parametrize("lda_extra,offset", [(0, 0), (1, 0), (0, 1), (3, 1)])
+def test_staged_layouts(T, lda_extra, offset):
+    """Odd leading dimensions and 8-byte (not 16-byte) aligned A go through the staging copy."""
+    import torch
+
+    m, n = 3001, 21
+    A_h = inputs.gaussian(m, n, 404 + lda_extra)
+    lda = n + lda_extra
+    buf = torch.zeros(m * lda + 2, dtype=torch.float64, device="cuda")
+    A = buf[offset:offset + m * lda].view(m, lda)[:, :n]
+    A.copy_(torch.from_numpy(A_h))
+    f = T.Factorization(A)
+    Q = f.form_q()
+    torch.cuda.synchronize()
+    assert f.status() == T.TSQR_OK
+    check_against_oracle(A_h, f.R.cpu().numpy(), Q.cpu().numpy())
+    assert np.array_equal(A.cpu().numpy(), A_h)  # A untouched
 
 
 def test_strided_and_inplace(T):
