@@ -66,8 +66,8 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P) {
   int np = 16;
   while (np < n) np *= 2;
   if (np > 64) return fail(TSQR_ERR_UNSUPPORTED, "n > 64 is not supported by this build");
-  if (o->precision != 0 && o->precision != 1)
-    return fail(TSQR_ERR_UNSUPPORTED, "precision must be 0 (native FP64) or 1 (double-float)");
+  if (o->precision < 0 || o->precision > 2)
+    return fail(TSQR_ERR_UNSUPPORTED, "precision must be 0 (native FP64), 1 (double-float) or 2 (Ozaki WY)");
   const int arity = o->arity ? o->arity : 2;
   if (arity < 2 || arity > tsqr::kMaxArity) return fail(TSQR_ERR_INVALID_ARG, "arity must be in 2..8");
   int h = o->leaf_h ? o->leaf_h : default_leaf_h(np);
@@ -118,7 +118,8 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P) {
   if (arity * np > rows_cap) rows_cap = arity * np;
   P->rows_cap = (rows_cap + 7) / 8 * 8;
   if (tsqr::factor_smem_bytes(*P) > kSmemLimit || tsqr::formq_smem_bytes(*P) > kSmemLimit ||
-      tsqr::apply_smem_bytes(*P, 32) > kSmemLimit)
+      tsqr::apply_smem_bytes(*P, 32) > kSmemLimit ||
+      (tsqr::ozaki_form_q_applies(*P) && tsqr::formq_ozaki_smem_bytes(*P) > kSmemLimit))
     return fail(TSQR_ERR_UNSUPPORTED, "leaf_h/arity too large for shared memory at this n");
   return TSQR_OK;
 }

@@ -11,6 +11,7 @@
 // workspace are in that policy's element format, B and Q are FP64 at the boundary.
 #include "arith.cuh"
 #include "factor_kernels.h"
+#include "ozaki.cuh"
 
 namespace tsqr {
 
@@ -218,6 +219,295 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
     }
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// Thin Q with the compact-WY products on the tensor cores (precision mode 2).
+//
+// Per chain leaf: M = T C and Q_rows = -Y M, each an Ozaki-split FP64 product (ozaki.cuh) of
+// 8 x 8 bf16 slice pairs on tcgen05 with exact FP32 accumulators in TMEM; C -= M in FP64.
+// The first leaf of a chain (V unit lower trapezoidal, one leaf in a chain) takes the native
+// FP64 route.  Needs np = 64 (33 <= n <= 64) and h <= 128.
+
+struct OzSmem {
+  Tile Y;           // h x 64 FP64 leaf tile (TMA); converted in place to fixed point
+  char* bsl;        // 8 B slices, 8 KB each; FP64 scratch (T, X) for the first leaf
+  char* asl;        // 2 A slice buffers, 16 KB each
+  double* C;        // 64 x 65
+  double* M;        // 64 x 65; fixed-point T (64 x 64 int64) before the T C product
+  int* expA;        // 128
+  int* expB;        // 64
+  uint64_t* bars;   // 0: TMA, 1: A buffer 0, 2: A buffer 1
+  uint32_t* slot;   // TMEM base address
+  int* flag;
+};
+
+static constexpr int kOzLd = 65;
+
+__device__ inline OzSmem carve_ozaki(char* raw, int h) {
+  OzSmem z;
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  const size_t ybytes = ((size_t)h * 64 * 8 + 1023) & ~size_t(1023);
+  z.Y = Tile{base, h};
+  z.bsl = base + ybytes;
+  z.asl = z.bsl + 8 * oz::kBSliceBytes;
+  z.C = reinterpret_cast<double*>(z.asl + 2 * oz::kASliceBytes);
+  z.M = z.C + 64 * kOzLd;
+  z.expA = reinterpret_cast<int*>(z.M + 64 * kOzLd);
+  z.expB = z.expA + 128;
+  z.bars = reinterpret_cast<uint64_t*>(z.expB + 64);
+  z.slot = reinterpret_cast<uint32_t*>(z.bars + 4);
+  z.flag = reinterpret_cast<int*>(z.slot + 2);
+  return z;
+}
+
+size_t formq_ozaki_smem_bytes(const Plan& P) {
+  const size_t ybytes = ((size_t)P.h * 64 * 8 + 1023) & ~size_t(1023);
+  return 1024 + ybytes + 8 * oz::kBSliceBytes + 2 * oz::kASliceBytes + 2 * 64 * kOzLd * 8 + 128 * 4 + 64 * 4 + 4 * 8 +
+         16;
+}
+
+// One Ozaki product D (128 x 64) = A (a_rows x 64) B (64 x 64): the B slices must already be in
+// z.bsl; afix(r, k) gives the fixed-point A entries (rows < a_rows), z.expA / z.expB the
+// exponents.  The 8 group accumulators land in TMEM.  All threads call.  False on timeout.
+template <class AFix>
+__device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows, AFix afix, uint32_t ph[2],
+                                      int* status) {
+  const int tid = threadIdx.x;
+  const uint32_t idesc = oz::idesc_bf16(oz::kM, oz::kN);
+  for (int s = 1; s <= oz::kSlices; ++s) {
+    const int b = (s - 1) & 1;
+    if (s >= 3) {
+      if (tid == 0) {
+        if (!oz::wait_bar(z.bars + 1 + b, ph[b])) {
+          atomicOr(status, kStatusTimeout);
+          *z.flag = 1;
+        }
+        ph[b] ^= 1u;
+      }
+      __syncthreads();
+      if (*z.flag) return false;
+    }
+    char* abuf = z.asl + b * oz::kASliceBytes;
+    for (int idx = tid; idx < oz::kM * 32; idx += kThreads) {  // two k per thread: one 32-bit store
+      const int r = idx >> 5, k = (idx & 31) * 2;
+      uint32_t lo = 0, hi = 0;
+      if (r < a_rows) {
+        lo = oz::slice_bf16(afix(r, k), s);
+        hi = oz::slice_bf16(afix(r, k + 1), s);
+      }
+      *reinterpret_cast<uint32_t*>(abuf + oz::op_off(r, k)) = lo | (hi << 16);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      oz::fence_after_sync();
+      const uint32_t a0 = smem_u32(abuf);
+      for (int t = 1; t <= oz::kSlices + 1 - s; ++t) {
+        const uint32_t d = tmem + (uint32_t)(s + t - 2) * 64u;
+        const uint32_t b0 = smem_u32(z.bsl + (t - 1) * oz::kBSliceBytes);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          oz::mma_bf16(d, oz::sw128_desc(a0 + kk * 32), oz::sw128_desc(b0 + kk * 32), idesc,
+                       (s > 1 || kk > 0) ? 1u : 0u);
+      }
+      oz::mma_commit(z.bars + 1 + b);
+    }
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      if (!oz::wait_bar(z.bars + 1 + b, ph[b])) {
+        atomicOr(status, kStatusTimeout);
+        *z.flag = 1;
+      }
+      ph[b] ^= 1u;
+    }
+  }
+  oz::fence_before_sync();
+  __syncthreads();
+  oz::fence_after_sync();
+  return *z.flag == 0;
+}
+
+// B slices of the 64 x 64 matrix whose output column j and k-th entry is bval(j, k), against the
+// column exponents z.expB (computed here).  All threads call; ends with a barrier.
+template <class BVal>
+__device__ inline void ozaki_b_slices(const OzSmem& z, BVal bval) {
+  const int tid = threadIdx.x;
+  for (int j = tid; j < 64; j += kThreads) z.expB[j] = 0;
+  __syncthreads();
+  for (int idx = tid; idx < 64 * 64; idx += kThreads) atomicMax(&z.expB[idx >> 6], oz::bexp(bval(idx >> 6, idx & 63)));
+  __syncthreads();
+  for (int idx = tid; idx < 64 * 32; idx += kThreads) {
+    const int j = idx >> 5, k = (idx & 31) * 2;
+    const uint64_t f0 = oz::to_fixed(bval(j, k), z.expB[j]);
+    const uint64_t f1 = oz::to_fixed(bval(j, k + 1), z.expB[j]);
+#pragma unroll
+    for (int s = 1; s <= oz::kSlices; ++s)
+      *reinterpret_cast<uint32_t*>(z.bsl + (s - 1) * oz::kBSliceBytes + oz::op_off(j, k)) =
+          oz::slice_bf16(f0, s) | (oz::slice_bf16(f1, s) << 16);
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+}
+
+// Reads the 8 group accumulators back: out(i, j, value) for rows i < rows and all 64 columns,
+// value = sum of the product's exact slice groups, rescaled to FP64.
+template <class Out>
+__device__ inline void ozaki_epilogue(const OzSmem& z, uint32_t tmem, int rows, Out out) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i = 32 * (warp & 3) + lane;
+  const int c0 = 32 * (warp >> 2);
+  const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+  long long acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0;
+#pragma unroll 1
+  for (int g = 2; g <= oz::kSlices + 1; ++g) {
+    uint32_t v[32];
+    oz::tmem_ld32(tb + (uint32_t)(g - 2) * 64u, v);
+    oz::tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const long long G = (long long)__float2int_rn(__uint_as_float(v[c]));
+      acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
+    }
+  }
+  if (i < rows) {
+    const int ea = z.expA[i];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) out(i, c0 + c, oz::scale_int(acc[c], ea + z.expB[c0 + c] - 2100));
+  }
+  oz::fence_before_sync();
+  __syncthreads();
+  oz::fence_after_sync();
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    formq_ozaki_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
+                       int64_t ldq, int box_rows) {
+  extern __shared__ char smem_raw[];
+  OzSmem z = carve_ozaki(smem_raw, P.h);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int np = 64, n = P.n, h = P.h;
+  const int g = blockIdx.x;
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) mbar_init(z.bars + b, 1);
+    fence_mbar_init();
+    *z.flag = 0;
+  }
+  if (warp == 0) oz::tmem_alloc(z.slot, oz::kTmemCols);
+  oz::fence_before_sync();
+  __syncthreads();
+  oz::fence_after_sync();
+  const uint32_t tmem = *z.slot;
+  uint32_t ph[2] = {0u, 0u};
+  uint32_t tma_phase = 0;
+  // C = this chain's block of Q_tree [D; 0]
+  for (int i = tid; i < np * np; i += kThreads) {
+    const int a = i / np, b = i % np;
+    z.C[a * kOzLd + b] = (P.depth == 0) ? ((a == b && a < n) ? __ldcg(st.signs + a) : 0.0)
+                                        : __ldcg(st.node_r + (size_t)g * np * np + i);
+  }
+  __syncthreads();
+  const int64_t l0 = chain_first_leaf(P, g), l1 = chain_end_leaf(P, g);
+  bool alive = true;
+  for (int64_t leaf = l1 - 1; leaf >= l0 && alive; --leaf) {
+    const int64_t row0 = leaf * h;
+    const int rows_valid = (int)((P.m - row0 < h) ? (P.m - row0) : h);
+    const double* Tg = st.t_leaf + leaf * np * np;
+    if (leaf != l0) {
+      // ---- T (A operand): row exponents, then fixed point into the M buffer
+      long long* Tfix = reinterpret_cast<long long*>(z.M);
+      for (int r = tid; r < 128; r += kThreads) z.expA[r] = 0;
+      __syncthreads();
+      for (int idx = tid; idx < np * np; idx += kThreads) atomicMax(&z.expA[idx >> 6], oz::bexp(__ldcg(Tg + idx)));
+      __syncthreads();
+      for (int idx = tid; idx < np * np; idx += kThreads)
+        Tfix[idx] = (long long)oz::to_fixed(__ldcg(Tg + idx), z.expA[idx >> 6]);
+      // ---- C (B operand): output column j, k-th entry C[k][j]
+      ozaki_b_slices(z, [&](int j, int k) { return z.C[k * kOzLd + j]; });
+      if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Tfix[r * 64 + k]; }, ph, st.status)) {
+        alive = false;
+        break;
+      }
+      // ---- M = T C  (M lives where Tfix was; every MMA reading the slices has completed)
+      ozaki_epilogue(z, tmem, np, [&](int i, int j, double v) { z.M[i * kOzLd + j] = v; });
+      for (int i = tid; i < np * np; i += kThreads) {
+        const int o = (i / np) * kOzLd + i % np;
+        z.C[o] -= z.M[o];
+      }
+      // ---- Y (A operand): TMA tile, row exponents, fixed point in place
+      if (!tile_load(z.Y, &mapV, z.bars, tma_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
+        alive = false;
+        break;
+      }
+      for (int r = tid; r < 128; r += kThreads) z.expA[r] = 0;
+      __syncthreads();
+      for (int idx = tid; idx < h * np; idx += kThreads)
+        atomicMax(&z.expA[idx >> 6], oz::bexp(*z.Y.ptr(idx >> 6, idx & 63)));
+      __syncthreads();
+      for (int idx = tid; idx < h * np; idx += kThreads) {
+        double* p = z.Y.ptr(idx >> 6, idx & 63);
+        *reinterpret_cast<uint64_t*>(p) = oz::to_fixed(*p, z.expA[idx >> 6]);
+      }
+      // ---- M (B operand): output column j, k-th entry M[k][j]
+      ozaki_b_slices(z, [&](int j, int k) { return z.M[k * kOzLd + j]; });
+      if (!ozaki_mma_pass(z, tmem, h, [&](int r, int k) { return *reinterpret_cast<const uint64_t*>(z.Y.ptr(r, k)); },
+                          ph, st.status)) {
+        alive = false;
+        break;
+      }
+      ozaki_epilogue(z, tmem, rows_valid, [&](int i, int j, double v) {
+        if (j < n) Q[(row0 + i) * ldq + j] = -v;
+      });
+    } else {
+      // ---- first leaf, native FP64: Q_rows = [C; 0] - V (T (V_top^T C))
+      double* T = reinterpret_cast<double*>(z.bsl);
+      double* X = T + np * np;
+      for (int i = tid; i < np * np; i += kThreads) T[i] = __ldcg(Tg + i);
+      if (!tile_load(z.Y, &mapV, z.bars, tma_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
+        alive = false;
+        break;
+      }
+      for (int o = tid; o < np * np; o += kThreads) {
+        const int a = o / np, b = o % np;
+        double v = 0.0;
+        if (a < n) {
+          v = z.C[a * kOzLd + b];
+          for (int r = a + 1; r < n; ++r) v = fma(*z.Y.ptr(r, a), z.C[r * kOzLd + b], v);
+        }
+        X[a * np + b] = v;
+      }
+      __syncthreads();
+      tri_mul<ArithF64>(T, np, X, np, z.M, kOzLd, n, np, np, false);
+      __syncthreads();
+      const int G = kThreads / np;
+      const int cown = tid & (np - 1), gown = tid / np;
+      if (cown < n) {
+        for (int r = gown; r < rows_valid; r += G) {
+          double acc = 0.0;
+          const int amax = (r < n) ? r : n;
+          for (int a = 0; a < amax; ++a) acc = fma(*z.Y.ptr(r, a), z.M[a * kOzLd + cown], acc);
+          if (r < n) acc += z.M[r * kOzLd + cown];
+          double v = -acc;
+          if (r < n) v += z.C[r * kOzLd + cown];
+          Q[(row0 + r) * ldq + cown] = v;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // every pass waits for its commits; after a timeout, give the MMAs in flight one more
+  // bounded wait before TMEM is freed
+  if (!alive && tid == 0) {
+    oz::wait_bar(z.bars + 1, ph[0]);
+    oz::wait_bar(z.bars + 2, ph[1]);
+  }
+  oz::fence_before_sync();
+  __syncthreads();
+  oz::fence_after_sync();
+  if (warp == 0) oz::tmem_dealloc(tmem, oz::kTmemCols);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -569,9 +859,30 @@ static cudaError_t launch_form_q_t(const CUtensorMap& mapV, const Plan& P, const
   return cudaGetLastError();
 }
 
+static cudaError_t launch_form_q_ozaki(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q,
+                                       int64_t ldq, int box_rows, cudaStream_t stream) {
+  const size_t smem_tree = formq_smem_bytes(P);
+  cudaError_t e =
+      cudaFuncSetAttribute(formq_tree_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tree);
+  if (e != cudaSuccess) return e;
+  for (int level = P.depth; level >= 1; --level) {
+    formq_tree_kernel<ArithF64><<<P.level_count[level], kThreads, smem_tree, stream>>>(P, st, level);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const size_t smem = formq_ozaki_smem_bytes(P);
+  e = cudaFuncSetAttribute(formq_ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  formq_ozaki_kernel<<<P.chains, kThreads, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+  return cudaGetLastError();
+}
+
+bool ozaki_form_q_applies(const Plan& P) { return P.precision == 2 && P.np == 64 && P.h <= 128; }
+
 cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,
                           int box_rows, cudaStream_t stream) {
   if (P.precision == 1) return launch_form_q_t<ArithDF>(mapV, P, st, Q, ldq, box_rows, stream);
+  if (ozaki_form_q_applies(P)) return launch_form_q_ozaki(mapV, P, st, Q, ldq, box_rows, stream);
   return launch_form_q_t<ArithF64>(mapV, P, st, Q, ldq, box_rows, stream);
 }
 

@@ -8,6 +8,8 @@ namespace tsqr {
 size_t factor_smem_bytes(const Plan& P);
 size_t formq_smem_bytes(const Plan& P);
 size_t apply_smem_bytes(const Plan& P, int kb);
+size_t formq_ozaki_smem_bytes(const Plan& P);
+bool ozaki_form_q_applies(const Plan& P);
 
 cudaError_t launch_stage_copy(const double* A, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
                               cudaStream_t stream);

@@ -1,0 +1,135 @@
+// FP64 products on the tensor cores by error-free splitting (the scheme of Ozaki, Ogita, Oishi
+// and Rump), for the compact-WY products of TSQR's thin-Q formation.
+//
+// Each FP64 operand row (A) or column (B) is written in fixed point against its largest
+// exponent: v = sign * mag * 2^(E_max - 1078) with mag < 2^56.  mag is cut into 8 slices of
+// 7 bits, c_1 (most significant) .. c_8, each an integer in [0, 127] held exactly in bf16 with
+// the sign of v.  Slice products c_s^A c_t^B are below 2^14; summed over K = 64 they stay below
+// 2^20, and the pairs of equal weight s + t = g (at most 8 of them) below 2^23, so one FP32
+// tensor-core accumulator per weight group g = 2..9 holds its sum exactly.  The epilogue
+// recombines the eight exact group sums in 64-bit integers,
+//   X = sum_{g<=8} G_g 2^(7(8-g)) + floor(G_9 / 2^7)   (|X| < 2^63),
+// and the FP64 product is X * 2^(E_A + E_B - 2100).  Pairs with s + t > 9 are left out: the
+// result is accurate to about 2^-50 relative to |A| |B| (row and column maxima), close to the
+// rounding of a native FP64 dot product of length 64.
+//
+// tcgen05 use: one thread issues kind::f16 MMAs (bf16 in, FP32 out, M = 128, N = 64, K = 16)
+// from 128-byte-swizzled K-major shared-memory operands; the eight group accumulators take all
+// 512 TMEM columns of the SM, so the kernel runs one block per SM.  Completion is signalled by
+// tcgen05.commit on an mbarrier; every wait on it is bounded.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tsqr {
+namespace oz {
+
+constexpr int kSlices = 8;        // 7-bit slices: 56 bits of each operand
+constexpr int kTmemCols = 512;    // 8 groups x 64 columns
+constexpr int kN = 64;            // N of every product (the padded column count)
+constexpr int kM = 128;           // M of every MMA (rows beyond the operand are zero)
+constexpr int kK = 64;            // K of every product
+constexpr uint32_t kASliceBytes = kM * kK * 2;  // 16 KB
+constexpr uint32_t kBSliceBytes = kN * kK * 2;  // 8 KB
+
+// ---- tcgen05 wrappers -------------------------------------------------------------------------
+// Shared-memory matrix descriptor of a K-major operand in 128-byte swizzled rows of 64 bf16:
+// 8-row groups 1024 bytes apart (SBO), descriptor version 1, swizzle mode 128B.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, M x N.
+__device__ __forceinline__ uint32_t idesc_bf16(uint32_t M, uint32_t N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t v[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- operand layout ---------------------------------------------------------------------------
+// Byte offset of element (row r, k) of a K-major bf16 operand with 64 k per 128-byte row and the
+// 128-byte swizzle (16-byte chunk index XOR row & 7); the operand base is 1024-byte aligned.
+__device__ __forceinline__ uint32_t op_off(int r, int k) {
+  const uint32_t byte = (uint32_t)k * 2u;
+  return (uint32_t)r * 128u + ((((byte >> 4) ^ ((uint32_t)r & 7u))) << 4) + (byte & 15u);
+}
+
+// ---- error-free splitting ----------------------------------------------------------------------
+// Biased exponent of v (0 for zero or subnormal).
+__device__ __forceinline__ int bexp(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+}
+// Fixed-point form against the row/column maximum biased exponent emax: bit 63 = sign,
+// bits 0..55 = mag with |v| = mag * 2^(emax - 1078) (truncated below 2^(emax - 1078)).
+__device__ __forceinline__ uint64_t to_fixed(double v, int emax) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return 0;
+  const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int d = E - emax + 3;  // <= 3
+  uint64_t mag;
+  if (d >= 0)
+    mag = m << d;
+  else
+    mag = (-d < 64) ? (m >> (-d)) : 0ull;
+  return (b & 0x8000000000000000ull) | mag;
+}
+// bf16 bits of slice s (1-based) of a fixed-point value: sign * ((mag >> (56 - 7 s)) & 127).
+__device__ __forceinline__ uint32_t slice_bf16(uint64_t fx, int s) {
+  const uint32_t c = (uint32_t)(fx >> (56 - 7 * s)) & 127u;
+  const uint32_t sign = (uint32_t)(fx >> 48) & 0x8000u;
+  if (c == 0) return 0;
+  const int p = 31 - __clz(c);  // 0..6
+  return sign | ((uint32_t)(127 + p) << 7) | ((c << (7 - p)) & 0x7Fu);
+}
+// X * 2^k as FP64 (X != 0 handled; k from E_A + E_B - 2100).
+__device__ __forceinline__ double scale_int(long long X, int k) {
+  if (X == 0) return 0.0;
+  const double d = (double)X;
+  const int E = (int)((__double_as_longlong(d) >> 52) & 0x7FF);
+  const int En = E + k;
+  if (En >= 1 && En <= 2046)
+    return __longlong_as_double(__double_as_longlong(d) + ((long long)k << 52));
+  return scalbn(d, k);
+}
+
+// Bounded wait on an mbarrier phase (thread-level); false on timeout.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_bounded(bar, parity, kWaitCycles);
+}
+
+}  // namespace oz
+}  // namespace tsqr

@@ -6,7 +6,8 @@ oracle's R when kappa(A) <= 1e6, where the sign-normalised thin QR is unique.  Q
 elementwise with a bound from QR perturbation theory: two backward-stable factorizations differ
 in Q by about kappa(A) * n * u, so the test allows 50 * kappa * n * u (at least 1e-13), with u
 the unit roundoff of the mode: 2^-53 for native FP64, 2^-46 for double-float (two FP32 halves
-with 24 + 24 significant bits, less the guard bits the sloppy sum gives up).
+with 24 + 24 significant bits, less the guard bits the sloppy sum gives up), 2^-50 for the
+Ozaki tensor-core products (56-bit fixed point per row/column, 9-term truncation).
 """
 import numpy as np
 import pytest
@@ -52,10 +53,10 @@ def run(T, A_h, lda=None, **opts):
     return f, f.R.cpu().numpy(), Q.cpu().numpy()
 
 
-UNIT = {0: 2.0 ** -53, 1: 2.0 ** -46}
+UNIT = {0: 2.0 ** -53, 1: 2.0 ** -46, 2: 2.0 ** -50}
 
 
-@pytest.fixture(params=[0, 1], ids=["f64", "df"])
+@pytest.fixture(params=[0, 1, 2], ids=["f64", "df", "ozaki"])
 def prec(request):
     return request.param
 
