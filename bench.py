@@ -303,6 +303,14 @@ def main():
             "ms_per_step": d_ms, "speedup_vs_f64": ms_step / d_ms,
             "kernel_ms": {k: statistics.mean(v) for k, v in dfm["ev"].items()},
             "backward_error": dfm["be"], "orthogonality": dfm["orth"]}
+        ozm = run_mode(2, args.steps, min(args.warmup, 3), False)
+        o_ms = ozm["ms"] / args.steps
+        forms["ozaki_wy"] = {
+            "precision": 2, "dtype": "f64+bf16x8-split", "value": per_step * world / (o_ms / 1e3) / 1e9,
+            "unit": "GFLOP/s", "ms_per_step": o_ms, "speedup_vs_f64": ms_step / o_ms,
+            "kernel_ms": {k: statistics.mean(v) for k, v in ozm["ev"].items()},
+            "backward_error": ozm["be"], "orthogonality": ozm["orth"],
+            "note": "native FP64 factor; thin-Q products T*C and Y*M on tcgen05 tensor cores as Ozaki splits"}
         opts = tsqr.Opts(precision=0)
 
     # end to end through the C-ABI with host buffers: H2D of A and b, D2H of R, Q and Q^T b

@@ -226,23 +226,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 //
 // Per chain leaf: M = T C and Q_rows = -Y M, each an Ozaki-split FP64 product (ozaki.cuh) of
 // 8 x 8 bf16 slice pairs on tcgen05 with exact FP32 accumulators in TMEM; C -= M in FP64.
-// The first leaf of a chain (V unit lower trapezoidal, one leaf in a chain) takes the native
-// FP64 route.  Needs np = 64 (33 <= n <= 64) and h <= 128.
+// The leaf's T arrives by a bulk copy and its reflector tile by TMA, both issued when the leaf
+// starts so that they overlap the T C product.  The first leaf of a chain (V unit lower
+// trapezoidal) takes the native FP64 route.  Needs np = 64 (33 <= n <= 64) and h <= 128.
+// 512 threads, one block per SM (all 512 TMEM columns).
+
+constexpr int kOzT = 512;
+static constexpr int kOzLd = 65;
 
 struct OzSmem {
   Tile Y;           // h x 64 FP64 leaf tile (TMA); converted in place to fixed point
   char* bsl;        // 8 B slices, 8 KB each; FP64 scratch (T, X) for the first leaf
   char* asl;        // 2 A slice buffers, 16 KB each
   double* C;        // 64 x 65
-  double* M;        // 64 x 65; fixed-point T (64 x 64 int64) before the T C product
+  double* M;        // 64 x 65; the leaf's T (64 x 64, bulk copy) then its fixed-point form
   int* expA;        // 128
   int* expB;        // 64
-  uint64_t* bars;   // 0: TMA, 1: A buffer 0, 2: A buffer 1
+  uint64_t* bars;   // 0: Y tile, 1: A buffer 0, 2: A buffer 1, 3: T
   uint32_t* slot;   // TMEM base address
   int* flag;
 };
-
-static constexpr int kOzLd = 65;
 
 __device__ inline OzSmem carve_ozaki(char* raw, int h) {
   OzSmem z;
@@ -267,9 +270,30 @@ size_t formq_ozaki_smem_bytes(const Plan& P) {
          16;
 }
 
-// One Ozaki product D (128 x 64) = A (a_rows x 64) B (64 x 64): the B slices must already be in
-// z.bsl; afix(r, k) gives the fixed-point A entries (rows < a_rows), z.expA / z.expB the
-// exponents.  The 8 group accumulators land in TMEM.  All threads call.  False on timeout.
+// bf16 bits of slices s of two fixed-point values, packed low|high: the 7-bit integer is made an
+// exact FP32 by the 2^23 magic add, whose upper 16 bits are its bf16 form.
+__device__ __forceinline__ uint32_t slice_pair(uint64_t f0, uint64_t f1, int s) {
+  const uint32_t c0 = (uint32_t)(f0 >> (56 - 7 * s)) & 127u;
+  const uint32_t c1 = (uint32_t)(f1 >> (56 - 7 * s)) & 127u;
+  const float x0 = __fsub_rn(__int_as_float(0x4B000000 | c0), 8388608.f);
+  const float x1 = __fsub_rn(__int_as_float(0x4B000000 | c1), 8388608.f);
+  const uint32_t sg = ((uint32_t)(f0 >> 48) & 0x8000u) | ((uint32_t)(f1 >> 32) & 0x80000000u);
+  return __byte_perm(__float_as_uint(x0), __float_as_uint(x1), 0x7632) | sg;
+}
+
+// Waits (thread 0, bounded) for a barrier phase; every thread learns the outcome.
+__device__ inline bool oz_wait_all(const OzSmem& z, uint64_t* bar, uint32_t parity, int* status) {
+  if (threadIdx.x == 0 && !oz::wait_bar(bar, parity)) {
+    atomicOr(status, kStatusTimeout);
+    *z.flag = 1;
+  }
+  __syncthreads();
+  return *z.flag == 0;
+}
+
+// One Ozaki product D (128 x 64) = A (a_rows x 64) B (64 x 64) into the 8 TMEM groups.  The B
+// slices must be in z.bsl and rows a_rows..127 of both A buffers zero; afix(r, k) gives the
+// fixed-point A entries.  All threads call.  False on timeout.
 template <class AFix>
 __device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows, AFix afix, uint32_t ph[2],
                                       int* status) {
@@ -278,55 +302,45 @@ __device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows
   for (int s = 1; s <= oz::kSlices; ++s) {
     const int b = (s - 1) & 1;
     if (s >= 3) {
-      if (tid == 0) {
-        if (!oz::wait_bar(z.bars + 1 + b, ph[b])) {
-          atomicOr(status, kStatusTimeout);
-          *z.flag = 1;
-        }
-        ph[b] ^= 1u;
-      }
-      __syncthreads();
-      if (*z.flag) return false;
+      const bool ok = oz_wait_all(z, z.bars + 1 + b, ph[b], status);
+      ph[b] ^= 1u;
+      if (!ok) return false;
     }
     char* abuf = z.asl + b * oz::kASliceBytes;
-    for (int idx = tid; idx < oz::kM * 32; idx += kThreads) {  // two k per thread: one 32-bit store
+    for (int idx = tid; idx < a_rows * 32; idx += kOzT) {  // two k per thread: one 32-bit store
       const int r = idx >> 5, k = (idx & 31) * 2;
-      uint32_t lo = 0, hi = 0;
-      if (r < a_rows) {
-        lo = oz::slice_bf16(afix(r, k), s);
-        hi = oz::slice_bf16(afix(r, k + 1), s);
-      }
-      *reinterpret_cast<uint32_t*>(abuf + oz::op_off(r, k)) = lo | (hi << 16);
+      *reinterpret_cast<uint32_t*>(abuf + oz::op_off(r, k)) = slice_pair(afix(r, k), afix(r, k + 1), s);
     }
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       oz::fence_after_sync();
-      const uint32_t a0 = smem_u32(abuf);
+      const uint64_t adesc = oz::sw128_desc(smem_u32(abuf));
       for (int t = 1; t <= oz::kSlices + 1 - s; ++t) {
         const uint32_t d = tmem + (uint32_t)(s + t - 2) * 64u;
-        const uint32_t b0 = smem_u32(z.bsl + (t - 1) * oz::kBSliceBytes);
+        const uint64_t bdesc = oz::sw128_desc(smem_u32(z.bsl + (t - 1) * oz::kBSliceBytes));
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          oz::mma_bf16(d, oz::sw128_desc(a0 + kk * 32), oz::sw128_desc(b0 + kk * 32), idesc,
-                       (s > 1 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < 4; ++kk)  // K step of 16 bf16 = 32 bytes = 2 descriptor units
+          oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (s > 1 || kk > 0) ? 1u : 0u);
       }
       oz::mma_commit(z.bars + 1 + b);
     }
   }
-  if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
-      if (!oz::wait_bar(z.bars + 1 + b, ph[b])) {
-        atomicOr(status, kStatusTimeout);
-        *z.flag = 1;
-      }
-      ph[b] ^= 1u;
-    }
-  }
-  oz::fence_before_sync();
-  __syncthreads();
+  bool ok = oz_wait_all(z, z.bars + 1, ph[0], status);
+  ph[0] ^= 1u;
+  ok = oz_wait_all(z, z.bars + 2, ph[1], status) && ok;
+  ph[1] ^= 1u;
   oz::fence_after_sync();
-  return *z.flag == 0;
+  return ok;
+}
+
+// Rows r0..r1-1 of both A buffers set to zero (the MMA reads all 128 rows).
+__device__ inline void ozaki_zero_a_rows(const OzSmem& z, int r0, int r1) {
+  for (int i = threadIdx.x; i < 2 * (r1 - r0) * 8; i += kOzT) {
+    const int b = i / ((r1 - r0) * 8), rem = i % ((r1 - r0) * 8);
+    *reinterpret_cast<uint4*>(z.asl + b * oz::kASliceBytes + (size_t)(r0 + rem / 8) * 128 + (rem % 8) * 16) =
+        make_uint4(0, 0, 0, 0);
+  }
 }
 
 // B slices of the 64 x 64 matrix whose output column j and k-th entry is bval(j, k), against the
@@ -334,56 +348,69 @@ __device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows
 template <class BVal>
 __device__ inline void ozaki_b_slices(const OzSmem& z, BVal bval) {
   const int tid = threadIdx.x;
-  for (int j = tid; j < 64; j += kThreads) z.expB[j] = 0;
+  for (int j = tid; j < 64; j += kOzT) z.expB[j] = 0;
   __syncthreads();
-  for (int idx = tid; idx < 64 * 64; idx += kThreads) atomicMax(&z.expB[idx >> 6], oz::bexp(bval(idx >> 6, idx & 63)));
+  for (int idx = tid; idx < 64 * 64; idx += kOzT) atomicMax(&z.expB[idx >> 6], oz::bexp(bval(idx >> 6, idx & 63)));
   __syncthreads();
-  for (int idx = tid; idx < 64 * 32; idx += kThreads) {
+  for (int idx = tid; idx < 64 * 32; idx += kOzT) {
     const int j = idx >> 5, k = (idx & 31) * 2;
     const uint64_t f0 = oz::to_fixed(bval(j, k), z.expB[j]);
     const uint64_t f1 = oz::to_fixed(bval(j, k + 1), z.expB[j]);
 #pragma unroll
     for (int s = 1; s <= oz::kSlices; ++s)
-      *reinterpret_cast<uint32_t*>(z.bsl + (s - 1) * oz::kBSliceBytes + oz::op_off(j, k)) =
-          oz::slice_bf16(f0, s) | (oz::slice_bf16(f1, s) << 16);
+      *reinterpret_cast<uint32_t*>(z.bsl + (s - 1) * oz::kBSliceBytes + oz::op_off(j, k)) = slice_pair(f0, f1, s);
   }
   fence_proxy_async_smem();
   __syncthreads();
 }
 
-// Reads the 8 group accumulators back: out(i, j, value) for rows i < rows and all 64 columns,
-// value = sum of the product's exact slice groups, rescaled to FP64.
+// Reads the 8 group accumulators back: out(i, j, value) for rows i < rows and all 64 columns.
+// Warp w reads TMEM lanes 32 (w & 3).. and columns 16 (w >> 2)..; warps without valid rows skip.
 template <class Out>
 __device__ inline void ozaki_epilogue(const OzSmem& z, uint32_t tmem, int rows, Out out) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int i = 32 * (warp & 3) + lane;
-  const int c0 = 32 * (warp >> 2);
-  const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
-  long long acc[32];
+  const int sp = warp & 3;
+  const int i = 32 * sp + lane;
+  const int c0 = 16 * (warp >> 2);
+  if (32 * sp < rows) {
+    const uint32_t tb = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)c0;
+    long long acc[16];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) acc[c] = 0;
+    for (int c = 0; c < 16; ++c) acc[c] = 0;
 #pragma unroll 1
-  for (int g = 2; g <= oz::kSlices + 1; ++g) {
-    uint32_t v[32];
-    oz::tmem_ld32(tb + (uint32_t)(g - 2) * 64u, v);
-    oz::tmem_wait_ld();
+    for (int g = 2; g <= oz::kSlices + 1; ++g) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+            "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tb + (uint32_t)(g - 2) * 64u));
+      oz::tmem_wait_ld();
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      const long long G = (long long)__float2int_rn(__uint_as_float(v[c]));
-      acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
+      for (int c = 0; c < 16; ++c) {
+        const long long G = (long long)__float2int_rn(__uint_as_float(v[c]));
+        acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
+      }
     }
-  }
-  if (i < rows) {
-    const int ea = z.expA[i];
+    if (i < rows) {
+      const int ea = z.expA[i];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) out(i, c0 + c, oz::scale_int(acc[c], ea + z.expB[c0 + c] - 2100));
+      for (int c = 0; c < 16; ++c) out(i, c0 + c, oz::scale_int(acc[c], ea + z.expB[c0 + c] - 2100));
+    }
   }
   oz::fence_before_sync();
   __syncthreads();
   oz::fence_after_sync();
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kOzT, 1)
     formq_ozaki_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
                        int64_t ldq, int box_rows) {
   extern __shared__ char smem_raw[];
@@ -392,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int np = 64, n = P.n, h = P.h;
   const int g = blockIdx.x;
   if (tid == 0) {
-    for (int b = 0; b < 3; ++b) mbar_init(z.bars + b, 1);
+    for (int b = 0; b < 4; ++b) mbar_init(z.bars + b, 1);
     fence_mbar_init();
     *z.flag = 0;
   }
@@ -402,9 +429,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   oz::fence_after_sync();
   const uint32_t tmem = *z.slot;
   uint32_t ph[2] = {0u, 0u};
-  uint32_t tma_phase = 0;
+  uint32_t y_phase = 0, t_phase = 0;
   // C = this chain's block of Q_tree [D; 0]
-  for (int i = tid; i < np * np; i += kThreads) {
+  for (int i = tid; i < np * np; i += kOzT) {
     const int a = i / np, b = i % np;
     z.C[a * kOzLd + b] = (P.depth == 0) ? ((a == b && a < n) ? __ldcg(st.signs + a) : 0.0)
                                         : __ldcg(st.node_r + (size_t)g * np * np + i);
@@ -417,42 +444,69 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int rows_valid = (int)((P.m - row0 < h) ? (P.m - row0) : h);
     const double* Tg = st.t_leaf + leaf * np * np;
     if (leaf != l0) {
-      // ---- T (A operand): row exponents, then fixed point into the M buffer
-      long long* Tfix = reinterpret_cast<long long*>(z.M);
-      for (int r = tid; r < 128; r += kThreads) z.expA[r] = 0;
+      // ---- both loads of the leaf start now: T into the M buffer, the reflector tile into Y
+      fence_proxy_async_smem();
       __syncthreads();
-      for (int idx = tid; idx < np * np; idx += kThreads) atomicMax(&z.expA[idx >> 6], oz::bexp(__ldcg(Tg + idx)));
-      __syncthreads();
-      for (int idx = tid; idx < np * np; idx += kThreads)
-        Tfix[idx] = (long long)oz::to_fixed(__ldcg(Tg + idx), z.expA[idx >> 6]);
+      if (tid == 0) {
+        mbar_arrive_expect_tx(z.bars + 3, np * np * 8);
+        bulk_load(z.M, Tg, np * np * 8, z.bars + 3);
+        mbar_arrive_expect_tx(z.bars + 0, (uint32_t)h * np * 8);
+        for (int pnl = 0; pnl < np / 16; ++pnl)
+          for (int r = 0; r < h; r += box_rows)
+            tma_load_2d(z.Y.base + (size_t)pnl * h * 128 + (size_t)r * 128, &mapV, z.bars + 0, pnl * 16,
+                        (int)(row0 + r));
+      }
       // ---- C (B operand): output column j, k-th entry C[k][j]
       ozaki_b_slices(z, [&](int j, int k) { return z.C[k * kOzLd + j]; });
+      ozaki_zero_a_rows(z, np, oz::kM);
+      // ---- T (A operand): row exponents, then fixed point in place
+      {
+        const bool ok = oz_wait_all(z, z.bars + 3, t_phase, st.status);
+        t_phase ^= 1u;
+        if (!ok) {
+          alive = false;
+          break;
+        }
+      }
+      long long* Tfix = reinterpret_cast<long long*>(z.M);
+      for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
+      __syncthreads();
+      for (int idx = tid; idx < np * np; idx += kOzT) atomicMax(&z.expA[idx >> 6], oz::bexp(z.M[idx]));
+      __syncthreads();
+      for (int idx = tid; idx < np * np; idx += kOzT) Tfix[idx] = (long long)oz::to_fixed(z.M[idx], z.expA[idx >> 6]);
+      __syncthreads();
       if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Tfix[r * 64 + k]; }, ph, st.status)) {
         alive = false;
         break;
       }
-      // ---- M = T C  (M lives where Tfix was; every MMA reading the slices has completed)
+      // ---- M = T C (M takes the buffer of Tfix; every MMA reading it has completed)
       ozaki_epilogue(z, tmem, np, [&](int i, int j, double v) { z.M[i * kOzLd + j] = v; });
-      for (int i = tid; i < np * np; i += kThreads) {
+      for (int i = tid; i < np * np; i += kOzT) {
         const int o = (i / np) * kOzLd + i % np;
         z.C[o] -= z.M[o];
       }
-      // ---- Y (A operand): TMA tile, row exponents, fixed point in place
-      if (!tile_load(z.Y, &mapV, z.bars, tma_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
-        alive = false;
-        break;
+      // ---- M (B operand): output column j, k-th entry M[k][j]
+      ozaki_b_slices(z, [&](int j, int k) { return z.M[k * kOzLd + j]; });
+      if (h < oz::kM) ozaki_zero_a_rows(z, h, oz::kM);
+      // ---- Y (A operand): row exponents, fixed point in place
+      {
+        const bool ok = oz_wait_all(z, z.bars + 0, y_phase, st.status);
+        y_phase ^= 1u;
+        if (!ok) {
+          alive = false;
+          break;
+        }
       }
-      for (int r = tid; r < 128; r += kThreads) z.expA[r] = 0;
+      for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
       __syncthreads();
-      for (int idx = tid; idx < h * np; idx += kThreads)
+      for (int idx = tid; idx < h * np; idx += kOzT)
         atomicMax(&z.expA[idx >> 6], oz::bexp(*z.Y.ptr(idx >> 6, idx & 63)));
       __syncthreads();
-      for (int idx = tid; idx < h * np; idx += kThreads) {
+      for (int idx = tid; idx < h * np; idx += kOzT) {
         double* p = z.Y.ptr(idx >> 6, idx & 63);
         *reinterpret_cast<uint64_t*>(p) = oz::to_fixed(*p, z.expA[idx >> 6]);
       }
-      // ---- M (B operand): output column j, k-th entry M[k][j]
-      ozaki_b_slices(z, [&](int j, int k) { return z.M[k * kOzLd + j]; });
+      __syncthreads();
       if (!ozaki_mma_pass(z, tmem, h, [&](int r, int k) { return *reinterpret_cast<const uint64_t*>(z.Y.ptr(r, k)); },
                           ph, st.status)) {
         alive = false;
@@ -465,12 +519,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- first leaf, native FP64: Q_rows = [C; 0] - V (T (V_top^T C))
       double* T = reinterpret_cast<double*>(z.bsl);
       double* X = T + np * np;
-      for (int i = tid; i < np * np; i += kThreads) T[i] = __ldcg(Tg + i);
-      if (!tile_load(z.Y, &mapV, z.bars, tma_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
+      for (int i = tid; i < np * np; i += kOzT) T[i] = __ldcg(Tg + i);
+      if (!tile_load(z.Y, &mapV, z.bars, y_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
         alive = false;
         break;
       }
-      for (int o = tid; o < np * np; o += kThreads) {
+      for (int o = tid; o < np * np; o += kOzT) {
         const int a = o / np, b = o % np;
         double v = 0.0;
         if (a < n) {
@@ -480,9 +534,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         X[a * np + b] = v;
       }
       __syncthreads();
-      tri_mul<ArithF64>(T, np, X, np, z.M, kOzLd, n, np, np, false);
+      for (int o = tid; o < np * np; o += kOzT) {  // M = T X, T upper triangular
+        const int a = o / np, b = o % np;
+        double v = 0.0;
+        for (int p = a; p < n; ++p) v = fma(T[a * np + p], X[p * np + b], v);
+        z.M[a * kOzLd + b] = v;
+      }
       __syncthreads();
-      const int G = kThreads / np;
+      const int G = kOzT / np;
       const int cown = tid & (np - 1), gown = tid / np;
       if (cown < n) {
         for (int r = gown; r < rows_valid; r += G) {
@@ -498,11 +557,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
     }
   }
-  // every pass waits for its commits; after a timeout, give the MMAs in flight one more
-  // bounded wait before TMEM is freed
+  // every pass waits for its commits; after a timeout, give the copies and MMAs in flight one
+  // more bounded wait before TMEM is freed
   if (!alive && tid == 0) {
     oz::wait_bar(z.bars + 1, ph[0]);
     oz::wait_bar(z.bars + 2, ph[1]);
+    oz::wait_bar(z.bars + 0, y_phase);
+    oz::wait_bar(z.bars + 3, t_phase);
   }
   oz::fence_before_sync();
   __syncthreads();
@@ -873,7 +934,7 @@ static cudaError_t launch_form_q_ozaki(const CUtensorMap& mapV, const Plan& P, c
   const size_t smem = formq_ozaki_smem_bytes(P);
   e = cudaFuncSetAttribute(formq_ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  formq_ozaki_kernel<<<P.chains, kThreads, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+  formq_ozaki_kernel<<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
   return cudaGetLastError();
 }
 
