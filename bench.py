@@ -152,6 +152,87 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
+    """512 matrices: m log-uniform in [1e4, 2^18], n from {8, 16, 32, 64}, N(0,1) entries from
+    per-matrix seeds (generated on the device).  Times factor + thin Q of all of them: one batched
+    launch sequence replayed from a CUDA graph, and a loop of single-matrix calls."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    ms = np.floor(np.exp(rng.uniform(np.log(1e4), np.log(2.0 ** 18), count))).astype(np.int64)
+    ns = rng.choice([8, 16, 32, 64], count)
+    mats = []
+    for i in range(count):
+        g = torch.Generator(device=dev).manual_seed(seed + i)
+        mats.append(torch.randn((int(ms[i]), int(ns[i])), dtype=torch.float64, device=dev, generator=g))
+    fl = float(sum(4.0 * m_ * n_ * n_ - 4.0 * n_ ** 3 / 3 for m_, n_ in zip(ms, ns)))
+    b = tsqr.Batch(mats)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            b.factor()
+            b.form_q()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.factor()
+        b.form_q()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batched = e0.elapsed_time(e1) / steps
+    ok = b.status() == tsqr.TSQR_OK
+    # accuracy of the largest matrix of the batch
+    big = int(np.argmax(ms))
+    A, Q, R = mats[big], b.Q[big], b.R[big]
+    be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
+    orth = torch.linalg.norm(torch.eye(int(ns[big]), dtype=torch.float64, device=dev) - Q.T @ Q).item()
+    b.close()
+    # the same work as a loop of single-matrix launches (workspaces and outputs preallocated)
+    items = []
+    for A in mats:
+        m_, n_ = A.shape
+        o = tsqr.Opts()
+        nb = tsqr.tsqr_workspace_size(tsqr.TSQR_F64, m_, n_, o)
+        items.append((A, torch.empty(nb, dtype=torch.uint8, device=dev), nb,
+                      torch.empty((n_, n_), dtype=torch.float64, device=dev),
+                      torch.empty((m_, n_), dtype=torch.float64, device=dev), o))
+
+    def loop():
+        for A, w, nb, R_, Q_, o in items:
+            m_, n_ = A.shape
+            h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m_, n_, A.data_ptr(), n_, R_.data_ptr(), n_,
+                                 w.data_ptr(), nb, o, sptr)
+            tsqr.tsqr_form_q(h, Q_.data_ptr(), n_, sptr)
+            tsqr.tsqr_destroy(h)
+
+    loop()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        loop()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1) / steps
+    del items
+    return {"matrices": count, "elements": int(sum(int(m_) * int(n_) for m_, n_ in zip(ms, ns))),
+            "workload": "m log-uniform in [1e4, 2^18], n in {8,16,32,64}, N(0,1), fp64, factor + thin Q",
+            "value": fl / (ms_batched / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms_batched,
+            "launch": "one factor launch + one thin-Q launch per tree depth + one chain launch, CUDA graph",
+            "loop_value": fl / (ms_loop / 1e3) / 1e9, "loop_ms_per_step": ms_loop,
+            "speedup_vs_loop": ms_loop / ms_batched, "status_ok": ok,
+            "largest": {"m": int(ms[big]), "n": int(ns[big]), "backward_error": be, "orthogonality": orth}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,7 +245,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=1 << 17, help="oracle rows of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip timing the double-float precision form")
+    ap.add_argument("--no-forms", action="store_true", help="skip timing the precision forms")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-matrix batched workload")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -313,6 +395,11 @@ def main():
             "note": "native FP64 factor; thin-Q products T*C and Y*M on tcgen05 tensor cores as Ozaki splits"}
         opts = tsqr.Opts(precision=0)
 
+    # batched TSQR: 512 uneven matrices in one persistent launch (CUDA graph) vs a per-matrix loop
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = run_batched(tsqr, torch, dev, stream, sptr, args)
+
     # end to end through the C-ABI with host buffers: H2D of A and b, D2H of R, Q and Q^T b
     e2e = None
     if not args.no_e2e:
@@ -359,7 +446,7 @@ def main():
                           "parallelism": "replicas" if world > 1 else "single-gpu"},
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
-               "roofline": roofline, "precision_forms": forms, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roofline, "precision_forms": forms, "batched": batched, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": 3 * args.steps, "clocks": clocks}
         print(json.dumps(out), flush=True)
     if dist:

@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct tsqr_handle_s* tsqr_handle_t; /* opaque; owns no device memory */
+typedef struct tsqr_batch_s* tsqr_batch_t;   /* opaque batch of factorizations; owns no device memory */
 typedef void* tsqr_stream_t;                  /* a cudaStream_t */
 
 typedef enum {
@@ -124,6 +125,29 @@ tsqr_status_t tsqr_status_poll(tsqr_handle_t h, tsqr_stream_t stream);
 
 /* Fills *info with the plan and workspace pointers of h. */
 tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info);
+
+/* ---- Batches: many independent tall-skinny factorizations in one launch --------------------
+ * The s-step and block Krylov uses of TSQR (Sec. 1) produce many small tall-skinny blocks; a
+ * batch factors all of them with one persistent launch of the factorization kernel (every
+ * chain of every matrix is one block) and forms their thin Q factors with one launch per tree
+ * depth plus one chain launch.  All arrays below are host arrays of `count` entries; matrices
+ * follow the conventions of tsqr_factor (A is read only; inplace is not supported).
+ * tsqr_batch_factor and tsqr_batch_form_q only enqueue kernels and memsets on `stream`, so a
+ * CUDA graph can capture them once and replay them; tsqr_batch_create plans the batch, uploads
+ * its descriptors into the workspace and synchronises `stream` once. */
+tsqr_status_t tsqr_batch_workspace_size(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
+                                        const tsqr_opts_t* opts, size_t* bytes);
+/* dQ / ldq may be NULL (no thin Q); otherwise dQ[i] is m[i] x n[i] with ldq[i] >= n[i]. */
+tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
+                                void* const* dA, const int64_t* lda, void* const* dR, const int64_t* ldr,
+                                void* const* dQ, const int64_t* ldq, void* dWork, size_t work_bytes,
+                                const tsqr_opts_t* opts, tsqr_stream_t stream, tsqr_batch_t* out);
+/* R of every matrix (Algorithms 1 and 2 per matrix). */
+tsqr_status_t tsqr_batch_factor(tsqr_batch_t b, tsqr_stream_t stream);
+/* Thin Q of every matrix (after tsqr_batch_factor). */
+tsqr_status_t tsqr_batch_form_q(tsqr_batch_t b, tsqr_stream_t stream);
+tsqr_status_t tsqr_batch_status_poll(tsqr_batch_t b, tsqr_stream_t stream);
+tsqr_status_t tsqr_batch_destroy(tsqr_batch_t b);
 
 /* R only, with no workspace and no allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc or hand the library a workspace, such as code

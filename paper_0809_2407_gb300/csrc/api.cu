@@ -5,14 +5,38 @@
 
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/tsqr.h"
 #include "factor_kernels.h"
 
 using tsqr::Plan;
 using tsqr::Store;
+
+struct tsqr_batch_s {
+  int count = 0, precision = 0;
+  int total_chains = 0, max_depth = 0;
+  size_t smem_factor = 0, smem_formq = 0;
+  tsqr::BatchItem* d_items = nullptr;
+  tsqr::BatchWork* d_chain_work = nullptr;
+  std::vector<const tsqr::BatchWork*> d_level_work;
+  std::vector<int> level_blocks;
+  int* d_counters = nullptr;
+  size_t counters_bytes = 0;
+  int* d_status = nullptr;
+  bool has_q = false;
+  struct Stage {
+    const double* A;
+    int64_t lda;
+    double* V;
+    int64_t ldv, m;
+    int n;
+  };
+  std::vector<Stage> stages;
+};
 
 struct tsqr_handle_s {
   Plan P;
@@ -353,6 +377,251 @@ tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info) {
 
 tsqr_status_t tsqr_destroy(tsqr_handle_t h) {
   delete h;
+  return TSQR_OK;
+}
+
+}  // extern "C"
+
+
+// ---------------------------------------------------------------------------------------------
+// Batches: many independent factorizations in one launch (plans, workspace layout, descriptors).
+namespace {
+
+struct BatchPlan {
+  std::vector<Plan> plans;
+  std::vector<Layout> layouts;
+  std::vector<size_t> item_off;
+  size_t items_off = 0, chain_work_off = 0, level_work_off = 0, counters_off = 0, status_off = 0, total = 0;
+  int total_chains = 0, max_depth = 0, level_items = 0;
+  size_t counters_bytes = 0;
+};
+
+tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n, const tsqr_opts_t* opts,
+                              BatchPlan* bp) {
+  if (count < 1) return fail(TSQR_ERR_INVALID_ARG, "count must be >= 1");
+  if (!m || !n) return fail(TSQR_ERR_INVALID_ARG, "m and n arrays must be non-NULL");
+  tsqr_opts_t base{};
+  if (opts) base = *opts;
+  if (base.inplace) return fail(TSQR_ERR_UNSUPPORTED, "batches keep A read-only (inplace is not supported)");
+  if (base.precision == 2) base.precision = 0;  // batched thin Q uses the FP64 kernels
+  // shared chain length: about 16 waves of two blocks per SM over the whole batch; double-float
+  // keeps chains of at most 18 leaves (its orthogonality grows with chain length)
+  tsqr_opts_t probe = base;
+  probe.chain = 1;
+  int64_t total_leaves = 0;
+  for (int i = 0; i < count; ++i) {
+    Plan P;
+    tsqr_status_t s = make_plan(m[i], n[i], &probe, &P);
+    if (s != TSQR_OK) return fail(s, "batch item " + std::to_string(i) + ": " + g_last_error);
+    total_leaves += P.leaves;
+  }
+  if (base.chain == 0) {
+    const int64_t blocks = 16LL * 2 * device_sms();
+    int64_t c = (total_leaves + blocks - 1) / blocks;
+    if (c < 1) c = 1;
+    if (base.precision == 1 && c > 18) c = 18;
+    base.chain = (int32_t)c;
+  }
+  bp->plans.resize(count);
+  bp->layouts.resize(count);
+  bp->item_off.resize(count);
+  for (int i = 0; i < count; ++i) {
+    tsqr_status_t s = make_plan(m[i], n[i], &base, &bp->plans[i]);
+    if (s != TSQR_OK) return fail(s, "batch item " + std::to_string(i) + ": " + g_last_error);
+    bp->layouts[i] = make_layout(bp->plans[i], false);
+    bp->total_chains += bp->plans[i].chains;
+    bp->max_depth = std::max(bp->max_depth, bp->plans[i].depth);
+    bp->level_items += bp->plans[i].tree_nodes;
+    bp->counters_bytes += sizeof(int) * (size_t)(bp->plans[i].tree_nodes > 0 ? bp->plans[i].tree_nodes : 1);
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  bp->status_off = take(256);
+  bp->items_off = take(sizeof(tsqr::BatchItem) * (size_t)count);
+  bp->chain_work_off = take(sizeof(tsqr::BatchWork) * (size_t)bp->total_chains);
+  bp->level_work_off = take(sizeof(tsqr::BatchWork) * (size_t)(bp->level_items > 0 ? bp->level_items : 1));
+  bp->counters_off = take(bp->counters_bytes);
+  for (int i = 0; i < count; ++i) bp->item_off[i] = take(bp->layouts[i].total);
+  bp->total = off;
+  return TSQR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tsqr_status_t tsqr_batch_workspace_size(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
+                                        const tsqr_opts_t* opts, size_t* bytes) {
+  if (!bytes) return fail(TSQR_ERR_INVALID_ARG, "bytes is NULL");
+  if (dtype != TSQR_F64) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_F64 is implemented");
+  BatchPlan bp;
+  tsqr_status_t s = make_batch_plan(count, m, n, opts, &bp);
+  if (s != TSQR_OK) return s;
+  *bytes = bp.total;
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
+                                void* const* dA, const int64_t* lda, void* const* dR, const int64_t* ldr,
+                                void* const* dQ, const int64_t* ldq, void* dWork, size_t work_bytes,
+                                const tsqr_opts_t* opts, tsqr_stream_t stream, tsqr_batch_t* out) {
+  if (!out) return fail(TSQR_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (dtype != TSQR_F64) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_F64 is implemented");
+  if (!dA || !lda || !dR || !ldr) return fail(TSQR_ERR_INVALID_ARG, "A, lda, R and ldr arrays must be non-NULL");
+  if (dQ && !ldq) return fail(TSQR_ERR_INVALID_ARG, "ldq array must be given with Q");
+  BatchPlan bp;
+  tsqr_status_t s = make_batch_plan(count, m, n, opts, &bp);
+  if (s != TSQR_OK) return s;
+  if (!dWork || work_bytes < bp.total)
+    return fail(TSQR_ERR_WORKSPACE, "batch workspace needs " + std::to_string(bp.total) + " bytes");
+  if ((reinterpret_cast<uintptr_t>(dWork) & 255) != 0) return fail(TSQR_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  char* w = static_cast<char*>(dWork);
+  tsqr_batch_s* b = new (std::nothrow) tsqr_batch_s;
+  if (!b) return fail(TSQR_ERR_INVALID_ARG, "out of host memory");
+  b->count = count;
+  b->precision = bp.plans[0].precision;
+  b->total_chains = bp.total_chains;
+  b->max_depth = bp.max_depth;
+  b->d_status = reinterpret_cast<int*>(w + bp.status_off);
+  b->d_items = reinterpret_cast<tsqr::BatchItem*>(w + bp.items_off);
+  b->d_chain_work = reinterpret_cast<tsqr::BatchWork*>(w + bp.chain_work_off);
+  b->d_counters = reinterpret_cast<int*>(w + bp.counters_off);
+  b->counters_bytes = bp.counters_bytes;
+  b->has_q = dQ != nullptr;
+  std::vector<tsqr::BatchItem> items(count);
+  std::vector<tsqr::BatchWork> chain_work;
+  chain_work.reserve(bp.total_chains);
+  size_t counter_ints = 0;
+  for (int i = 0; i < count; ++i) {
+    const Plan& P = bp.plans[i];
+    const Layout& L = bp.layouts[i];
+    if (!dA[i] || !dR[i] || (dQ && !dQ[i])) {
+      delete b;
+      return fail(TSQR_ERR_INVALID_ARG, "batch item " + std::to_string(i) + ": NULL matrix pointer");
+    }
+    if (lda[i] < n[i] || ldr[i] < n[i] || (dQ && ldq[i] < n[i]) ||
+        (reinterpret_cast<uintptr_t>(dA[i]) & 7) != 0) {
+      delete b;
+      return fail(TSQR_ERR_INVALID_ARG, "batch item " + std::to_string(i) + ": bad leading dimension or alignment");
+    }
+    char* wi = w + bp.item_off[i];
+    tsqr::BatchItem& it = items[i];
+    std::memset(&it, 0, sizeof(it));
+    it.plan = P;
+    Store& st = it.store;
+    st.v = reinterpret_cast<double*>(wi + L.v);
+    st.ldv = L.ldv;
+    st.tau_leaf = reinterpret_cast<double*>(wi + L.tau_leaf);
+    st.t_leaf = reinterpret_cast<double*>(wi + L.t_leaf);
+    st.node_r = reinterpret_cast<double*>(wi + L.node_r);
+    st.node_y = reinterpret_cast<double*>(wi + L.node_y);
+    st.node_tau = reinterpret_cast<double*>(wi + L.node_tau);
+    st.node_t = reinterpret_cast<double*>(wi + L.node_t);
+    st.signs = reinterpret_cast<double*>(wi + L.signs);
+    st.counters = b->d_counters + counter_ints;
+    counter_ints += (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1);
+    st.status = b->d_status;
+    it.R = static_cast<double*>(dR[i]);
+    it.ldr = ldr[i];
+    it.Q = dQ ? static_cast<double*>(dQ[i]) : nullptr;
+    it.ldq = dQ ? ldq[i] : 0;
+    it.box_rows = P.h < 256 ? P.h : 256;
+    const bool stage = (lda[i] % 2 != 0) || !aligned16(dA[i]);
+    if ((s = make_map(&it.mapV, st.v, m[i], n[i], st.ldv, it.box_rows)) != TSQR_OK) {
+      delete b;
+      return s;
+    }
+    if (stage) {
+      it.mapA = it.mapV;
+      b->stages.push_back({static_cast<const double*>(dA[i]), lda[i], st.v, st.ldv, m[i], (int)n[i]});
+    } else if ((s = make_map(&it.mapA, dA[i], m[i], n[i], lda[i], it.box_rows)) != TSQR_OK) {
+      delete b;
+      return s;
+    }
+    b->smem_factor = std::max(b->smem_factor, tsqr::factor_smem_bytes(P));
+    b->smem_formq = std::max(b->smem_formq, tsqr::formq_smem_bytes(P));
+    for (int g = 0; g < P.chains; ++g) chain_work.push_back({i, g, 0});
+  }
+  // tree steps of the batched thin Q, by distance d from each item's root
+  std::vector<std::vector<tsqr::BatchWork>> levels(bp.max_depth);
+  for (int i = 0; i < count; ++i) {
+    const Plan& P = bp.plans[i];
+    for (int d = 0; d < P.depth; ++d) {
+      const int level = P.depth - d;
+      for (int node = 0; node < P.level_count[level]; ++node) levels[d].push_back({i, node, level});
+    }
+  }
+  std::vector<tsqr::BatchWork> level_flat;
+  std::vector<size_t> level_start;
+  for (int d = 0; d < bp.max_depth; ++d) {
+    level_start.push_back(level_flat.size());
+    b->level_blocks.push_back((int)levels[d].size());
+    level_flat.insert(level_flat.end(), levels[d].begin(), levels[d].end());
+  }
+  tsqr::BatchWork* d_levels = reinterpret_cast<tsqr::BatchWork*>(w + bp.level_work_off);
+  for (int d = 0; d < bp.max_depth; ++d) b->d_level_work.push_back(d_levels + level_start[d]);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(tsqr::BatchItem) * count, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_chain_work, chain_work.data(), sizeof(tsqr::BatchWork) * chain_work.size(),
+                        cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && !level_flat.empty())
+    e = cudaMemcpyAsync(d_levels, level_flat.data(), sizeof(tsqr::BatchWork) * level_flat.size(),
+                        cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);  // the host arrays above are about to go away
+  if (e == cudaSuccess) e = tsqr::prepare_factor_batched(b->precision, b->smem_factor);
+  if (e == cudaSuccess) e = tsqr::prepare_form_q_batched(b->precision, b->smem_formq);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch descriptor upload");
+  }
+  *out = b;
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_batch_factor(tsqr_batch_t b, tsqr_stream_t stream) {
+  if (!b) return fail(TSQR_ERR_INVALID_ARG, "batch is NULL");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(b->d_status, 0, sizeof(int), cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, b->counters_bytes, cs);
+  for (size_t k = 0; e == cudaSuccess && k < b->stages.size(); ++k) {
+    const auto& sg = b->stages[k];
+    e = tsqr::launch_stage_copy(sg.A, sg.lda, sg.V, sg.ldv, sg.m, sg.n, cs);
+  }
+  if (e == cudaSuccess)
+    e = tsqr::launch_factor_batched(b->d_items, b->d_chain_work, b->total_chains, b->precision, b->smem_factor, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "batched factor launch");
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_batch_form_q(tsqr_batch_t b, tsqr_stream_t stream) {
+  if (!b) return fail(TSQR_ERR_INVALID_ARG, "batch is NULL");
+  if (!b->has_q) return fail(TSQR_ERR_INVALID_ARG, "the batch was created without Q outputs");
+  cudaError_t e = tsqr::launch_form_q_batched(b->d_items, b->d_chain_work, b->total_chains, b->d_level_work.data(),
+                                              b->level_blocks.data(), b->max_depth, b->precision, b->smem_formq,
+                                              static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "batched form_q launch");
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_batch_status_poll(tsqr_batch_t b, tsqr_stream_t stream) {
+  if (!b) return fail(TSQR_ERR_INVALID_ARG, "batch is NULL");
+  int v = 0;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (v & tsqr::kStatusTimeout) return fail(TSQR_ERR_TIMEOUT, "a device-side bounded wait timed out");
+  return TSQR_OK;
+}
+
+tsqr_status_t tsqr_batch_destroy(tsqr_batch_t b) {
+  delete b;
   return TSQR_OK;
 }
 

@@ -84,14 +84,11 @@ size_t formq_smem_bytes(const Plan& P) {
 // C - T C for s = 0 and -Y_s T C for s >= 1 (V = [I; Y_1; ...], Sec. 3.2).  The blocks live in
 // the node_r slots, which the factorization no longer needs.
 template <class Ar>
-__global__ void __launch_bounds__(kThreads, 1)
-    formq_tree_kernel(const Plan P, const Store st, int level) {
+__device__ __forceinline__ void formq_tree_node(const Plan& P, const Store& st, int level, int node, char* smem_raw) {
   using E = typename Ar::E;
-  extern __shared__ char smem_raw[];
   FormQSmem<E> f = carve_formq<E>(smem_raw, P);
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, ld = f.ld;
-  const int node = blockIdx.x;
   const int tn = P.level_offset[level] + node - P.chains;
   E* blocks = reinterpret_cast<E*>(st.node_r);
   const E* Cn = blocks + (size_t)(P.level_offset[level] + node) * np * np;
@@ -131,19 +128,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 1) formq_tree_kernel(const Plan P, const Store st, int level) {
+  extern __shared__ char smem_raw[];
+  formq_tree_node<Ar>(P, st, level, blockIdx.x, smem_raw);
+}
+
 // Q rows of chain g, last leaf first.  chain step (V = [I; Y]): Q_rows = -Y M with M = T C,
 // then C -= M.  first leaf (V unit lower trapezoidal): Q_rows = [C; 0] - V (T (V_top^T C)).
 template <class Ar>
-__global__ void __launch_bounds__(kThreads, 1)
-    formq_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
-                 int64_t ldq, int box_rows) {
+__device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Plan& P, const Store& st,
+                                            double* __restrict__ Q, int64_t ldq, int box_rows, int g,
+                                            char* smem_raw) {
   using E = typename Ar::E;
-  extern __shared__ char smem_raw[];
   FormQSmem<E> f = carve_formq<E>(smem_raw, P);
   const Tile& S = f.S;
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, h = P.h, ld = f.ld;
-  const int g = blockIdx.x;
   if (tid == 0) {
     mbar_init(f.bar, 1);
     fence_mbar_init();
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool plain = (leaf == l0);
     const int64_t row0 = leaf * h;
     load_square(st.t_leaf + leaf * np * np, f.T, np, ld);
-    if (!tile_load(S, &mapV, f.bar, phase, np, row0, h, 0, box_rows, st.status, f.flag)) return;
+    if (!tile_load(S, mapV_p, f.bar, phase, np, row0, h, 0, box_rows, st.status, f.flag)) return;
     const int64_t rows_valid = (P.m - row0 < h) ? (P.m - row0) : h;
     if (!plain) {
       tri_mul<Ar>(f.T, ld, f.C, ld, f.M, ld, n, np, np, false);
@@ -219,6 +220,69 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
     }
   }
+}
+
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 1)
+    formq_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
+                 int64_t ldq, int box_rows) {
+  extern __shared__ char smem_raw[];
+  formq_chain<Ar>(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
+}
+
+// Batched thin Q: one tree step (item, node, level) per block, or one chain per block.
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 1)
+    formq_tree_batched_kernel(const BatchItem* __restrict__ items, const BatchWork* __restrict__ work) {
+  extern __shared__ char smem_raw[];
+  const BatchWork w = work[blockIdx.x];
+  const BatchItem& it = items[w.item];
+  formq_tree_node<Ar>(it.plan, it.store, w.level, w.chain, smem_raw);
+}
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 1)
+    formq_chain_batched_kernel(const BatchItem* __restrict__ items, const BatchWork* __restrict__ work) {
+  extern __shared__ char smem_raw[];
+  const BatchWork w = work[blockIdx.x];
+  const BatchItem& it = items[w.item];
+  formq_chain<Ar>(&it.mapV, it.plan, it.store, it.Q, it.ldq, it.box_rows, w.chain, smem_raw);
+}
+
+template <class Ar>
+static cudaError_t prepare_form_q_batched_t(size_t smem) {
+  cudaError_t e =
+      cudaFuncSetAttribute(formq_tree_batched_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(formq_chain_batched_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t prepare_form_q_batched(int precision, size_t smem) {
+  return precision == 1 ? prepare_form_q_batched_t<ArithDF>(smem) : prepare_form_q_batched_t<ArithF64>(smem);
+}
+
+template <class Ar>
+static cudaError_t launch_form_q_batched_t(const BatchItem* items, const BatchWork* chain_work, int chain_blocks,
+                                           const BatchWork* const* level_work, const int* level_blocks, int depth,
+                                           size_t smem, cudaStream_t stream) {
+  cudaError_t e;
+  for (int d = 0; d < depth; ++d) {
+    if (level_blocks[d] == 0) continue;
+    formq_tree_batched_kernel<Ar><<<level_blocks[d], kThreads, smem, stream>>>(items, level_work[d]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  formq_chain_batched_kernel<Ar><<<chain_blocks, kThreads, smem, stream>>>(items, chain_work);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain_work, int chain_blocks,
+                                  const BatchWork* const* level_work, const int* level_blocks, int depth,
+                                  int precision, size_t smem, cudaStream_t stream) {
+  if (precision == 1)
+    return launch_form_q_batched_t<ArithDF>(items, chain_work, chain_blocks, level_work, level_blocks, depth, smem,
+                                            stream);
+  return launch_form_q_batched_t<ArithF64>(items, chain_work, chain_blocks, level_work, level_blocks, depth, smem,
+                                           stream);
 }
 
 // ------------------------------------------------------------------------------------------

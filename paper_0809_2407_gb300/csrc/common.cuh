@@ -57,6 +57,25 @@ struct Store {
   int* status;      // 1
 };
 
+// One factorization of a batch, as the batched kernels read it from device memory.
+struct __align__(64) BatchItem {
+  CUtensorMap mapA;  // A, or its staged copy
+  CUtensorMap mapV;  // reflector storage
+  Plan plan;
+  Store store;
+  double* R;         // n x n, leading dimension ldr
+  int64_t ldr;
+  double* Q;         // thin Q output of the batched form-Q, leading dimension ldq
+  int64_t ldq;
+  int box_rows;
+};
+// Block b of a batched launch works on chain `chain` (or tree node `chain` of a level) of item.
+struct BatchWork {
+  int item;
+  int chain;
+  int level;  // tree level of a form-Q tree step (unused for chain work)
+};
+
 // ---------------------------------------------------------------------------------------------
 // Shared-memory tile in the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_128B and 16-double
 // (128-byte) inner boxes: the columns are split into panels of 16; a panel holds rows_cap rows

@@ -76,17 +76,16 @@ __device__ inline void convert_rows_in(const Tile& S, int r0, int rows, int np) 
   }
 }
 
+// Chain g of one factorization, then the tree above it while this block arrives last.
 template <class Ar>
-__global__ void __launch_bounds__(kThreads, 2)
-    factor_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, const Plan P,
-                  const Store st, double* __restrict__ R_out, int64_t ldr, int box_rows) {
+__device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CUtensorMap* mapV_p, const Plan& P,
+                                             const Store& st, double* __restrict__ R_out, int64_t ldr, int box_rows,
+                                             int g, char* smem_raw) {
   using E = typename Ar::E;
-  extern __shared__ char smem_raw[];
   FactorSmem<E> f = carve_factor<E>(smem_raw, P);
   const Tile& S = f.S;
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, h = P.h;
-  const int g = blockIdx.x;
   E* tau_leaf = reinterpret_cast<E*>(st.tau_leaf);
   E* t_leaf = reinterpret_cast<E*>(st.t_leaf);
   E* node_r = reinterpret_cast<E*>(st.node_r);
@@ -103,7 +102,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const bool plain = (leaf == l0);
     const int dst = plain ? 0 : np;
     const int64_t row0 = leaf * h;
-    if (!tile_load(S, &mapA, f.bar, phase, np, row0, h, dst, box_rows, st.status, f.flag)) {
+    if (!tile_load(S, mapA_p, f.bar, phase, np, row0, h, dst, box_rows, st.status, f.flag)) {
       if (tid == 0) tma_store_wait_all();
       return;
     }
@@ -112,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       stacked_qr<Ar>(S, PLAIN, h, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
     else
       chain_step<Ar>(f, P);
-    tile_store(S, &mapV, np, row0, h, dst, box_rows);
+    tile_store(S, mapV_p, np, row0, h, dst, box_rows);
     E* tau_g = tau_leaf + leaf * np;
     E* T_g = t_leaf + leaf * np * np;
     for (int i = tid; i < np; i += kThreads) tau_g[i] = f.tau_s[i];
@@ -194,6 +193,39 @@ __global__ void __launch_bounds__(kThreads, 2)
     const double d = Ar::is_neg(at<E>(S, r, r)) ? -1.0 : 1.0;
     R_out[(int64_t)r * ldr + c] = (c >= r) ? d * Ar::to_f64(at<E>(S, r, c)) : 0.0;
   }
+}
+
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 2)
+    factor_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, const Plan P,
+                  const Store st, double* __restrict__ R_out, int64_t ldr, int box_rows) {
+  extern __shared__ char smem_raw[];
+  factor_chain<Ar>(&mapA, &mapV, P, st, R_out, ldr, box_rows, blockIdx.x, smem_raw);
+}
+
+// Many factorizations in one launch: block b runs chain work[b].chain of item work[b].item.
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 2)
+    factor_batched_kernel(const BatchItem* __restrict__ items, const BatchWork* __restrict__ work) {
+  extern __shared__ char smem_raw[];
+  const BatchWork w = work[blockIdx.x];
+  const BatchItem& it = items[w.item];
+  factor_chain<Ar>(&it.mapA, &it.mapV, it.plan, it.store, it.R, it.ldr, it.box_rows, w.chain, smem_raw);
+}
+
+cudaError_t prepare_factor_batched(int precision, size_t smem) {
+  if (precision == 1)
+    return cudaFuncSetAttribute(factor_batched_kernel<ArithDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(factor_batched_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work, int blocks, int precision,
+                                  size_t smem, cudaStream_t stream) {
+  if (precision == 1)
+    factor_batched_kernel<ArithDF><<<blocks, kThreads, smem, stream>>>(items, work);
+  else
+    factor_batched_kernel<ArithF64><<<blocks, kThreads, smem, stream>>>(items, work);
+  return cudaGetLastError();
 }
 
 template <class Ar>

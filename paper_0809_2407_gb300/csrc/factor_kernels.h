@@ -15,6 +15,13 @@ cudaError_t launch_stage_copy(const double* A, int64_t lda, double* V, int64_t l
                               cudaStream_t stream);
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                           double* R_out, int64_t ldr, int box_rows, cudaStream_t stream);
+cudaError_t prepare_factor_batched(int precision, size_t smem);
+cudaError_t prepare_form_q_batched(int precision, size_t smem);
+cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work, int blocks, int precision,
+                                  size_t smem, cudaStream_t stream);
+cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain_work, int chain_blocks,
+                                  const BatchWork* const* level_work, const int* level_blocks, int depth,
+                                  int precision, size_t smem, cudaStream_t stream);
 cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,
                           int box_rows, cudaStream_t stream);
 cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,

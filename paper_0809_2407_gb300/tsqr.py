@@ -22,7 +22,8 @@ TSQR_ROW_MAJOR, TSQR_COL_MAJOR = 0, 1
 
 EXPORTED = ("tsqr_workspace_size", "tsqr_factor", "tsqr_apply_qt", "tsqr_apply_q", "tsqr_form_q",
             "tsqr_status_poll", "tsqr_handle_info", "tsqr_destroy", "tsqr_status_string", "tsqr_last_error",
-            "tsqr_factor_r_noalloc")
+            "tsqr_factor_r_noalloc", "tsqr_batch_workspace_size", "tsqr_batch_create", "tsqr_batch_factor",
+            "tsqr_batch_form_q", "tsqr_batch_status_poll", "tsqr_batch_destroy")
 
 
 class Opts(ctypes.Structure):
@@ -68,6 +69,14 @@ def load(path: str = LIB_PATH):
     lib.tsqr_handle_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.tsqr_destroy.argtypes = [vp]
     lib.tsqr_factor_r_noalloc.argtypes = [i64, i64, vp, i64, vp, i64, vp]
+    i32, pi64, pvp = ctypes.c_int32, ctypes.POINTER(i64), ctypes.POINTER(vp)
+    lib.tsqr_batch_workspace_size.argtypes = [ctypes.c_int, i32, pi64, pi64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+    lib.tsqr_batch_create.argtypes = [ctypes.c_int, i32, pi64, pi64, pvp, pi64, pvp, pi64, pvp, pi64, vp, sz,
+                                      ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.tsqr_batch_factor.argtypes = [vp, vp]
+    lib.tsqr_batch_form_q.argtypes = [vp, vp]
+    lib.tsqr_batch_status_poll.argtypes = [vp, vp]
+    lib.tsqr_batch_destroy.argtypes = [vp]
     lib.tsqr_status_string.argtypes = [ctypes.c_int]
     lib.tsqr_status_string.restype = ctypes.c_char_p
     lib.tsqr_last_error.argtypes = []
@@ -143,6 +152,44 @@ def tsqr_destroy(h):
 def tsqr_factor_r_noalloc(m, n, dA, lda, dR, ldr, stream):
     """R only, using the library's static device scratch: for callers that cannot allocate."""
     _check(load().tsqr_factor_r_noalloc(m, n, dA, lda, dR, ldr, stream))
+
+
+def _arr(ctype, vals):
+    return (ctype * len(vals))(*vals)
+
+
+def tsqr_batch_workspace_size(dtype, count, m, n, opts=None):
+    out = ctypes.c_size_t(0)
+    _check(load().tsqr_batch_workspace_size(dtype, count, _arr(ctypes.c_int64, m), _arr(ctypes.c_int64, n),
+                                            _opts(opts), ctypes.byref(out)))
+    return out.value
+
+
+def tsqr_batch_create(dtype, count, m, n, dA, lda, dR, ldr, dQ, ldq, dWork, work_bytes, opts, stream):
+    h = ctypes.c_void_p()
+    vp = ctypes.c_void_p
+    _check(load().tsqr_batch_create(dtype, count, _arr(ctypes.c_int64, m), _arr(ctypes.c_int64, n), _arr(vp, dA),
+                                    _arr(ctypes.c_int64, lda), _arr(vp, dR), _arr(ctypes.c_int64, ldr),
+                                    _arr(vp, dQ) if dQ is not None else None,
+                                    _arr(ctypes.c_int64, ldq) if ldq is not None else None,
+                                    dWork, work_bytes, _opts(opts), stream, ctypes.byref(h)))
+    return h
+
+
+def tsqr_batch_factor(b, stream):
+    _check(load().tsqr_batch_factor(b, stream))
+
+
+def tsqr_batch_form_q(b, stream):
+    _check(load().tsqr_batch_form_q(b, stream))
+
+
+def tsqr_batch_status_poll(b, stream):
+    return load().tsqr_batch_status_poll(b, stream)
+
+
+def tsqr_batch_destroy(b):
+    load().tsqr_batch_destroy(b)
 
 
 # ---------------------------------------------------------------- torch convenience layer
@@ -225,3 +272,122 @@ def qr(A, **opts):
     R = f.R
     f.close()
     return Q, R
+
+
+class Batch:
+    """Many CUDA float64 tall-skinny matrices factored together (one launch for all R factors,
+    one launch per tree depth plus one for all thin Q factors).  The launches only enqueue work on
+    the current stream, so ``factor()`` and ``form_q()`` can be captured in a CUDA graph.
+    """
+
+    def __init__(self, mats, want_q=True, leaf_h=0, chain=0, arity=0, precision=0):
+        import torch
+
+        for i, A in enumerate(mats):
+            _check_matrix(A, "A[%d]" % i)
+        self.mats = list(mats)
+        dev = self.mats[0].device
+        self.m = [A.shape[0] for A in self.mats]
+        self.n = [A.shape[1] for A in self.mats]
+        count = len(self.mats)
+        self.opts = Opts(leaf_h=leaf_h, chain=chain, arity=arity, precision=precision, inplace=0)
+        nbytes = tsqr_batch_workspace_size(TSQR_F64, count, self.m, self.n, self.opts)
+        self.work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+        self.R = [torch.empty((k, k), dtype=torch.float64, device=dev) for k in self.n]
+        self.Q = [torch.empty((mm, k), dtype=torch.float64, device=dev) for mm, k in zip(self.m, self.n)] \
+            if want_q else None
+        self.handle = tsqr_batch_create(
+            TSQR_F64, count, self.m, self.n, [A.data_ptr() for A in self.mats], [A.stride(0) for A in self.mats],
+            [R.data_ptr() for R in self.R], [R.stride(0) for R in self.R],
+            [Q.data_ptr() for Q in self.Q] if want_q else None, [Q.stride(0) for Q in self.Q] if want_q else None,
+            self.work.data_ptr(), nbytes, self.opts, _stream())
+
+    def factor(self):
+        tsqr_batch_factor(self.handle, _stream())
+
+    def form_q(self):
+        tsqr_batch_form_q(self.handle, _stream())
+
+    def status(self):
+        return tsqr_batch_status_poll(self.handle, _stream())
+
+    def close(self):
+        if self.handle:
+            tsqr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- autotuner
+_TUNE_CACHE = {}
+
+
+def tune_key(m, n, precision):
+    """Cache key: (log2 bucket of m, n rounded up to the padded width, precision)."""
+    mb = max(0, int(m).bit_length() - 1)
+    np_ = 16
+    while np_ < n:
+        np_ *= 2
+    return (mb, np_, int(precision))
+
+
+def candidate_opts(m, n, precision=0):
+    """Plans the library accepts for an m x n problem: leaf height 64..1024, arity 2/4/8, flat
+    chains (auto) or a pure tree (chain 1)."""
+    out = []
+    for h in (64, 96, 128, 192, 256, 512, 1024):
+        for arity in (2, 4, 8):
+            for chain in (0, 1):
+                o = Opts(leaf_h=h, chain=chain, arity=arity, precision=precision, inplace=0)
+                try:
+                    tsqr_workspace_size(TSQR_F64, m, n, o)
+                except TsqrError:
+                    continue
+                out.append(o)
+    return out
+
+
+def autotune(m, n, precision=0, reps=2, proxy_rows=1 << 18, path=None):
+    """Times factor + thin Q for each candidate plan on a seeded N(0,1) matrix of min(m, proxy_rows)
+    rows and returns the fastest Opts, caching it by tune_key (and in the JSON file `path` if given).
+    """
+    import json
+
+    import torch
+
+    key = tune_key(m, n, precision)
+    if path and not _TUNE_CACHE and os.path.exists(path):
+        with open(path) as fh:
+            for k, v in json.load(fh).items():
+                _TUNE_CACHE[tuple(int(x) for x in k.split(","))] = v
+    if key in _TUNE_CACHE:
+        return Opts(**_TUNE_CACHE[key])
+    rows = int(min(m, proxy_rows))
+    g = torch.Generator(device="cuda").manual_seed(20080809)
+    A = torch.randn((rows, n), dtype=torch.float64, device="cuda", generator=g)
+    best, best_ms = None, float("inf")
+    for o in candidate_opts(rows, n, precision):
+        times = []
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f = Factorization(A, leaf_h=o.leaf_h, chain=o.chain, arity=o.arity, precision=precision)
+            f.form_q()
+            e1.record()
+            torch.cuda.synchronize()
+            f.close()
+            times.append(e0.elapsed_time(e1))
+        ms = min(times[1:])
+        if ms < best_ms:
+            best, best_ms = o, ms
+    _TUNE_CACHE[key] = {"leaf_h": best.leaf_h, "chain": best.chain, "arity": best.arity, "precision": precision,
+                        "inplace": 0}
+    if path:
+        with open(path, "w") as fh:
+            json.dump({",".join(map(str, k)): v for k, v in _TUNE_CACHE.items()}, fh, indent=1)
+    return best

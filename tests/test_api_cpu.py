@@ -92,3 +92,26 @@ def test_factor_rejects_before_launch(lib):
     assert L.tsqr_apply_q(None, 1, fake, 1, None) == 1
     assert L.tsqr_status_poll(None, None) == 1
     assert L.tsqr_destroy(None) == 0
+
+
+def test_batch_plans_and_errors(lib):
+    m, n = [1000, 5000, 300, 77777], [8, 16, 50, 64]
+    size = lib.tsqr_batch_workspace_size(lib.TSQR_F64, 4, m, n)
+    single = sum(lib.tsqr_workspace_size(lib.TSQR_F64, mm, nn) for mm, nn in zip(m, n))
+    assert size >= single // 2  # every item keeps its own factors
+    with pytest.raises(lib.TsqrError) as ei:
+        lib.tsqr_batch_workspace_size(lib.TSQR_F64, 2, [10, 100], [20, 4])  # item 0: m < n
+    assert ei.value.status == 1 and "item 0" in str(ei.value)
+    with pytest.raises(lib.TsqrError):
+        lib.tsqr_batch_workspace_size(lib.TSQR_F64, 0, [], [])
+    with pytest.raises(lib.TsqrError) as ei:
+        lib.tsqr_batch_workspace_size(lib.TSQR_F64, 1, [100], [4], {"inplace": 1})
+    assert ei.value.status == 2
+
+
+def test_autotune_candidates_and_key(lib):
+    c = lib.candidate_opts(1 << 20, 64)
+    assert len(c) >= 6
+    assert all(o.leaf_h >= 64 for o in c)
+    assert lib.tune_key(1 << 20, 50, 0) == (20, 64, 0)
+    assert lib.tune_key(3 << 19, 9, 1) == (20, 16, 1)

@@ -276,3 +276,63 @@ def test_full_size_properties(T, prec):
     be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
     orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device="cuda") - Q.T @ Q).item()
     assert be <= TOL_BACK and orth <= TOL_ORTH
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_uneven(T, precision):
+    """One launch for many matrices of uneven m and n (block Krylov / s-step batches)."""
+    import torch
+
+    rng = np.random.default_rng(4)
+    ms = [int(x) for x in np.exp(rng.uniform(np.log(300), np.log(40000), 14)).astype(int)]
+    ns = [int(x) for x in rng.choice([8, 16, 32, 50, 64], 14)]
+    ms = [max(m_, n_) for m_, n_ in zip(ms, ns)]
+    hs = [inputs.gaussian(m_, n_, 5000 + i) for i, (m_, n_) in enumerate(zip(ms, ns))]
+    mats = [torch.from_numpy(a).cuda() for a in hs]
+    b = T.Batch(mats, precision=precision)
+    b.factor()
+    b.form_q()
+    torch.cuda.synchronize()
+    assert b.status() == T.TSQR_OK
+    for a, R, Q in zip(hs, b.R, b.Q):
+        check_against_oracle(a, R.cpu().numpy(), Q.cpu().numpy(), precision=precision)
+    b.close()
+
+
+def test_batched_cuda_graph(T):
+    """tsqr_batch_factor / tsqr_batch_form_q captured once in a CUDA graph and replayed."""
+    import torch
+
+    hs = [inputs.gaussian(4000 + 37 * i, 16 + 8 * (i % 3), 6000 + i) for i in range(6)]
+    mats = [torch.from_numpy(a).cuda() for a in hs]
+    b = T.Batch(mats)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.factor()
+        b.form_q()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    R0 = [R.clone() for R in b.R]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.factor()
+        b.form_q()
+    for R in b.R:
+        R.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for R, r0, a, Q in zip(b.R, R0, hs, b.Q):
+        assert torch.equal(R, r0)
+        check_against_oracle(a, R.cpu().numpy(), Q.cpu().numpy())
+    b.close()
+
+
+def test_autotune_returns_valid_plan(T):
+    import torch
+
+    o = T.autotune(20000, 24, reps=1, proxy_rows=20000)
+    A_h = inputs.gaussian(20000, 24, 31337)
+    _, R, Q = run(T, A_h, leaf_h=o.leaf_h, chain=o.chain, arity=o.arity)
+    check_against_oracle(A_h, R, Q)
+    assert T.autotune(20000, 24) is not None  # cached
