@@ -126,6 +126,18 @@ tsqr_status_t tsqr_status_poll(tsqr_handle_t h, tsqr_stream_t stream);
 /* Fills *info with the plan and workspace pointers of h. */
 tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info);
 
+/* Reverse-mode derivative of (Q, R) = qr(A) through the handle's implicit Q.  Given the
+ * cotangents Qbar = dL/dQ (m x n, device, ldqb >= n; NULL when L does not depend on Q) and
+ * Rbar = dL/dR (n x n, device, ldrb >= n, upper triangle used: R's strict lower part is
+ * structurally zero; NULL when L does not depend on R), writes
+ * Abar = dL/dA (m x n, device, ldab >= n) by the published adjoint of the thin QR,
+ *   M = R Rbar^T - Qbar^T Q,  Abar = (Qbar + Q copyltu(M)) R^{-T},  copyltu(M) = tril(M) + tril(M,-1)^T,
+ * with Q^T Qbar and Q copyltu(M) applied from the implicit Q (tsqr_apply_qt, tsqr_apply_q):
+ * no explicit Q is needed.  R (n x n, ldr >= n) is the R that tsqr_factor returned.  A must have
+ * full column rank (the derivative does not exist otherwise; a zero R_jj gives Inf/NaN). */
+tsqr_status_t tsqr_backward(tsqr_handle_t h, const void* dQbar, int64_t ldqb, const void* dRbar, int64_t ldrb,
+                            const void* dR, int64_t ldr, void* dAbar, int64_t ldab, tsqr_stream_t stream);
+
 /* ---- Batches: many independent tall-skinny factorizations in one launch --------------------
  * The s-step and block Krylov uses of TSQR (Sec. 1) produce many small tall-skinny blocks; a
  * batch factors all of them with one persistent launch of the factorization kernel (every

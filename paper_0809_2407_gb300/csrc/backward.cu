@@ -1,0 +1,104 @@
+// Backward of the thin QR computed by TSQR, for reverse-mode differentiation.
+//
+// For (Q, R) = qr(A) and a scalar loss with cotangents Qbar = dL/dQ and Rbar = dL/dR, the
+// published adjoint of the thin QR of a full-rank A is
+//   M = R Rbar^T - Qbar^T Q,   Abar = (Qbar + Q copyltu(M)) R^{-T},
+// copyltu(M) = tril(M) + tril(M, -1)^T.  The implicit Q of the factorization gives both
+// products without an explicit Q: Z = Q_full^T Qbar has Q^T Qbar in its top n rows (so
+// M = R Rbar^T - Z_top^T), and Q_full (Z + [copyltu(M); 0]) = Qbar + Q copyltu(M).  The steps
+// are tsqr_apply_qt, the small kernel below, tsqr_apply_q and a row-wise triangular solve.
+#include "../../include/tsqr.h"
+#include "factor_kernels.h"
+#include "internal.h"
+
+namespace tsqr {
+
+// Z_top += copyltu(R Rbar^T - Z_top^T) for the n x n top block of Z (one block of 256 threads).
+__global__ void backward_small_kernel(int n, const double* __restrict__ R, int64_t ldr,
+                                      const double* __restrict__ Rbar, int64_t ldrb, double* __restrict__ Z,
+                                      int64_t ldz) {
+  extern __shared__ double Ms[];  // n x (n + 1)
+  const int ld = n + 1;
+  for (int o = threadIdx.x; o < n * n; o += blockDim.x) {
+    const int i = o / n, j = o % n;
+    double v = -Z[(int64_t)j * ldz + i];
+    // (R triu(Rbar)^T)_ij: R's strict lower part is structurally zero, so its cotangent is ignored
+    if (Rbar != nullptr)
+      for (int k = (i > j ? i : j); k < n; ++k) v = fma(R[(int64_t)i * ldr + k], Rbar[(int64_t)j * ldrb + k], v);
+    Ms[i * ld + j] = v;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < n * n; o += blockDim.x) {
+    const int i = o / n, j = o % n;
+    Z[(int64_t)i * ldz + j] += (i >= j) ? Ms[i * ld + j] : Ms[j * ld + i];
+  }
+}
+
+// B <- B R^{-T} row by row: each row b solves R x = b by back substitution.  A block stages 128
+// rows through shared memory (coalesced loads and stores), one thread per row.
+constexpr int kSolveRows = 128;
+
+__global__ void __launch_bounds__(kSolveRows)
+    trsm_rt_kernel(int64_t m, int n, const double* __restrict__ R, int64_t ldr, double* __restrict__ B, int64_t ldb) {
+  extern __shared__ double sm[];
+  const int ldt = n + 1;
+  double* Rs = sm;                  // n x (n + 1)
+  double* rinv = Rs + n * ldt;      // n
+  double* tile = rinv + n;          // kSolveRows x (n + 1)
+  for (int o = threadIdx.x; o < n * n; o += blockDim.x) Rs[(o / n) * ldt + o % n] = R[(int64_t)(o / n) * ldr + o % n];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rinv[i] = 1.0 / R[(int64_t)i * ldr + i];
+  const int64_t r0 = (int64_t)blockIdx.x * kSolveRows;
+  const int rows = (int)((m - r0 < kSolveRows) ? (m - r0) : kSolveRows);
+  for (int o = threadIdx.x; o < rows * n; o += blockDim.x) tile[(o / n) * ldt + o % n] = B[(r0 + o / n) * ldb + o % n];
+  __syncthreads();
+  if (threadIdx.x < rows) {
+    double* x = tile + threadIdx.x * ldt;
+    for (int i = n - 1; i >= 0; --i) {
+      double v = x[i];
+      for (int k = i + 1; k < n; ++k) v = fma(-Rs[i * ldt + k], x[k], v);
+      x[i] = v * rinv[i];
+    }
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < rows * n; o += blockDim.x) B[(r0 + o / n) * ldb + o % n] = tile[(o / n) * ldt + o % n];
+}
+
+}  // namespace tsqr
+
+extern "C" tsqr_status_t tsqr_backward(tsqr_handle_t h, const void* dQbar, int64_t ldqb, const void* dRbar, int64_t ldrb,
+                                       const void* dR, int64_t ldr, void* dAbar, int64_t ldab, tsqr_stream_t stream) {
+  using namespace tsqr;
+  tsqr_info_t info;
+  tsqr_status_t s = tsqr_handle_info(h, &info);
+  if (s != TSQR_OK) return s;
+  const int64_t m = info.m;
+  const int n = (int)info.n;
+  if (!dR || !dAbar) return internal_fail(TSQR_ERR_INVALID_ARG, "R and Abar must be non-NULL");
+  if (ldr < n || ldab < n || (dQbar && ldqb < n) || (dRbar && ldrb < n))
+    return internal_fail(TSQR_ERR_INVALID_ARG, "leading dimensions must be >= n");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  // Z = Q_full^T Qbar (zero when the loss does not depend on Q)
+  if (dQbar)
+    e = cudaMemcpy2DAsync(dAbar, ldab * 8, dQbar, ldqb * 8, (size_t)n * 8, (size_t)m, cudaMemcpyDeviceToDevice, cs);
+  else
+    e = cudaMemset2DAsync(dAbar, ldab * 8, 0, (size_t)n * 8, (size_t)m, cs);
+  if (e != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
+  if (dQbar && (s = tsqr_apply_qt(h, n, dAbar, ldab, stream)) != TSQR_OK) return s;
+  // Z_top += copyltu(R Rbar^T - Z_top^T)
+  backward_small_kernel<<<1, 256, (size_t)n * (n + 1) * 8, cs>>>(n, static_cast<const double*>(dR), ldr,
+                                                                  static_cast<const double*>(dRbar), ldrb,
+                                                                  static_cast<double*>(dAbar), ldab);
+  if ((e = cudaGetLastError()) != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
+  // B = Q_full Z = Qbar + Q copyltu(M)
+  if ((s = tsqr_apply_q(h, n, dAbar, ldab, stream)) != TSQR_OK) return s;
+  // Abar = B R^{-T}
+  const size_t smem = ((size_t)n * (n + 1) + n + (size_t)kSolveRows * (n + 1)) * 8;
+  e = cudaFuncSetAttribute(trsm_rt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
+  const int64_t blocks = (m + kSolveRows - 1) / kSolveRows;
+  trsm_rt_kernel<<<(unsigned)blocks, kSolveRows, smem, cs>>>(m, n, static_cast<const double*>(dR), ldr,
+                                                             static_cast<double*>(dAbar), ldab);
+  if ((e = cudaGetLastError()) != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
+  return TSQR_OK;
+}

@@ -23,7 +23,7 @@ TSQR_ROW_MAJOR, TSQR_COL_MAJOR = 0, 1
 EXPORTED = ("tsqr_workspace_size", "tsqr_factor", "tsqr_apply_qt", "tsqr_apply_q", "tsqr_form_q",
             "tsqr_status_poll", "tsqr_handle_info", "tsqr_destroy", "tsqr_status_string", "tsqr_last_error",
             "tsqr_factor_r_noalloc", "tsqr_batch_workspace_size", "tsqr_batch_create", "tsqr_batch_factor",
-            "tsqr_batch_form_q", "tsqr_batch_status_poll", "tsqr_batch_destroy")
+            "tsqr_batch_form_q", "tsqr_batch_status_poll", "tsqr_batch_destroy", "tsqr_backward")
 
 
 class Opts(ctypes.Structure):
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
     lib.tsqr_batch_form_q.argtypes = [vp, vp]
     lib.tsqr_batch_status_poll.argtypes = [vp, vp]
     lib.tsqr_batch_destroy.argtypes = [vp]
+    lib.tsqr_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, i64, vp]
     lib.tsqr_status_string.argtypes = [ctypes.c_int]
     lib.tsqr_status_string.restype = ctypes.c_char_p
     lib.tsqr_last_error.argtypes = []
@@ -152,6 +153,10 @@ def tsqr_destroy(h):
 def tsqr_factor_r_noalloc(m, n, dA, lda, dR, ldr, stream):
     """R only, using the library's static device scratch: for callers that cannot allocate."""
     _check(load().tsqr_factor_r_noalloc(m, n, dA, lda, dR, ldr, stream))
+
+
+def tsqr_backward(h, dQbar, ldqb, dRbar, ldrb, dR, ldr, dAbar, ldab, stream):
+    _check(load().tsqr_backward(h, dQbar, ldqb, dRbar, ldrb, dR, ldr, dAbar, ldab, stream))
 
 
 def _arr(ctype, vals):
@@ -391,3 +396,68 @@ def autotune(m, n, precision=0, reps=2, proxy_rows=1 << 18, path=None):
         with open(path, "w") as fh:
             json.dump({",".join(map(str, k)): v for k, v in _TUNE_CACHE.items()}, fh, indent=1)
     return best
+
+
+# ---------------------------------------------------------------- differentiation
+def _qr_function():
+    import torch
+
+    class QR(torch.autograd.Function):
+        """(Q, R) = qr(A) by TSQR with a hand-written backward (tsqr_backward).
+
+        keep="tree": the forward keeps its workspace (the implicit Q tree: reflectors, T, tree
+        nodes) for the backward.  keep="recompute": the forward frees it and the backward
+        factors A again (A is alive anyway), so between forward and backward only Q and R are
+        held.  Neither stores an explicit Q for the backward.
+        """
+
+        @staticmethod
+        def forward(ctx, A, keep, opts):
+            f = Factorization(A, **opts)
+            Q = f.form_q()
+            R = f.R.clone()
+            ctx.keep, ctx.opts = keep, opts
+            if keep == "tree":
+                ctx.fact = f
+            else:
+                f.close()
+                del f
+                ctx.fact = None
+            ctx.save_for_backward(A, R)
+            return Q, R
+
+        @staticmethod
+        def backward(ctx, Qbar, Rbar):
+            A, R = ctx.saved_tensors
+            f = ctx.fact if ctx.fact is not None else Factorization(A, **ctx.opts)
+            m, n = A.shape
+            Abar = torch.empty((m, n), dtype=torch.float64, device=A.device)
+            qb = Qbar.contiguous() if Qbar is not None else None
+            rb = Rbar.contiguous() if Rbar is not None else None
+            tsqr_backward(f.handle, qb.data_ptr() if qb is not None else None, n,
+                          rb.data_ptr() if rb is not None else None, n, R.data_ptr(), n,
+                          Abar.data_ptr(), n, _stream())
+            if ctx.fact is None:
+                torch.cuda.current_stream().synchronize()
+                f.close()
+            ctx.fact = None
+            return Abar, None, None
+
+    return QR
+
+
+_QR = None
+
+
+def qr_autograd(A, keep="tree", **opts):
+    """Differentiable thin QR of a CUDA float64 matrix (or a batch: leading dimensions looped).
+    Returns (Q, R) with diag(R) >= 0; gradients flow through tsqr_backward."""
+    global _QR
+    if _QR is None:
+        _QR = _qr_function()
+    if A.dim() == 2:
+        return _QR.apply(A, keep, dict(opts))
+    import torch
+
+    outs = [_QR.apply(A[i], keep, dict(opts)) for i in range(A.shape[0])]
+    return torch.stack([q for q, _ in outs]), torch.stack([r for _, r in outs])
