@@ -233,6 +233,50 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
             "largest": {"m": int(ms[big]), "n": int(ns[big]), "backward_error": be, "orthogonality": orth}}
 
 
+def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, warmup=2):
+    """Plain FP64 TSQR (factor + thin Q + Q^T b) on the other column counts of the workload
+    family, A = U Sigma V^T with kappa = 1: n = 16 and 32 are single TSQRs with taller leaves,
+    n = 128 is the blocked QR over two 64-column TSQR panels."""
+    import numpy as np
+
+    out = {}
+    for n in ns:
+        A = torch.from_numpy(make_input(m, n)).to(dev)
+        b = torch.from_numpy(np.random.default_rng(6).standard_normal((m, 1))).to(dev)
+        Q = torch.empty((m, n), dtype=torch.float64, device=dev)
+        R = torch.empty((n, n), dtype=torch.float64, device=dev)
+        nbytes = tsqr.tsqr_workspace_size(tsqr.TSQR_F64, m, n, None)
+        work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        ev = {"factor": [], "form_q": [], "apply_qt": []}
+        for it in range(warmup + steps):
+            mk = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            mk[0].record(stream)
+            h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
+                                 work.data_ptr(), nbytes, None, sptr)
+            mk[1].record(stream)
+            tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
+            mk[2].record(stream)
+            tsqr.tsqr_apply_qt(h, 1, b.data_ptr(), 1, sptr)
+            mk[3].record(stream)
+            info = tsqr.tsqr_handle_info(h)
+            tsqr.tsqr_destroy(h)
+            torch.cuda.synchronize()
+            if it >= warmup:
+                for i, k in enumerate(("factor", "form_q", "apply_qt")):
+                    ev[k].append(mk[i].elapsed_time(mk[i + 1]))
+        fl = flops(m, n)
+        ms = sum(statistics.mean(v) for v in ev.values())
+        out["n%d" % n] = {
+            "m": m, "n": n, "panels": info.panels, "leaf_h": info.leaf_h, "chains": info.chains,
+            "value": sum(fl.values()) / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
+            "kernel_ms": {k: statistics.mean(v) for k, v in ev.items()},
+            "backward_error": (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item(),
+            "orthogonality": torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Q.T @ Q).item()}
+        del A, b, Q, R, work
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_autograd(tsqr, torch, dev, args, batch=64, m=65536, n=32, seed=20085000):
     """Forward + backward of sum(W1*Q) + sum(W2*R) for a batch of 64 matrices of 65536 x 32
     (FP64): time and peak extra memory when the backward keeps the implicit Q tree, when it
@@ -291,6 +335,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip timing the precision forms")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-matrix batched workload")
     ap.add_argument("--no-autograd", action="store_true", help="skip the differentiable-QR workload")
+    ap.add_argument("--no-shapes", action="store_true", help="skip the n = 16, 32, 128 shapes")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -362,6 +407,15 @@ def main():
 
         for _ in range(warmup):
             step(False)
+        # kernels of one step: the factorization, one thin-Q launch per tree level plus the chain
+        # launch, and one Q^T b launch; with P > 1 panels (n > 64) also the staging copy, the
+        # trailing updates and the earlier panels' Q applied to the later column blocks
+        h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
+                             work.data_ptr(), nbytes, opts, sptr)
+        info = tsqr.tsqr_handle_info(h)
+        tsqr.tsqr_destroy(h)
+        P, d = info.panels, info.depth
+        launches = (P > 1) + P + (P - 1) + P * (d + 1) + (P - 1) * (d + 1) + P
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -387,7 +441,8 @@ def main():
             ms = t.item()
         be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
         orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Q.T @ Q).item()
-        return {"ms": ms, "ev": ev, "be": be, "orth": orth, "clocks": clocks, "opts": opts, "nbytes": nbytes}
+        return {"ms": ms, "ev": ev, "be": be, "orth": orth, "clocks": clocks, "opts": opts, "nbytes": nbytes,
+                "launches": launches}
 
     main_mode = run_mode(0, args.steps, args.warmup, True)
     ms = main_mode["ms"]
@@ -444,6 +499,10 @@ def main():
     if not args.no_batched and world == 1:
         batched = run_batched(tsqr, torch, dev, stream, sptr, args)
 
+    shapes = None
+    if not args.no_shapes and world == 1:
+        shapes = run_shapes(tsqr, torch, dev, stream, sptr, m)
+
     autograd = None
     if not args.no_autograd and world == 1:
         autograd = run_autograd(tsqr, torch, dev, args)
@@ -494,9 +553,9 @@ def main():
                           "parallelism": "replicas" if world > 1 else "single-gpu"},
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
-               "roofline": roofline, "precision_forms": forms, "batched": batched, "autograd": autograd, "cpu_baseline": cpu,
-               "e2e": e2e,
-               "gpu_launches": 3 * args.steps, "clocks": clocks}
+               "roofline": roofline, "precision_forms": forms, "batched": batched, "shapes": shapes,
+               "autograd": autograd, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": main_mode["launches"] * args.steps, "clocks": clocks}
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()

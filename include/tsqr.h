@@ -46,7 +46,7 @@ typedef void* tsqr_stream_t;                  /* a cudaStream_t */
 typedef enum {
   TSQR_OK = 0,
   TSQR_ERR_INVALID_ARG = 1, /* bad shape, stride, pointer alignment or option */
-  TSQR_ERR_UNSUPPORTED = 2, /* a valid request this build does not implement (e.g. n > 128) */
+  TSQR_ERR_UNSUPPORTED = 2, /* a valid request this build does not implement (e.g. n > 4096) */
   TSQR_ERR_CUDA = 3,        /* a CUDA runtime or driver call failed */
   TSQR_ERR_WORKSPACE = 4,   /* workspace missing or smaller than tsqr_workspace_size */
   TSQR_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up (see tsqr_status_poll) */
@@ -73,7 +73,8 @@ typedef struct {
 } tsqr_opts_t;
 
 /* Plan and storage of a factorization, for inspection and tests.  The pointers are device
- * pointers into the workspace (row-major FP64, np = n rounded up to a power of two >= 16). */
+ * pointers into the workspace (row-major FP64, np = n rounded up to a power of two >= 16).
+ * For n > 64 (panels > 1) every field but m, n and panels describes the first panel's TSQR. */
 typedef struct {
   int64_t m, n, np;
   int32_t leaf_h, chain, arity, depth; /* depth = levels of the tree above the chains */
@@ -87,6 +88,7 @@ typedef struct {
   const double* node_tau; /* tree_nodes x np */
   const double* node_t;   /* tree_nodes x np x np */
   const double* signs;    /* np: D = diag(sign(R_jj)) of the root, sign(0) = +1 */
+  int32_t panels;         /* 64-column panels of the factorization (1 when n <= 64) */
 } tsqr_info_t;
 
 /* Bytes of device workspace tsqr_factor needs for an m x n factorization with `opts`
@@ -96,6 +98,12 @@ tsqr_status_t tsqr_workspace_size(tsqr_dtype_t dtype, int64_t m, int64_t n, cons
 
 /* Factors A (m x n, m >= n >= 1, device, leading dimension lda >= n) into R and an implicit
  * Q (Algorithms 1 and 2, Sec. 3.1).  With inplace, lda must be even and A 16-byte aligned.
+ * n <= 64 is one TSQR.  64 < n <= 4096 is a right-looking blocked QR over panels of 64 columns
+ * (the panel factorization and trailing update of Sec. 6, Algorithm 3, on one GPU): panel p
+ * (columns 64p.., rows 64p..m-1 of the updated matrix) is one TSQR, its Q^T updates the
+ * trailing columns, and the top rows of that update are R's block row p.  A is then first
+ * copied into the workspace, unless inplace is set, in which case A holds the updated matrix
+ * and the panels' reflectors afterwards.
  *   dR     : device, n x n with ldr >= n; receives R with diag(R) >= 0, strict lower zeroed.
  *   dWork  : device workspace of at least tsqr_workspace_size bytes, 256-byte aligned.
  *   out    : receives a new handle (free with tsqr_destroy).  The handle records A's pointer
@@ -134,7 +142,8 @@ tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info);
  *   M = R Rbar^T - Qbar^T Q,  Abar = (Qbar + Q copyltu(M)) R^{-T},  copyltu(M) = tril(M) + tril(M,-1)^T,
  * with Q^T Qbar and Q copyltu(M) applied from the implicit Q (tsqr_apply_qt, tsqr_apply_q):
  * no explicit Q is needed.  R (n x n, ldr >= n) is the R that tsqr_factor returned.  A must have
- * full column rank (the derivative does not exist otherwise; a zero R_jj gives Inf/NaN). */
+ * full column rank (the derivative does not exist otherwise; a zero R_jj gives Inf/NaN).  The
+ * final solve keeps R in shared memory, so n > 154 returns TSQR_ERR_UNSUPPORTED. */
 tsqr_status_t tsqr_backward(tsqr_handle_t h, const void* dQbar, int64_t ldqb, const void* dRbar, int64_t ldrb,
                             const void* dR, int64_t ldr, void* dAbar, int64_t ldab, tsqr_stream_t stream);
 

@@ -44,6 +44,14 @@ struct tsqr_handle_s {
   CUtensorMap mapV;
   int box_rows;
   int inplace;
+  // n > 64: a right-looking blocked QR whose panels are TSQRs (the panel factorization and
+  // trailing update of Sec. 6, Algorithm 3, on one GPU).  Panel p covers columns c_p..c_p+w_p-1
+  // and rows c_p..m-1 of the updated matrix; Q = Q_0 diag(I, Q_1) diag(I, Q_2) ...
+  std::vector<tsqr_handle_s*> panels;
+  int64_t m = 0, n = 0;
+  ~tsqr_handle_s() {
+    for (tsqr_handle_s* p : panels) delete p;
+  }
 };
 
 namespace {
@@ -215,6 +223,98 @@ tsqr_status_t make_map(CUtensorMap* map, const void* ptr, int64_t m, int64_t n, 
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// ---- n > 64: panels of 64 columns ---------------------------------------------------------
+constexpr int64_t kPanel = 64;
+constexpr int64_t kMaxN = 4096;  // 64 panels; wider matrices are not tall-skinny
+
+struct PanelLayout {
+  int count = 0;
+  int64_t ldw = 0;              // leading dimension of the staged copy of A
+  std::vector<size_t> off, bytes;  // each panel's own TSQR workspace
+  size_t total = 0;
+};
+
+// Every panel is factored in place in the working copy of A (the staged copy, or A itself with
+// inplace), with the caller's tree options.
+tsqr_opts_t panel_opts(const tsqr_opts_t* o) {
+  tsqr_opts_t s{};
+  if (o) s = *o;
+  s.inplace = 1;
+  return s;
+}
+
+tsqr_status_t make_panel_layout(int64_t m, int64_t n, const tsqr_opts_t* o, PanelLayout* L) {
+  if (n > kMaxN) return fail(TSQR_ERR_UNSUPPORTED, "n > 4096 is not supported");
+  const bool inplace = o && o->inplace;
+  L->count = (int)((n + kPanel - 1) / kPanel);
+  L->ldw = (n + 1) / 2 * 2;
+  size_t off = inplace ? 0 : align256((size_t)m * L->ldw * 8);
+  const tsqr_opts_t so = panel_opts(o);
+  for (int p = 0; p < L->count; ++p) {
+    const int64_t c = p * kPanel, w = std::min(kPanel, n - c);
+    Plan P;
+    tsqr_status_t s = make_plan(m - c, w, &so, &P);
+    if (s != TSQR_OK) return fail(s, "panel " + std::to_string(p) + ": " + g_last_error);
+    const size_t b = make_layout(P, true).total;
+    L->off.push_back(off);
+    L->bytes.push_back(b);
+    off = align256(off + b);
+  }
+  L->total = off;
+  return TSQR_OK;
+}
+
+// Blocked factorization: panel p is a TSQR of the updated columns c_p.. (rows c_p..m-1), whose
+// Q^T then updates the trailing columns; the top w_p rows of that update are R's block row p.
+tsqr_status_t factor_panels(int64_t m, int64_t n, const void* dA, int64_t lda, double* R, int64_t ldr, void* dWork,
+                            size_t work_bytes, const tsqr_opts_t* opts, tsqr_stream_t stream, tsqr_handle_t* out) {
+  PanelLayout L;
+  tsqr_status_t s = make_panel_layout(m, n, opts, &L);
+  if (s != TSQR_OK) return s;
+  const bool inplace = opts && opts->inplace;
+  if (inplace && (lda % 2 != 0 || !aligned16(dA)))
+    return fail(TSQR_ERR_INVALID_ARG, "inplace needs an even lda and a 16-byte aligned A");
+  if (!dWork || work_bytes < L.total)
+    return fail(TSQR_ERR_WORKSPACE, "workspace needs " + std::to_string(L.total) + " bytes");
+  if ((reinterpret_cast<uintptr_t>(dWork) & 255) != 0) return fail(TSQR_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  char* w = static_cast<char*>(dWork);
+  double* Aw = inplace ? static_cast<double*>(const_cast<void*>(dA)) : reinterpret_cast<double*>(w);
+  const int64_t ldw = inplace ? lda : L.ldw;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (!inplace && (e = tsqr::launch_stage_copy(static_cast<const double*>(dA), lda, Aw, ldw, m, (int)n, cs)) != cudaSuccess)
+    return cuda_fail(e, "staging copy launch");
+  if ((e = cudaMemset2DAsync(R, (size_t)ldr * 8, 0, (size_t)n * 8, (size_t)n, cs)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemset2DAsync");
+  tsqr_handle_s* h = new (std::nothrow) tsqr_handle_s;
+  if (!h) return fail(TSQR_ERR_INVALID_ARG, "out of host memory");
+  h->m = m;
+  h->n = n;
+  h->inplace = inplace ? 1 : 0;
+  const tsqr_opts_t so = panel_opts(opts);
+  for (int p = 0; p < L.count; ++p) {
+    const int64_t c = p * kPanel, wp = std::min(kPanel, n - c), rest = n - c - wp;
+    tsqr_handle_t hp = nullptr;
+    s = tsqr_factor(TSQR_F64, TSQR_ROW_MAJOR, m - c, wp, Aw + c * ldw + c, ldw, R + c * ldr + c, ldr, w + L.off[p],
+                    L.bytes[p], &so, stream, &hp);
+    if (s == TSQR_OK) h->panels.push_back(hp);
+    if (s == TSQR_OK && rest > 0) {
+      double* trail = Aw + c * ldw + c + wp;
+      s = tsqr_apply_qt(hp, rest, trail, ldw, stream);
+      if (s == TSQR_OK &&
+          (e = cudaMemcpy2DAsync(R + c * ldr + c + wp, (size_t)ldr * 8, trail, (size_t)ldw * 8, (size_t)rest * 8,
+                                 (size_t)wp, cudaMemcpyDeviceToDevice, cs)) != cudaSuccess)
+        s = cuda_fail(e, "cudaMemcpy2DAsync");
+    }
+    if (s != TSQR_OK) {
+      delete h;
+      return s;
+    }
+  }
+  *out = h;
+  return TSQR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -236,6 +336,13 @@ const char* tsqr_last_error(void) { return g_last_error.c_str(); }
 tsqr_status_t tsqr_workspace_size(tsqr_dtype_t dtype, int64_t m, int64_t n, const tsqr_opts_t* opts, size_t* bytes) {
   if (!bytes) return fail(TSQR_ERR_INVALID_ARG, "bytes is NULL");
   if (dtype != TSQR_F64) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_F64 is implemented");
+  if (n > kPanel && m >= n) {
+    PanelLayout L;
+    tsqr_status_t s = make_panel_layout(m, n, opts, &L);
+    if (s != TSQR_OK) return s;
+    *bytes = L.total;
+    return TSQR_OK;
+  }
   Plan P;
   tsqr_status_t s = make_plan(m, n, opts, &P);
   if (s != TSQR_OK) return s;
@@ -255,6 +362,8 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
   if (lda < n) return fail(TSQR_ERR_INVALID_ARG, "lda must be >= n");
   if (ldr < n) return fail(TSQR_ERR_INVALID_ARG, "ldr must be >= n");
   if ((reinterpret_cast<uintptr_t>(dA) & 7) != 0) return fail(TSQR_ERR_INVALID_ARG, "A must be 8-byte aligned");
+  if (n > kPanel)
+    return factor_panels(m, n, dA, lda, static_cast<double*>(dR), ldr, dWork, work_bytes, opts, stream, out);
   Plan P;
   tsqr_status_t s = make_plan(m, n, opts, &P);
   if (s != TSQR_OK) return s;
@@ -311,6 +420,28 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
 
 tsqr_status_t tsqr_form_q(tsqr_handle_t h, void* dQ, int64_t ldq, tsqr_stream_t stream) {
   if (!h) return fail(TSQR_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->panels.empty()) {
+    // Q [I_n; 0], column block p: [0; thin Q_p] (rows c_p.. are untouched by the later panels'
+    // factors), then the earlier panels' factors applied innermost first.
+    if (!dQ || ldq < h->n) return fail(TSQR_ERR_INVALID_ARG, "Q must be non-NULL with ldq >= n");
+    double* Q = static_cast<double*>(dQ);
+    const int count = (int)h->panels.size();
+    for (int p = 0; p < count; ++p) {
+      const int64_t c = p * kPanel, wp = std::min(kPanel, h->n - c);
+      cudaError_t e;
+      if (c > 0 && (e = cudaMemset2DAsync(Q + c, (size_t)ldq * 8, 0, (size_t)wp * 8, (size_t)c,
+                                          static_cast<cudaStream_t>(stream))) != cudaSuccess)
+        return cuda_fail(e, "cudaMemset2DAsync");
+      tsqr_status_t s = tsqr_form_q(h->panels[p], Q + c * ldq + c, ldq, stream);
+      if (s != TSQR_OK) return s;
+    }
+    for (int p = count - 2; p >= 0; --p) {
+      const int64_t c = p * kPanel;
+      tsqr_status_t s = tsqr_apply_q(h->panels[p], h->n - c - kPanel, Q + c * ldq + c + kPanel, ldq, stream);
+      if (s != TSQR_OK) return s;
+    }
+    return TSQR_OK;
+  }
   if (!dQ || ldq < h->P.n) return fail(TSQR_ERR_INVALID_ARG, "Q must be non-NULL with ldq >= n");
   cudaError_t e = tsqr::launch_form_q(h->mapV, h->P, h->st, static_cast<double*>(dQ), ldq, h->box_rows,
                                       static_cast<cudaStream_t>(stream));
@@ -323,6 +454,14 @@ tsqr_status_t tsqr_apply_qt(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, t
   if (k < 0) return fail(TSQR_ERR_INVALID_ARG, "k must be >= 0");
   if (k == 0) return TSQR_OK;
   if (!dB || ldb < k) return fail(TSQR_ERR_INVALID_ARG, "B must be non-NULL with ldb >= k");
+  if (!h->panels.empty()) {  // Q^T = ... diag(I, Q_1^T) Q_0^T: panel p acts on rows c_p..
+    double* B = static_cast<double*>(dB);
+    for (size_t p = 0; p < h->panels.size(); ++p) {
+      tsqr_status_t s = tsqr_apply_qt(h->panels[p], k, B + (int64_t)p * kPanel * ldb, ldb, stream);
+      if (s != TSQR_OK) return s;
+    }
+    return TSQR_OK;
+  }
   cudaError_t e = tsqr::launch_apply_qt(h->mapV, h->P, h->st, k, static_cast<double*>(dB), ldb, h->box_rows,
                                         static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "apply_qt launch");
@@ -334,6 +473,14 @@ tsqr_status_t tsqr_apply_q(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, ts
   if (k < 0) return fail(TSQR_ERR_INVALID_ARG, "k must be >= 0");
   if (k == 0) return TSQR_OK;
   if (!dB || ldb < k) return fail(TSQR_ERR_INVALID_ARG, "B must be non-NULL with ldb >= k");
+  if (!h->panels.empty()) {  // Q = Q_0 diag(I, Q_1) ...: the last panel first
+    double* B = static_cast<double*>(dB);
+    for (size_t p = h->panels.size(); p-- > 0;) {
+      tsqr_status_t s = tsqr_apply_q(h->panels[p], k, B + (int64_t)p * kPanel * ldb, ldb, stream);
+      if (s != TSQR_OK) return s;
+    }
+    return TSQR_OK;
+  }
   cudaError_t e = tsqr::launch_apply_q(h->mapV, h->P, h->st, k, static_cast<double*>(dB), ldb, h->box_rows,
                                        static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "apply_q launch");
@@ -342,6 +489,13 @@ tsqr_status_t tsqr_apply_q(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, ts
 
 tsqr_status_t tsqr_status_poll(tsqr_handle_t h, tsqr_stream_t stream) {
   if (!h) return fail(TSQR_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->panels.empty()) {
+    for (tsqr_handle_s* p : h->panels) {
+      tsqr_status_t s = tsqr_status_poll(p, stream);
+      if (s != TSQR_OK) return s;
+    }
+    return TSQR_OK;
+  }
   int v = 0;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(&v, h->st.status, sizeof(int), cudaMemcpyDeviceToHost, cs);
@@ -353,6 +507,14 @@ tsqr_status_t tsqr_status_poll(tsqr_handle_t h, tsqr_stream_t stream) {
 
 tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info) {
   if (!h || !info) return fail(TSQR_ERR_INVALID_ARG, "NULL argument");
+  if (!h->panels.empty()) {  // the first panel's tree, with the whole matrix's shape
+    tsqr_status_t s = tsqr_handle_info(h->panels[0], info);
+    info->m = h->m;
+    info->n = h->n;
+    info->panels = (int32_t)h->panels.size();
+    return s;
+  }
+  info->panels = 1;
   const Plan& P = h->P;
   info->m = P.m;
   info->n = P.n;

@@ -34,21 +34,23 @@ __global__ void backward_small_kernel(int n, const double* __restrict__ R, int64
   }
 }
 
-// B <- B R^{-T} row by row: each row b solves R x = b by back substitution.  A block stages 128
-// rows through shared memory (coalesced loads and stores), one thread per row.
+// B <- B R^{-T} row by row: each row b solves R x = b by back substitution.  A block stages
+// blockDim.x rows (128, fewer when R is large) through shared memory (coalesced loads and
+// stores), one thread per row.
 constexpr int kSolveRows = 128;
 
 __global__ void __launch_bounds__(kSolveRows)
     trsm_rt_kernel(int64_t m, int n, const double* __restrict__ R, int64_t ldr, double* __restrict__ B, int64_t ldb) {
   extern __shared__ double sm[];
   const int ldt = n + 1;
+  const int block_rows = (int)blockDim.x;
   double* Rs = sm;                  // n x (n + 1)
   double* rinv = Rs + n * ldt;      // n
-  double* tile = rinv + n;          // kSolveRows x (n + 1)
+  double* tile = rinv + n;          // block_rows x (n + 1)
   for (int o = threadIdx.x; o < n * n; o += blockDim.x) Rs[(o / n) * ldt + o % n] = R[(int64_t)(o / n) * ldr + o % n];
   for (int i = threadIdx.x; i < n; i += blockDim.x) rinv[i] = 1.0 / R[(int64_t)i * ldr + i];
-  const int64_t r0 = (int64_t)blockIdx.x * kSolveRows;
-  const int rows = (int)((m - r0 < kSolveRows) ? (m - r0) : kSolveRows);
+  const int64_t r0 = (int64_t)blockIdx.x * block_rows;
+  const int rows = (int)((m - r0 < block_rows) ? (m - r0) : block_rows);
   for (int o = threadIdx.x; o < rows * n; o += blockDim.x) tile[(o / n) * ldt + o % n] = B[(r0 + o / n) * ldb + o % n];
   __syncthreads();
   if (threadIdx.x < rows) {
@@ -76,6 +78,13 @@ extern "C" tsqr_status_t tsqr_backward(tsqr_handle_t h, const void* dQbar, int64
   if (!dR || !dAbar) return internal_fail(TSQR_ERR_INVALID_ARG, "R and Abar must be non-NULL");
   if (ldr < n || ldab < n || (dQbar && ldqb < n) || (dRbar && ldrb < n))
     return internal_fail(TSQR_ERR_INVALID_ARG, "leading dimensions must be >= n");
+  // R (n x n) and a block of rows stay in shared memory for the solve
+  constexpr size_t kSmemLimit = 232448;
+  int solve_rows = kSolveRows;
+  auto solve_smem = [n](int rows) { return ((size_t)n * (n + 1) + n + (size_t)rows * (n + 1)) * 8; };
+  while (solve_rows > 32 && solve_smem(solve_rows) > kSmemLimit) solve_rows /= 2;
+  if (solve_smem(solve_rows) > kSmemLimit)
+    return internal_fail(TSQR_ERR_UNSUPPORTED, "tsqr_backward keeps R in shared memory: n must be <= 154");
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   // Z = Q_full^T Qbar (zero when the loss does not depend on Q)
@@ -86,18 +95,21 @@ extern "C" tsqr_status_t tsqr_backward(tsqr_handle_t h, const void* dQbar, int64
   if (e != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
   if (dQbar && (s = tsqr_apply_qt(h, n, dAbar, ldab, stream)) != TSQR_OK) return s;
   // Z_top += copyltu(R Rbar^T - Z_top^T)
-  backward_small_kernel<<<1, 256, (size_t)n * (n + 1) * 8, cs>>>(n, static_cast<const double*>(dR), ldr,
+  const size_t small_smem = (size_t)n * (n + 1) * 8;
+  e = cudaFuncSetAttribute(backward_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem);
+  if (e != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
+  backward_small_kernel<<<1, 256, small_smem, cs>>>(n, static_cast<const double*>(dR), ldr,
                                                                   static_cast<const double*>(dRbar), ldrb,
                                                                   static_cast<double*>(dAbar), ldab);
   if ((e = cudaGetLastError()) != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
   // B = Q_full Z = Qbar + Q copyltu(M)
   if ((s = tsqr_apply_q(h, n, dAbar, ldab, stream)) != TSQR_OK) return s;
   // Abar = B R^{-T}
-  const size_t smem = ((size_t)n * (n + 1) + n + (size_t)kSolveRows * (n + 1)) * 8;
+  const size_t smem = solve_smem(solve_rows);
   e = cudaFuncSetAttribute(trsm_rt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
-  const int64_t blocks = (m + kSolveRows - 1) / kSolveRows;
-  trsm_rt_kernel<<<(unsigned)blocks, kSolveRows, smem, cs>>>(m, n, static_cast<const double*>(dR), ldr,
+  const int64_t blocks = (m + solve_rows - 1) / solve_rows;
+  trsm_rt_kernel<<<(unsigned)blocks, solve_rows, smem, cs>>>(m, n, static_cast<const double*>(dR), ldr,
                                                              static_cast<double*>(dAbar), ldab);
   if ((e = cudaGetLastError()) != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
   return TSQR_OK;

@@ -38,7 +38,8 @@ class Info(ctypes.Structure):
                 ("leaves", ctypes.c_int64), ("chains", ctypes.c_int64), ("tree_nodes", ctypes.c_int64),
                 ("v", ctypes.c_void_p), ("ldv", ctypes.c_int64),
                 ("tau_leaf", ctypes.c_void_p), ("t_leaf", ctypes.c_void_p), ("node_y", ctypes.c_void_p),
-                ("node_tau", ctypes.c_void_p), ("node_t", ctypes.c_void_p), ("signs", ctypes.c_void_p)]
+                ("node_tau", ctypes.c_void_p), ("node_t", ctypes.c_void_p), ("signs", ctypes.c_void_p),
+                ("panels", ctypes.c_int32)]
 
 
 class TsqrError(RuntimeError):

@@ -50,7 +50,8 @@ def test_workspace_size_grows_with_m(lib):
 @pytest.mark.parametrize("m,n,opts,status", [
     (10, 20, None, 1),                      # m < n
     (100, 0, None, 1),                      # n < 1
-    (1000, 200, None, 2),                   # n > 64 not built yet
+    (10000, 5000, None, 2),                 # n > 4096
+    (1000, 200, {"precision": 3}, 2),       # every panel's plan is checked
     (1000, 16, {"arity": 1}, 1),
     (1000, 16, {"arity": 9}, 1),
     (1000, 16, {"leaf_h": 12}, 1),          # not a multiple of 8
@@ -115,3 +116,28 @@ def test_autotune_candidates_and_key(lib):
     assert all(o.leaf_h >= 64 for o in c)
     assert lib.tune_key(1 << 20, 50, 0) == (20, 64, 0)
     assert lib.tune_key(3 << 19, 9, 1) == (20, 16, 1)
+
+
+def test_panel_workspace(lib):
+    """n > 64: a staged copy of A plus one in-place TSQR workspace per 64-column panel."""
+    m = 100000
+    one = lib.tsqr_workspace_size(lib.TSQR_F64, m, 64, {"inplace": 1})
+    two = lib.tsqr_workspace_size(lib.TSQR_F64, m, 128)
+    two_inplace = lib.tsqr_workspace_size(lib.TSQR_F64, m, 128, {"inplace": 1})
+    assert two - two_inplace >= m * 128 * 8
+    assert two_inplace >= one + lib.tsqr_workspace_size(lib.TSQR_F64, m - 64, 64, {"inplace": 1})
+    # a 65th column adds a narrow panel
+    assert lib.tsqr_workspace_size(lib.TSQR_F64, m, 65, {"inplace": 1}) > one
+
+
+def test_panel_factor_rejects_before_launch(lib):
+    L = lib.load()
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)
+    inpl = lib.Opts(inplace=1)
+    # in place needs an even lda for the panels too
+    assert L.tsqr_factor(0, 0, 1000, 100, fake, 101, fake, 100, fake, 1 << 30, ctypes.byref(inpl), None,
+                         ctypes.byref(h)) == 1
+    # workspace too small
+    assert L.tsqr_factor(0, 0, 1000, 100, fake, 100, fake, 100, fake, 1 << 10, None, None, ctypes.byref(h)) == 4
+    assert h.value is None

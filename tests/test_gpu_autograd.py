@@ -60,7 +60,8 @@ def loss_only(T, A_h, W1, W2):
     return L.item()
 
 
-@pytest.mark.parametrize("m,n,prec", [(300, 7, 0), (2000, 16, 0), (5000, 40, 0), (3000, 32, 1), (4096, 64, 2)])
+@pytest.mark.parametrize("m,n,prec", [(300, 7, 0), (2000, 16, 0), (5000, 40, 0), (3000, 32, 1), (4096, 64, 2),
+                                      (6000, 128, 0), (3000 + 7, 100, 1), (2500, 154, 0)])
 def test_against_cpu_reference(T, m, n, prec):
     A_h = inputs.usv(m, n, 2.0, 700 + m)
     rng = np.random.default_rng(m + n)

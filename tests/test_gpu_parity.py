@@ -207,6 +207,55 @@ def test_apply_column_counts(T, k):
     assert np.abs(B.cpu().numpy() - B_h).max() <= 1e-12
 
 
+@pytest.mark.parametrize("m,n,opts", [(20000, 128, {}), (5000 + 33, 65, {"leaf_h": 128}),
+                                      (3001, 100, {"chain": 2, "arity": 3}), (2000, 200, {}), (300, 150, {}),
+                                      (129, 129, {}), (64 * 9 + 7, 128, {"leaf_h": 64, "chain": 1})])
+def test_panels_n_above_64(T, m, n, opts, prec):
+    """n > 64: right-looking blocked QR over 64-column TSQR panels (Sec. 6, Algorithm 3)."""
+    import torch
+
+    A_h = inputs.gaussian(m, n, inputs.seed_for(9, m + n))
+    f, R, Q = run(T, A_h, precision=prec, **opts)
+    assert f.info().panels == (n + 63) // 64
+    check_against_oracle(A_h, R, Q, precision=prec)
+    tol = 1e-11 if prec == 0 else 1e-10
+    k = 5
+    B_h = inputs.gaussian(m, k, inputs.seed_for(10, m + n))
+    B = torch.from_numpy(B_h.copy()).cuda()
+    f.apply_qt(B)
+    QtB = B.cpu().numpy()
+    assert np.abs(QtB[:n] - oracle.thin_qt(A_h, B_h)).max() <= tol
+    Ad = torch.from_numpy(A_h.copy()).cuda()
+    f.apply_qt(Ad)
+    QtA = Ad.cpu().numpy()
+    assert np.abs(QtA[:n] - R).max() <= tol * np.abs(R).max()
+    if m > n:
+        assert np.abs(QtA[n:]).max() <= tol * np.abs(R).max()
+    f.apply_q(B)
+    assert np.abs(B.cpu().numpy() - B_h).max() <= 100 * tol
+    E = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    E[:n] = torch.eye(n, dtype=torch.float64, device="cuda")
+    f.apply_q(E)
+    assert np.abs(E.cpu().numpy() - Q).max() <= 100 * n * UNIT[prec]
+
+
+def test_panels_staged_and_inplace(T):
+    """n > 64 with an odd lda (staged) and in place: the same arithmetic, bitwise."""
+    import torch
+
+    m, n = 4000, 96
+    A_h = inputs.gaussian(m, n, 812)
+    _, R1, Q1 = run(T, A_h)
+    _, R2, Q2 = run(T, A_h, lda=n + 1)
+    assert np.array_equal(R1, R2) and np.array_equal(Q1, Q2)
+    A = torch.from_numpy(A_h.copy()).cuda()
+    f = T.Factorization(A, inplace=True)
+    Q3 = f.form_q()
+    torch.cuda.synchronize()
+    assert np.array_equal(f.R.cpu().numpy(), R1) and np.array_equal(Q3.cpu().numpy(), Q1)
+    check_against_oracle(A_h, R1, Q1)
+
+
 def test_node_structure_eq_fact_2rs(T):
     """Tree-node reflectors: lower blocks upper triangular (eq. fact_2rs), T upper triangular."""
     A_h = inputs.gaussian(2048, 16, 5)
