@@ -47,6 +47,11 @@ def load_peaks():
         return {}
 
 
+# DRAM bytes (read + write) of one factor_kernel<ArithF64> launch, from an ncu capture at
+# m = 524288, n = 64 (701.2 MB), scaled by rows to m = 4194304: A is read once and V and T are
+# written once, so traffic grows in proportion to m.  Only valid for the kernel as captured.
+FACTOR_F64_TRAFFIC = {(4194304, 64): 8 * 701.19e6}
+
 # FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -336,6 +341,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-matrix batched workload")
     ap.add_argument("--no-autograd", action="store_true", help="skip the differentiable-QR workload")
     ap.add_argument("--no-shapes", action="store_true", help="skip the n = 16, 32, 128 shapes")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="arithmetic mode of the main line (0 native FP64; 1 and 2 are for profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -444,7 +451,7 @@ def main():
         return {"ms": ms, "ev": ev, "be": be, "orth": orth, "clocks": clocks, "opts": opts, "nbytes": nbytes,
                 "launches": launches}
 
-    main_mode = run_mode(0, args.steps, args.warmup, True)
+    main_mode = run_mode(args.precision, args.steps, args.warmup, True)
     ms = main_mode["ms"]
     ev = main_mode["ev"]
     clocks = main_mode["clocks"]
@@ -469,7 +476,9 @@ def main():
     hbm = peaks.get("hbm_gbs")
     ab = algorithmic_bytes(m, n)
     roofline = {"bound": "alu", "kernel": dom + "_kernel", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                "traffic": FACTOR_F64_TRAFFIC.get((m, n)) if (dom == "factor" and args.precision == 0) else None,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": "FP64 pipe, 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
                 "hbm_view": {"achieved_gbs": ab[dom] / (dom_ms / 1e3) / 1e9, "peak_gbs": hbm,
                              "frac_of_measured": (ab[dom] / (dom_ms / 1e3) / 1e9 / hbm) if hbm else None}}
@@ -546,10 +555,10 @@ def main():
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "vs_baseline": None, "dtype": {0: "f64", 1: "f32x2", 2: "f64"}[args.precision], "data": "synthetic",
                "config": {"workload": "tsqr factor + form_q + apply_qt(k=1), fp64, m=%d n=%d, A=U S V^T kappa=1"
                                       % (m, n), "m": m, "n": n, "k": 1, "leaf_h": None, "chain": "auto",
-                          "arity": 2, "l2": "inputs larger than L2 (A is %.1f GB)" % (8.0 * m * n / 1e9),
+                          "arity": 2, "precision": args.precision, "l2": "inputs larger than L2 (A is %.1f GB)" % (8.0 * m * n / 1e9),
                           "parallelism": "replicas" if world > 1 else "single-gpu"},
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
