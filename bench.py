@@ -384,10 +384,16 @@ def main():
     sptr = tsqr.ctypes.c_void_p(stream.cuda_stream)
     work_holder = {}
 
-    def run_mode(precision, steps, warmup, sample_clocks):
-        """Times `steps` full steps in one arithmetic mode; returns timings and accuracy."""
+    def run_mode(precision, steps, warmup, sample_clocks, f32=False):
+        """Times `steps` full steps in one arithmetic mode (f32: FP32 storage, the float32
+        rounding of the same A); returns timings and accuracy."""
         opts = tsqr.Opts(precision=precision)
-        nbytes = tsqr.tsqr_workspace_size(tsqr.TSQR_F64, m, n, opts)
+        code = tsqr.TSQR_F32 if f32 else tsqr.TSQR_F64
+        if f32:
+            A_, Q_, R_, b_ = A.float(), Q.float(), R.float(), b.float()
+        else:
+            A_, Q_, R_, b_ = A, Q, R, b
+        nbytes = tsqr.tsqr_workspace_size(code, m, n, opts)
         if work_holder.get("bytes", 0) < nbytes:
             work_holder.pop("t", None)
             torch.cuda.empty_cache()
@@ -399,14 +405,14 @@ def main():
             marks = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
             if record:
                 marks[0].record(stream)
-            h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
+            h = tsqr.tsqr_factor(code, tsqr.TSQR_ROW_MAJOR, m, n, A_.data_ptr(), n, R_.data_ptr(), n,
                                  work.data_ptr(), nbytes, opts, sptr)
             if record:
                 marks[1].record(stream)
-            tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
+            tsqr.tsqr_form_q(h, Q_.data_ptr(), n, sptr)
             if record:
                 marks[2].record(stream)
-            tsqr.tsqr_apply_qt(h, 1, b.data_ptr(), 1, sptr)
+            tsqr.tsqr_apply_qt(h, 1, b_.data_ptr(), 1, sptr)
             if record:
                 marks[3].record(stream)
             tsqr.tsqr_destroy(h)
@@ -417,7 +423,7 @@ def main():
         # kernels of one step: the factorization, one thin-Q launch per tree level plus the chain
         # launch, and one Q^T b launch; with P > 1 panels (n > 64) also the staging copy, the
         # trailing updates and the earlier panels' Q applied to the later column blocks
-        h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
+        h = tsqr.tsqr_factor(code, tsqr.TSQR_ROW_MAJOR, m, n, A_.data_ptr(), n, R_.data_ptr(), n,
                              work.data_ptr(), nbytes, opts, sptr)
         info = tsqr.tsqr_handle_info(h)
         tsqr.tsqr_destroy(h)
@@ -446,8 +452,10 @@ def main():
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = t.item()
-        be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
-        orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Q.T @ Q).item()
+        Ad, Qd, Rd = A_.double(), Q_.double(), R_.double()
+        be = (torch.linalg.norm(Ad - Qd @ Rd) / torch.linalg.norm(Ad)).item()
+        orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Qd.T @ Qd).item()
+        del Ad, Qd, Rd
         return {"ms": ms, "ev": ev, "be": be, "orth": orth, "clocks": clocks, "opts": opts, "nbytes": nbytes,
                 "launches": launches}
 
@@ -501,6 +509,15 @@ def main():
             "kernel_ms": {k: statistics.mean(v) for k, v in ozm["ev"].items()},
             "backward_error": ozm["be"], "orthogonality": ozm["orth"],
             "note": "native FP64 factor; thin-Q products T*C and Y*M on tcgen05 tensor cores as Ozaki splits"}
+        f3 = run_mode(0, args.steps, min(args.warmup, 3), False, f32=True)
+        s_ms = f3["ms"] / args.steps
+        forms["fp32"] = {
+            "dtype": "f32", "value": per_step * world / (s_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+            "ms_per_step": s_ms, "speedup_vs_f64": ms_step / s_ms,
+            "kernel_ms": {k: statistics.mean(v) for k, v in f3["ev"].items()},
+            "backward_error": f3["be"], "orthogonality": f3["orth"],
+            "note": "FP32 storage (A rounded to float32, R, Q, b float32) and FP32 arithmetic; "
+                    "measures against the float32 A, bar 5e-5"}
         opts = tsqr.Opts(precision=0)
 
     # batched TSQR: 512 uneven matrices in one persistent launch (CUDA graph) vs a per-matrix loop

@@ -12,9 +12,10 @@
  * or Q B (a broadcast), or expanded to the explicit thin Q (Sec. 7.2).
  *
  * Conventions shared by every call:
- *   - Matrices are FP64, row-major: element (i, j) of X with leading dimension ldx is
- *     X[i * ldx + j], 8-byte aligned.  A is read by TMA, which needs a 16-byte aligned base
- *     and an even lda; any other A is first copied into the workspace by a staging kernel.
+ *   - Matrices are row-major FP64 (or FP32 with TSQR_F32): element (i, j) of X with leading
+ *     dimension ldx is X[i * ldx + j], aligned to its element size.  A is read by TMA, which
+ *     needs a 16-byte aligned base and an even lda; any other A is first copied into the
+ *     workspace by a staging kernel.
  *   - Reflectors are H = I - tau v v^T with v_0 = 1; beta = -sign(alpha) ||x||, sign(0) = +1.
  *   - R is returned with a non-negative diagonal: D = diag(sign(R_jj)), R <- D R and the
  *     thin Q <- Q D (the QR is unique only up to these signs, Sec. 2).
@@ -52,6 +53,11 @@ typedef enum {
   TSQR_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up (see tsqr_status_poll) */
 } tsqr_status_t;
 
+/* TSQR_F64: A, R, Q and B are binary64, arithmetic per tsqr_opts_t.precision.
+ * TSQR_F32: A, R, Q and B are binary32 and every operation is binary32 (the FP32-level form of
+ * the precision forms: backward error and loss of orthogonality of order n * 2^-24).  A is
+ * widened into the workspace first (it is never overwritten: inplace is not supported), and
+ * precision must be 0.  tsqr_backward and the batch calls take TSQR_F64 only. */
 typedef enum { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype_t;
 typedef enum { TSQR_ROW_MAJOR = 0, TSQR_COL_MAJOR = 1 } tsqr_layout_t;
 
@@ -89,6 +95,7 @@ typedef struct {
   const double* node_t;   /* tree_nodes x np x np */
   const double* signs;    /* np: D = diag(sign(R_jj)) of the root, sign(0) = +1 */
   int32_t panels;         /* 64-column panels of the factorization (1 when n <= 64) */
+  int32_t dtype;          /* tsqr_dtype_t of A, R, Q and B */
 } tsqr_info_t;
 
 /* Bytes of device workspace tsqr_factor needs for an m x n factorization with `opts`

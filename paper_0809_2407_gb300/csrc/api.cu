@@ -49,6 +49,7 @@ struct tsqr_handle_s {
   // and rows c_p..m-1 of the updated matrix; Q = Q_0 diag(I, Q_1) diag(I, Q_2) ...
   std::vector<tsqr_handle_s*> panels;
   int64_t m = 0, n = 0;
+  int f32 = 0;  // FP32 storage (A, R, Q and B are float)
   ~tsqr_handle_s() {
     for (tsqr_handle_s* p : panels) delete p;
   }
@@ -90,8 +91,9 @@ int default_leaf_h(int np) {
   }
 }
 
-// Builds the plan of an m x n factorization; see Plan in common.cuh.
-tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P) {
+// Builds the plan of an m x n factorization; see Plan in common.cuh.  FP32 storage (f32) runs
+// the FP32 arithmetic, Plan::precision 3.
+tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P, bool f32 = false) {
   tsqr_opts_t d{};
   if (!o) o = &d;
   if (n < 1 || m < n) return fail(TSQR_ERR_INVALID_ARG, "need m >= n >= 1");
@@ -100,6 +102,9 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P) {
   if (np > 64) return fail(TSQR_ERR_UNSUPPORTED, "n > 64 is not supported by this build");
   if (o->precision < 0 || o->precision > 2)
     return fail(TSQR_ERR_UNSUPPORTED, "precision must be 0 (native FP64), 1 (double-float) or 2 (Ozaki WY)");
+  if (f32 && o->precision != 0)
+    return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 runs FP32 arithmetic: precision must be 0");
+  if (f32 && o->inplace) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 keeps A read-only (inplace is not supported)");
   const int arity = o->arity ? o->arity : 2;
   if (arity < 2 || arity > tsqr::kMaxArity) return fail(TSQR_ERR_INVALID_ARG, "arity must be in 2..8");
   int h = o->leaf_h ? o->leaf_h : default_leaf_h(np);
@@ -112,7 +117,7 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P) {
   P->np = np;
   P->h = h;
   P->arity = arity;
-  P->precision = o->precision;
+  P->precision = f32 ? 3 : o->precision;
   P->leaves = (m + h - 1) / h;
   int64_t chain = o->chain;
   if (chain == 0) {
@@ -243,19 +248,23 @@ tsqr_opts_t panel_opts(const tsqr_opts_t* o) {
   return s;
 }
 
-tsqr_status_t make_panel_layout(int64_t m, int64_t n, const tsqr_opts_t* o, PanelLayout* L) {
+// FP32 storage: the working copy of A is float and every panel keeps its reflectors in its own
+// workspace (the FP32 factorization widens its input into it).
+tsqr_status_t make_panel_layout(int64_t m, int64_t n, const tsqr_opts_t* o, PanelLayout* L, bool f32 = false) {
   if (n > kMaxN) return fail(TSQR_ERR_UNSUPPORTED, "n > 4096 is not supported");
+  if (f32 && o && o->inplace) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 keeps A read-only (inplace is not supported)");
   const bool inplace = o && o->inplace;
   L->count = (int)((n + kPanel - 1) / kPanel);
   L->ldw = (n + 1) / 2 * 2;
-  size_t off = inplace ? 0 : align256((size_t)m * L->ldw * 8);
-  const tsqr_opts_t so = panel_opts(o);
+  size_t off = inplace ? 0 : align256((size_t)m * L->ldw * (f32 ? 4 : 8));
+  tsqr_opts_t so = panel_opts(o);
+  if (f32) so.inplace = 0;
   for (int p = 0; p < L->count; ++p) {
     const int64_t c = p * kPanel, w = std::min(kPanel, n - c);
     Plan P;
-    tsqr_status_t s = make_plan(m - c, w, &so, &P);
+    tsqr_status_t s = make_plan(m - c, w, &so, &P, f32);
     if (s != TSQR_OK) return fail(s, "panel " + std::to_string(p) + ": " + g_last_error);
-    const size_t b = make_layout(P, true).total;
+    const size_t b = make_layout(P, !f32).total;
     L->off.push_back(off);
     L->bytes.push_back(b);
     off = align256(off + b);
@@ -266,10 +275,13 @@ tsqr_status_t make_panel_layout(int64_t m, int64_t n, const tsqr_opts_t* o, Pane
 
 // Blocked factorization: panel p is a TSQR of the updated columns c_p.. (rows c_p..m-1), whose
 // Q^T then updates the trailing columns; the top w_p rows of that update are R's block row p.
-tsqr_status_t factor_panels(int64_t m, int64_t n, const void* dA, int64_t lda, double* R, int64_t ldr, void* dWork,
-                            size_t work_bytes, const tsqr_opts_t* opts, tsqr_stream_t stream, tsqr_handle_t* out) {
+tsqr_status_t factor_panels(tsqr_dtype_t dtype, int64_t m, int64_t n, const void* dA, int64_t lda, void* dR,
+                            int64_t ldr, void* dWork, size_t work_bytes, const tsqr_opts_t* opts, tsqr_stream_t stream,
+                            tsqr_handle_t* out) {
+  const bool f32 = dtype == TSQR_F32;
+  const size_t es = f32 ? 4 : 8;  // element size of A, R and the working copy
   PanelLayout L;
-  tsqr_status_t s = make_panel_layout(m, n, opts, &L);
+  tsqr_status_t s = make_panel_layout(m, n, opts, &L, f32);
   if (s != TSQR_OK) return s;
   const bool inplace = opts && opts->inplace;
   if (inplace && (lda % 2 != 0 || !aligned16(dA)))
@@ -278,31 +290,40 @@ tsqr_status_t factor_panels(int64_t m, int64_t n, const void* dA, int64_t lda, d
     return fail(TSQR_ERR_WORKSPACE, "workspace needs " + std::to_string(L.total) + " bytes");
   if ((reinterpret_cast<uintptr_t>(dWork) & 255) != 0) return fail(TSQR_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   char* w = static_cast<char*>(dWork);
-  double* Aw = inplace ? static_cast<double*>(const_cast<void*>(dA)) : reinterpret_cast<double*>(w);
+  char* Aw = inplace ? static_cast<char*>(const_cast<void*>(dA)) : w;
   const int64_t ldw = inplace ? lda : L.ldw;
+  char* R = static_cast<char*>(dR);
+  auto at = [es](char* base, int64_t ld, int64_t r, int64_t c) { return base + (r * ld + c) * (int64_t)es; };
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (!inplace && (e = tsqr::launch_stage_copy(static_cast<const double*>(dA), lda, Aw, ldw, m, (int)n, cs)) != cudaSuccess)
-    return cuda_fail(e, "staging copy launch");
-  if ((e = cudaMemset2DAsync(R, (size_t)ldr * 8, 0, (size_t)n * 8, (size_t)n, cs)) != cudaSuccess)
+  if (!inplace) {
+    if (f32)
+      e = cudaMemcpy2DAsync(Aw, (size_t)ldw * 4, dA, (size_t)lda * 4, (size_t)n * 4, (size_t)m, cudaMemcpyDeviceToDevice, cs);
+    else
+      e = tsqr::launch_stage_copy(static_cast<const double*>(dA), lda, reinterpret_cast<double*>(Aw), ldw, m, (int)n, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "staging copy");
+  }
+  if ((e = cudaMemset2DAsync(R, (size_t)ldr * es, 0, (size_t)n * es, (size_t)n, cs)) != cudaSuccess)
     return cuda_fail(e, "cudaMemset2DAsync");
   tsqr_handle_s* h = new (std::nothrow) tsqr_handle_s;
   if (!h) return fail(TSQR_ERR_INVALID_ARG, "out of host memory");
   h->m = m;
   h->n = n;
   h->inplace = inplace ? 1 : 0;
-  const tsqr_opts_t so = panel_opts(opts);
+  h->f32 = f32 ? 1 : 0;
+  tsqr_opts_t so = panel_opts(opts);
+  if (f32) so.inplace = 0;
   for (int p = 0; p < L.count; ++p) {
     const int64_t c = p * kPanel, wp = std::min(kPanel, n - c), rest = n - c - wp;
     tsqr_handle_t hp = nullptr;
-    s = tsqr_factor(TSQR_F64, TSQR_ROW_MAJOR, m - c, wp, Aw + c * ldw + c, ldw, R + c * ldr + c, ldr, w + L.off[p],
+    s = tsqr_factor(dtype, TSQR_ROW_MAJOR, m - c, wp, at(Aw, ldw, c, c), ldw, at(R, ldr, c, c), ldr, w + L.off[p],
                     L.bytes[p], &so, stream, &hp);
     if (s == TSQR_OK) h->panels.push_back(hp);
     if (s == TSQR_OK && rest > 0) {
-      double* trail = Aw + c * ldw + c + wp;
+      char* trail = at(Aw, ldw, c, c + wp);
       s = tsqr_apply_qt(hp, rest, trail, ldw, stream);
       if (s == TSQR_OK &&
-          (e = cudaMemcpy2DAsync(R + c * ldr + c + wp, (size_t)ldr * 8, trail, (size_t)ldw * 8, (size_t)rest * 8,
+          (e = cudaMemcpy2DAsync(at(R, ldr, c, c + wp), (size_t)ldr * es, trail, (size_t)ldw * es, (size_t)rest * es,
                                  (size_t)wp, cudaMemcpyDeviceToDevice, cs)) != cudaSuccess)
         s = cuda_fail(e, "cudaMemcpy2DAsync");
     }
@@ -335,16 +356,17 @@ const char* tsqr_last_error(void) { return g_last_error.c_str(); }
 
 tsqr_status_t tsqr_workspace_size(tsqr_dtype_t dtype, int64_t m, int64_t n, const tsqr_opts_t* opts, size_t* bytes) {
   if (!bytes) return fail(TSQR_ERR_INVALID_ARG, "bytes is NULL");
-  if (dtype != TSQR_F64) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_F64 is implemented");
+  if (dtype != TSQR_F64 && dtype != TSQR_F32) return fail(TSQR_ERR_INVALID_ARG, "unknown dtype");
+  const bool f32 = dtype == TSQR_F32;
   if (n > kPanel && m >= n) {
     PanelLayout L;
-    tsqr_status_t s = make_panel_layout(m, n, opts, &L);
+    tsqr_status_t s = make_panel_layout(m, n, opts, &L, f32);
     if (s != TSQR_OK) return s;
     *bytes = L.total;
     return TSQR_OK;
   }
   Plan P;
-  tsqr_status_t s = make_plan(m, n, opts, &P);
+  tsqr_status_t s = make_plan(m, n, opts, &P, f32);
   if (s != TSQR_OK) return s;
   *bytes = make_layout(P, opts && opts->inplace).total;
   return TSQR_OK;
@@ -355,22 +377,25 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
                           tsqr_stream_t stream, tsqr_handle_t* out) {
   if (!out) return fail(TSQR_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (dtype != TSQR_F64) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_F64 is implemented");
+  if (dtype != TSQR_F64 && dtype != TSQR_F32) return fail(TSQR_ERR_INVALID_ARG, "unknown dtype");
+  const bool f32 = dtype == TSQR_F32;
   if (layout != TSQR_ROW_MAJOR) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_ROW_MAJOR is implemented");
   if (!dA || !dR) return fail(TSQR_ERR_INVALID_ARG, "A and R must be non-NULL");
   if (n < 1 || m < n) return fail(TSQR_ERR_INVALID_ARG, "need m >= n >= 1");
   if (lda < n) return fail(TSQR_ERR_INVALID_ARG, "lda must be >= n");
   if (ldr < n) return fail(TSQR_ERR_INVALID_ARG, "ldr must be >= n");
-  if ((reinterpret_cast<uintptr_t>(dA) & 7) != 0) return fail(TSQR_ERR_INVALID_ARG, "A must be 8-byte aligned");
-  if (n > kPanel)
-    return factor_panels(m, n, dA, lda, static_cast<double*>(dR), ldr, dWork, work_bytes, opts, stream, out);
+  const uintptr_t amask = f32 ? 3 : 7;
+  if ((reinterpret_cast<uintptr_t>(dA) & amask) != 0 || (reinterpret_cast<uintptr_t>(dR) & amask) != 0)
+    return fail(TSQR_ERR_INVALID_ARG, f32 ? "A and R must be 4-byte aligned" : "A and R must be 8-byte aligned");
+  if (n > kPanel) return factor_panels(dtype, m, n, dA, lda, dR, ldr, dWork, work_bytes, opts, stream, out);
   Plan P;
-  tsqr_status_t s = make_plan(m, n, opts, &P);
+  tsqr_status_t s = make_plan(m, n, opts, &P, f32);
   if (s != TSQR_OK) return s;
   const bool inplace = opts && opts->inplace;
   // TMA needs a 16-byte aligned base and a row stride that is a multiple of 16 bytes; any other A
   // is first copied into the reflector storage of the workspace (which then holds V as usual).
-  const bool stage = (lda % 2 != 0) || !aligned16(dA);
+  // FP32 input is always widened into it.
+  const bool stage = f32 || (lda % 2 != 0) || !aligned16(dA);
   if (stage && inplace)
     return fail(TSQR_ERR_INVALID_ARG, "inplace needs an even lda and a 16-byte aligned A");
   const Layout L = make_layout(P, inplace);
@@ -402,10 +427,11 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
   cudaError_t e = cudaMemsetAsync(st.status, 0, sizeof(int), cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   if (stage) {
-    e = tsqr::launch_stage_copy(static_cast<const double*>(dA), lda, st.v, st.ldv, m, (int)n, cs);
+    e = f32 ? tsqr::launch_stage_widen(static_cast<const float*>(dA), lda, st.v, st.ldv, m, (int)n, cs)
+            : tsqr::launch_stage_copy(static_cast<const double*>(dA), lda, st.v, st.ldv, m, (int)n, cs);
     if (e != cudaSuccess) return cuda_fail(e, "staging copy launch");
   }
-  e = tsqr::launch_factor(mapA, mapV, P, st, static_cast<double*>(dR), ldr, box_rows, cs);
+  e = tsqr::launch_factor(mapA, mapV, P, st, dR, ldr, box_rows, cs);
   if (e != cudaSuccess) return cuda_fail(e, "factor launch");
   tsqr_handle_s* h = new (std::nothrow) tsqr_handle_s;
   if (!h) return fail(TSQR_ERR_INVALID_ARG, "out of host memory");
@@ -414,6 +440,9 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
   h->mapV = mapV;
   h->box_rows = box_rows;
   h->inplace = inplace ? 1 : 0;
+  h->f32 = f32 ? 1 : 0;
+  h->m = m;
+  h->n = n;
   *out = h;
   return TSQR_OK;
 }
@@ -424,26 +453,27 @@ tsqr_status_t tsqr_form_q(tsqr_handle_t h, void* dQ, int64_t ldq, tsqr_stream_t 
     // Q [I_n; 0], column block p: [0; thin Q_p] (rows c_p.. are untouched by the later panels'
     // factors), then the earlier panels' factors applied innermost first.
     if (!dQ || ldq < h->n) return fail(TSQR_ERR_INVALID_ARG, "Q must be non-NULL with ldq >= n");
-    double* Q = static_cast<double*>(dQ);
+    char* Q = static_cast<char*>(dQ);
+    const int64_t es = h->f32 ? 4 : 8;
     const int count = (int)h->panels.size();
     for (int p = 0; p < count; ++p) {
       const int64_t c = p * kPanel, wp = std::min(kPanel, h->n - c);
       cudaError_t e;
-      if (c > 0 && (e = cudaMemset2DAsync(Q + c, (size_t)ldq * 8, 0, (size_t)wp * 8, (size_t)c,
+      if (c > 0 && (e = cudaMemset2DAsync(Q + c * es, (size_t)(ldq * es), 0, (size_t)(wp * es), (size_t)c,
                                           static_cast<cudaStream_t>(stream))) != cudaSuccess)
         return cuda_fail(e, "cudaMemset2DAsync");
-      tsqr_status_t s = tsqr_form_q(h->panels[p], Q + c * ldq + c, ldq, stream);
+      tsqr_status_t s = tsqr_form_q(h->panels[p], Q + (c * ldq + c) * es, ldq, stream);
       if (s != TSQR_OK) return s;
     }
     for (int p = count - 2; p >= 0; --p) {
       const int64_t c = p * kPanel;
-      tsqr_status_t s = tsqr_apply_q(h->panels[p], h->n - c - kPanel, Q + c * ldq + c + kPanel, ldq, stream);
+      tsqr_status_t s = tsqr_apply_q(h->panels[p], h->n - c - kPanel, Q + (c * ldq + c + kPanel) * es, ldq, stream);
       if (s != TSQR_OK) return s;
     }
     return TSQR_OK;
   }
   if (!dQ || ldq < h->P.n) return fail(TSQR_ERR_INVALID_ARG, "Q must be non-NULL with ldq >= n");
-  cudaError_t e = tsqr::launch_form_q(h->mapV, h->P, h->st, static_cast<double*>(dQ), ldq, h->box_rows,
+  cudaError_t e = tsqr::launch_form_q(h->mapV, h->P, h->st, dQ, ldq, h->box_rows,
                                       static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "form_q launch");
   return TSQR_OK;
@@ -455,14 +485,15 @@ tsqr_status_t tsqr_apply_qt(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, t
   if (k == 0) return TSQR_OK;
   if (!dB || ldb < k) return fail(TSQR_ERR_INVALID_ARG, "B must be non-NULL with ldb >= k");
   if (!h->panels.empty()) {  // Q^T = ... diag(I, Q_1^T) Q_0^T: panel p acts on rows c_p..
-    double* B = static_cast<double*>(dB);
+    char* B = static_cast<char*>(dB);
+    const int64_t es = h->f32 ? 4 : 8;
     for (size_t p = 0; p < h->panels.size(); ++p) {
-      tsqr_status_t s = tsqr_apply_qt(h->panels[p], k, B + (int64_t)p * kPanel * ldb, ldb, stream);
+      tsqr_status_t s = tsqr_apply_qt(h->panels[p], k, B + (int64_t)p * kPanel * ldb * es, ldb, stream);
       if (s != TSQR_OK) return s;
     }
     return TSQR_OK;
   }
-  cudaError_t e = tsqr::launch_apply_qt(h->mapV, h->P, h->st, k, static_cast<double*>(dB), ldb, h->box_rows,
+  cudaError_t e = tsqr::launch_apply_qt(h->mapV, h->P, h->st, k, dB, ldb, h->box_rows,
                                         static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "apply_qt launch");
   return TSQR_OK;
@@ -474,14 +505,15 @@ tsqr_status_t tsqr_apply_q(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, ts
   if (k == 0) return TSQR_OK;
   if (!dB || ldb < k) return fail(TSQR_ERR_INVALID_ARG, "B must be non-NULL with ldb >= k");
   if (!h->panels.empty()) {  // Q = Q_0 diag(I, Q_1) ...: the last panel first
-    double* B = static_cast<double*>(dB);
+    char* B = static_cast<char*>(dB);
+    const int64_t es = h->f32 ? 4 : 8;
     for (size_t p = h->panels.size(); p-- > 0;) {
-      tsqr_status_t s = tsqr_apply_q(h->panels[p], k, B + (int64_t)p * kPanel * ldb, ldb, stream);
+      tsqr_status_t s = tsqr_apply_q(h->panels[p], k, B + (int64_t)p * kPanel * ldb * es, ldb, stream);
       if (s != TSQR_OK) return s;
     }
     return TSQR_OK;
   }
-  cudaError_t e = tsqr::launch_apply_q(h->mapV, h->P, h->st, k, static_cast<double*>(dB), ldb, h->box_rows,
+  cudaError_t e = tsqr::launch_apply_q(h->mapV, h->P, h->st, k, dB, ldb, h->box_rows,
                                        static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "apply_q launch");
   return TSQR_OK;
@@ -515,6 +547,7 @@ tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info) {
     return s;
   }
   info->panels = 1;
+  info->dtype = h->f32 ? TSQR_F32 : TSQR_F64;
   const Plan& P = h->P;
   info->m = P.m;
   info->n = P.n;

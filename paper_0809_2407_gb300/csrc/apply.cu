@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1) formq_tree_kernel(const Plan P, c
 // then C -= M.  first leaf (V unit lower trapezoidal): Q_rows = [C; 0] - V (T (V_top^T C)).
 template <class Ar>
 __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Plan& P, const Store& st,
-                                            double* __restrict__ Q, int64_t ldq, int box_rows, int g,
+                                            typename Ar::Out* __restrict__ Q, int64_t ldq, int box_rows, int g,
                                             char* smem_raw) {
   using E = typename Ar::E;
   FormQSmem<E> f = carve_formq<E>(smem_raw, P);
@@ -182,7 +182,7 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
         for (int r = gown; r < rows_valid; r += G) {
           E v = Ar::zero();
           for (int a = 0; a < n; ++a) Ar::fma_acc(v, tat<E>(S, r, a), f.M[a * ld + cown]);
-          Q[(row0 + r) * ldq + cown] = -Ar::to_f64(Ar::add(v, Ar::zero()));
+          Q[(row0 + r) * ldq + cown] = -Ar::to_out(Ar::add(v, Ar::zero()));
         }
       }
       for (int i = tid; i < np * np; i += kThreads) {
@@ -214,7 +214,7 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
           if (r < n) Ar::fma_acc(acc, Ar::from_int(1), f.M[r * ld + cown]);
           E v = Ar::neg(Ar::add(acc, Ar::zero()));
           if (r < n) v = Ar::add(v, f.C[r * ld + cown]);
-          Q[(row0 + r) * ldq + cown] = Ar::to_f64(v);
+          Q[(row0 + r) * ldq + cown] = Ar::to_out(v);
         }
       }
       __syncthreads();
@@ -224,8 +224,8 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
 
 template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1)
-    formq_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
-                 int64_t ldq, int box_rows) {
+    formq_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st,
+                 typename Ar::Out* __restrict__ Q, int64_t ldq, int box_rows) {
   extern __shared__ char smem_raw[];
   formq_chain<Ar>(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
 }
@@ -736,21 +736,21 @@ __device__ inline void wy_update(const Tile& S, bool plain, int h, int n, int np
 }
 
 template <class Ar>
-__device__ inline void load_b(const double* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k, int64_t row0,
-                              int rows, int64_t col0, int kb, typename Ar::E* Bs) {
+__device__ inline void load_b(const typename Ar::Out* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k,
+                              int64_t row0, int rows, int64_t col0, int kb, typename Ar::E* Bs) {
   for (int o = threadIdx.x; o < rows * kb; o += kThreads) {
     const int r = o / kb, b = o % kb;
     const int64_t gr = row0 + r, gc = col0 + b;
-    Bs[o] = Ar::from_f64((gr < m && gc < k) ? __ldcg(Bg + gr * ldb + gc) : 0.0);
+    Bs[o] = (gr < m && gc < k) ? Ar::from_out(__ldcg(Bg + gr * ldb + gc)) : Ar::zero();
   }
 }
 template <class Ar>
-__device__ inline void store_b(double* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k, int64_t row0, int r_begin,
-                               int rows, int64_t col0, int kb, const typename Ar::E* Bs) {
+__device__ inline void store_b(typename Ar::Out* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k, int64_t row0,
+                               int r_begin, int rows, int64_t col0, int kb, const typename Ar::E* Bs) {
   for (int o = threadIdx.x; o < (rows - r_begin) * kb; o += kThreads) {
     const int r = r_begin + o / kb, b = o % kb;
     const int64_t gr = row0 + r, gc = col0 + b;
-    if (gr < m && gc < k) Bg[gr * ldb + gc] = Ar::to_f64(Bs[r * kb + b]);
+    if (gr < m && gc < k) Bg[gr * ldb + gc] = Ar::to_out(Bs[r * kb + b]);
   }
 }
 
@@ -806,7 +806,7 @@ __device__ inline int64_t node_top_row(const Plan& P, int level, int idx) {
 template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1)
     apply_qt_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, int64_t k,
-                    double* __restrict__ Bg, int64_t ldb, int kb, int box_rows) {
+                    typename Ar::Out* __restrict__ Bg, int64_t ldb, int kb, int box_rows) {
   using E = typename Ar::E;
   extern __shared__ char smem_raw[];
   ApplySmem<E> f = carve_apply<E>(smem_raw, P, kb);
@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int o = tid; o < np * kb; o += kThreads) {
         const int a = o / kb, b = o % kb;
         const int64_t gc = col0 + b;
-        f.B[(size_t)s * np * kb + o] = Ar::from_f64((a < n && gc < k) ? __ldcg(Bg + (top + a) * ldb + gc) : 0.0);
+        f.B[(size_t)s * np * kb + o] = (a < n && gc < k) ? Ar::from_out(__ldcg(Bg + (top + a) * ldb + gc)) : Ar::zero();
       }
     }
     __syncthreads();
@@ -878,15 +878,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   const E* topblk = (P.depth == 0) ? f.C : f.B;
   for (int o = tid; o < n * kb; o += kThreads) {
     const int a = o / kb, b = o % kb;
-    if (col0 + b < k) Bg[(int64_t)a * ldb + col0 + b] = __ldcg(st.signs + a) * Ar::to_f64(topblk[o]);
+    if (col0 + b < k) Bg[(int64_t)a * ldb + col0 + b] = (typename Ar::Out)__ldcg(st.signs + a) * Ar::to_out(topblk[o]);
   }
 }
 
 // ---- Q B, tree part: one launch per level, top-down; the root level first applies D.
 template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1)
-    apply_q_tree_kernel(const Plan P, const Store st, int level, int64_t k, double* __restrict__ Bg, int64_t ldb,
-                        int kb) {
+    apply_q_tree_kernel(const Plan P, const Store st, int level, int64_t k, typename Ar::Out* __restrict__ Bg,
+                        int64_t ldb, int kb) {
   using E = typename Ar::E;
   extern __shared__ char smem_raw[];
   ApplySmem<E> f = carve_apply<E>(smem_raw, P, kb);
@@ -902,9 +902,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int o = tid; o < np * kb; o += kThreads) {
       const int a = o / kb, b = o % kb;
       const int64_t gc = col0 + b;
-      double v = (a < n && gc < k) ? Bg[(top + a) * ldb + gc] : 0.0;
-      if (level == P.depth && s == 0 && a < n) v *= st.signs[a];
-      f.B[(size_t)s * np * kb + o] = Ar::from_f64(v);
+      typename Ar::Out v = (a < n && gc < k) ? Bg[(top + a) * ldb + gc] : typename Ar::Out(0);
+      if (level == P.depth && s == 0 && a < n) v *= (typename Ar::Out)st.signs[a];
+      f.B[(size_t)s * np * kb + o] = Ar::from_out(v);
     }
   }
   __syncthreads();
@@ -918,7 +918,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1)
     apply_q_chain_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, int64_t k,
-                         double* __restrict__ Bg, int64_t ldb, int kb, int box_rows) {
+                         typename Ar::Out* __restrict__ Bg, int64_t ldb, int kb, int box_rows) {
   using E = typename Ar::E;
   extern __shared__ char smem_raw[];
   ApplySmem<E> f = carve_apply<E>(smem_raw, P, kb);
@@ -934,9 +934,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int o = tid; o < np * kb; o += kThreads) {
     const int a = o / kb, b = o % kb;
     const int64_t gc = col0 + b;
-    double v = (a < n && gc < k) ? Bg[(top + a) * ldb + gc] : 0.0;
-    if (P.depth == 0 && a < n) v *= st.signs[a];
-    f.C[o] = Ar::from_f64(v);
+    typename Ar::Out v = (a < n && gc < k) ? Bg[(top + a) * ldb + gc] : typename Ar::Out(0);
+    if (P.depth == 0 && a < n) v *= (typename Ar::Out)st.signs[a];
+    f.C[o] = Ar::from_out(v);
   }
   __syncthreads();
   uint32_t phase = 0;
@@ -968,8 +968,9 @@ static int pick_kb(int64_t k) {
 }
 
 template <class Ar>
-static cudaError_t launch_form_q_t(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,
+static cudaError_t launch_form_q_t(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q_, int64_t ldq,
                                    int box_rows, cudaStream_t stream) {
+  typename Ar::Out* Q = static_cast<typename Ar::Out*>(Q_);
   const size_t smem = formq_smem_bytes(P);
   cudaError_t e = cudaFuncSetAttribute(formq_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -984,8 +985,9 @@ static cudaError_t launch_form_q_t(const CUtensorMap& mapV, const Plan& P, const
   return cudaGetLastError();
 }
 
-static cudaError_t launch_form_q_ozaki(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q,
+static cudaError_t launch_form_q_ozaki(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q_,
                                        int64_t ldq, int box_rows, cudaStream_t stream) {
+  double* Q = static_cast<double*>(Q_);
   const size_t smem_tree = formq_smem_bytes(P);
   cudaError_t e =
       cudaFuncSetAttribute(formq_tree_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tree);
@@ -1004,16 +1006,18 @@ static cudaError_t launch_form_q_ozaki(const CUtensorMap& mapV, const Plan& P, c
 
 bool ozaki_form_q_applies(const Plan& P) { return P.precision == 2 && P.np == 64 && P.h <= 128; }
 
-cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,
+cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q, int64_t ldq,
                           int box_rows, cudaStream_t stream) {
   if (P.precision == 1) return launch_form_q_t<ArithDF>(mapV, P, st, Q, ldq, box_rows, stream);
+  if (P.precision == 3) return launch_form_q_t<ArithF32>(mapV, P, st, Q, ldq, box_rows, stream);
   if (ozaki_form_q_applies(P)) return launch_form_q_ozaki(mapV, P, st, Q, ldq, box_rows, stream);
   return launch_form_q_t<ArithF64>(mapV, P, st, Q, ldq, box_rows, stream);
 }
 
 template <class Ar>
-static cudaError_t launch_apply_qt_t(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+static cudaError_t launch_apply_qt_t(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B_,
                                      int64_t ldb, int box_rows, cudaStream_t stream) {
+  typename Ar::Out* B = static_cast<typename Ar::Out*>(B_);
   const int kb = pick_kb(k);
   const size_t smem = apply_smem_bytes(P, kb);
   cudaError_t e = cudaFuncSetAttribute(apply_qt_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1031,15 +1035,17 @@ static cudaError_t launch_apply_qt_t(const CUtensorMap& mapV, const Plan& P, con
   return cudaSuccess;
 }
 
-cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B,
                             int64_t ldb, int box_rows, cudaStream_t stream) {
   if (P.precision == 1) return launch_apply_qt_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
+  if (P.precision == 3) return launch_apply_qt_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);
   return launch_apply_qt_t<ArithF64>(mapV, P, st, k, B, ldb, box_rows, stream);
 }
 
 template <class Ar>
-static cudaError_t launch_apply_q_t(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+static cudaError_t launch_apply_q_t(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B_,
                                     int64_t ldb, int box_rows, cudaStream_t stream) {
+  typename Ar::Out* B = static_cast<typename Ar::Out*>(B_);
   const int kb = pick_kb(k);
   const size_t smem = apply_smem_bytes(P, kb);
   cudaError_t e =
@@ -1064,9 +1070,10 @@ static cudaError_t launch_apply_q_t(const CUtensorMap& mapV, const Plan& P, cons
   return cudaSuccess;
 }
 
-cudaError_t launch_apply_q(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+cudaError_t launch_apply_q(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B,
                            int64_t ldb, int box_rows, cudaStream_t stream) {
   if (P.precision == 1) return launch_apply_q_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
+  if (P.precision == 3) return launch_apply_q_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);
   return launch_apply_q_t<ArithF64>(mapV, P, st, k, B, ldb, box_rows, stream);
 }
 

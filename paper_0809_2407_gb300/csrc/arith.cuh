@@ -15,8 +15,13 @@
 //           Range: magnitudes within about [2^-100, 2^100] keep full accuracy (FP32 exponent
 //           range); sums of squares are taken after a power-of-two rescaling.
 //
-// Both store an element in 8 bytes, so the shared-memory tile layout, the TMA descriptors and
-// the workspace are shared; in double-float mode the workspace holds (hi, lo) pairs.
+// ArithF32: IEEE binary32 arithmetic for FP32 storage (A, R, Q and B are float): each value is
+//           the hi half of a pair whose lo half stays zero, so that it shares the 8-byte
+//           element of the other policies.
+//
+// All store an element in 8 bytes, so the shared-memory tile layout, the TMA descriptors and
+// the workspace are shared; in double-float mode the workspace holds (hi, lo) pairs.  Out is the
+// type of the caller's R, Q and B.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,9 +31,12 @@ namespace tsqr {
 
 struct ArithF64 {
   using E = double;
+  using Out = double;
   static constexpr int kPrecision = 0;
   __device__ __forceinline__ static E from_f64(double x) { return x; }
   __device__ __forceinline__ static double to_f64(E x) { return x; }
+  __device__ __forceinline__ static E from_out(Out x) { return x; }
+  __device__ __forceinline__ static Out to_out(E x) { return x; }
   __device__ __forceinline__ static E zero() { return 0.0; }
   __device__ __forceinline__ static E from_int(int v) { return (double)v; }
   // s += a * b
@@ -50,6 +58,7 @@ struct __align__(8) f32x2 {
 
 struct ArithDF {
   using E = f32x2;
+  using Out = double;
   static constexpr int kPrecision = 1;
 
   // Knuth TwoSum: a + b = s + e exactly.
@@ -76,6 +85,8 @@ struct ArithDF {
     return E{h, __double2float_rn(x - (double)h)};
   }
   __device__ __forceinline__ static double to_f64(E x) { return (double)x.hi + (double)x.lo; }
+  __device__ __forceinline__ static E from_out(Out x) { return from_f64(x); }
+  __device__ __forceinline__ static Out to_out(E x) { return to_f64(x); }
   __device__ __forceinline__ static E zero() { return E{0.f, 0.f}; }
   __device__ __forceinline__ static E from_int(int v) { return E{(float)v, 0.f}; }
   // s += a * b, with s left unnormalised (hi carries the running TwoSum, lo the errors)
@@ -138,6 +149,31 @@ struct ArithDF {
     const float s = __int_as_float((127 + k) << 23);
     return E{__fmul_rn(x.hi, s), __fmul_rn(x.lo, s)};
   }
+};
+
+struct ArithF32 {
+  using E = f32x2;  // lo == 0
+  using Out = float;
+  static constexpr int kPrecision = 3;
+  __device__ __forceinline__ static E mk(float v) { return E{v, 0.f}; }
+  __device__ __forceinline__ static E from_f64(double x) { return mk(__double2float_rn(x)); }
+  __device__ __forceinline__ static double to_f64(E x) { return (double)x.hi; }
+  __device__ __forceinline__ static E from_out(Out x) { return mk(x); }
+  __device__ __forceinline__ static Out to_out(E x) { return x.hi; }
+  __device__ __forceinline__ static E zero() { return mk(0.f); }
+  __device__ __forceinline__ static E from_int(int v) { return mk((float)v); }
+  __device__ __forceinline__ static void fma_acc(E& s, E a, E b) { s.hi = __fmaf_rn(a.hi, b.hi, s.hi); }
+  __device__ __forceinline__ static E add(E a, E b) { return mk(__fadd_rn(a.hi, b.hi)); }
+  __device__ __forceinline__ static E sub(E a, E b) { return mk(__fsub_rn(a.hi, b.hi)); }
+  __device__ __forceinline__ static E mul(E a, E b) { return mk(__fmul_rn(a.hi, b.hi)); }
+  __device__ __forceinline__ static E neg(E a) { return mk(-a.hi); }
+  // a - w * y
+  __device__ __forceinline__ static E axpy(E a, E w, E y) { return mk(__fmaf_rn(-w.hi, y.hi, a.hi)); }
+  __device__ __forceinline__ static E shfl_xor(E v, int o) { return mk(__shfl_xor_sync(0xffffffffu, v.hi, o)); }
+  __device__ __forceinline__ static bool is_zero(E x) { return x.hi == 0.f; }
+  __device__ __forceinline__ static bool is_neg(E x) { return x.hi < 0.f; }
+  // x * 2^k exactly, k chosen so no under/overflow occurs
+  __device__ __forceinline__ static E ldexp(E x, int k) { return mk(__fmul_rn(x.hi, __int_as_float((127 + k) << 23))); }
 };
 
 }  // namespace tsqr

@@ -73,6 +73,7 @@ extern "C" tsqr_status_t tsqr_backward(tsqr_handle_t h, const void* dQbar, int64
   tsqr_info_t info;
   tsqr_status_t s = tsqr_handle_info(h, &info);
   if (s != TSQR_OK) return s;
+  if (info.dtype != TSQR_F64) return internal_fail(TSQR_ERR_UNSUPPORTED, "tsqr_backward needs a TSQR_F64 factorization");
   const int64_t m = info.m;
   const int n = (int)info.n;
   if (!dR || !dAbar) return internal_fail(TSQR_ERR_INVALID_ARG, "R and Abar must be non-NULL");

@@ -79,7 +79,8 @@ __device__ inline void convert_rows_in(const Tile& S, int r0, int rows, int np) 
 // Chain g of one factorization, then the tree above it while this block arrives last.
 template <class Ar>
 __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CUtensorMap* mapV_p, const Plan& P,
-                                             const Store& st, double* __restrict__ R_out, int64_t ldr, int box_rows,
+                                             const Store& st, typename Ar::Out* __restrict__ R_out, int64_t ldr,
+                                             int box_rows,
                                              int g, char* smem_raw) {
   using E = typename Ar::E;
   FactorSmem<E> f = carve_factor<E>(smem_raw, P);
@@ -188,17 +189,18 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
   // ---- root: R <- D R with D = diag(sign(R_jj)), sign(0) = +1
   __syncthreads();
   for (int j = tid; j < np; j += kThreads) st.signs[j] = (j < n && Ar::is_neg(at<E>(S, j, j))) ? -1.0 : 1.0;
+  using Out = typename Ar::Out;
   for (int i = tid; i < n * n; i += kThreads) {
     const int r = i / n, c = i % n;
-    const double d = Ar::is_neg(at<E>(S, r, r)) ? -1.0 : 1.0;
-    R_out[(int64_t)r * ldr + c] = (c >= r) ? d * Ar::to_f64(at<E>(S, r, c)) : 0.0;
+    const Out d = Ar::is_neg(at<E>(S, r, r)) ? Out(-1) : Out(1);
+    R_out[(int64_t)r * ldr + c] = (c >= r) ? d * Ar::to_out(at<E>(S, r, c)) : Out(0);
   }
 }
 
 template <class Ar>
 __global__ void __launch_bounds__(kThreads, 2)
     factor_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, const Plan P,
-                  const Store st, double* __restrict__ R_out, int64_t ldr, int box_rows) {
+                  const Store st, typename Ar::Out* __restrict__ R_out, int64_t ldr, int box_rows) {
   extern __shared__ char smem_raw[];
   factor_chain<Ar>(&mapA, &mapV, P, st, R_out, ldr, box_rows, blockIdx.x, smem_raw);
 }
@@ -230,13 +232,14 @@ cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work,
 
 template <class Ar>
 static cudaError_t launch_factor_t(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
-                                   double* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
+                                   void* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
   const size_t smem = factor_smem_bytes(P);
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(st.counters, 0, sizeof(int) * (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1), stream);
   if (e != cudaSuccess) return e;
-  factor_kernel<Ar><<<P.chains, kThreads, smem, stream>>>(mapA, mapV, P, st, R_out, ldr, box_rows);
+  factor_kernel<Ar><<<P.chains, kThreads, smem, stream>>>(mapA, mapV, P, st, static_cast<typename Ar::Out*>(R_out),
+                                                          ldr, box_rows);
   return cudaGetLastError();
 }
 
@@ -258,9 +261,28 @@ cudaError_t launch_stage_copy(const double* A, int64_t lda, double* V, int64_t l
   return cudaGetLastError();
 }
 
+// FP32 storage: A (float, m x n, leading dimension lda) widened exactly into V's 8-byte slots, from
+// which the factorization loads its tiles as for FP64 input.
+__global__ void stage_widen_kernel(const float* __restrict__ A, int64_t lda, double* __restrict__ V, int64_t ldv,
+                                   int64_t m, int n) {
+  const int64_t total = m * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n;
+    const int c = (int)(i - r * n);
+    V[r * ldv + c] = (double)A[r * lda + c];
+  }
+}
+
+cudaError_t launch_stage_widen(const float* A, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
+                               cudaStream_t stream) {
+  stage_widen_kernel<<<152 * 8, 256, 0, stream>>>(A, lda, V, ldv, m, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
-                          double* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
+                          void* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
   if (P.precision == 1) return launch_factor_t<ArithDF>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
+  if (P.precision == 3) return launch_factor_t<ArithF32>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
   return launch_factor_t<ArithF64>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
 }
 

@@ -13,8 +13,11 @@ bool ozaki_form_q_applies(const Plan& P);
 
 cudaError_t launch_stage_copy(const double* A, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
                               cudaStream_t stream);
+cudaError_t launch_stage_widen(const float* A, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
+                               cudaStream_t stream);
+// R_out, Q and B are double*, or float* when P.precision == 3 (FP32 storage)
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
-                          double* R_out, int64_t ldr, int box_rows, cudaStream_t stream);
+                          void* R_out, int64_t ldr, int box_rows, cudaStream_t stream);
 cudaError_t prepare_factor_batched(int precision, size_t smem);
 cudaError_t prepare_form_q_batched(int precision, size_t smem);
 cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work, int blocks, int precision,
@@ -22,11 +25,11 @@ cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work,
 cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain_work, int chain_blocks,
                                   const BatchWork* const* level_work, const int* level_blocks, int depth,
                                   int precision, size_t smem, cudaStream_t stream);
-cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, double* Q, int64_t ldq,
+cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q, int64_t ldq,
                           int box_rows, cudaStream_t stream);
-cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B,
                             int64_t ldb, int box_rows, cudaStream_t stream);
-cudaError_t launch_apply_q(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
+cudaError_t launch_apply_q(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B,
                            int64_t ldb, int box_rows, cudaStream_t stream);
 
 }  // namespace tsqr

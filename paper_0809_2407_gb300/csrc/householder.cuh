@@ -151,6 +151,52 @@ __device__ inline void reflector_warp<ArithDF>(const Tile& S, int kind, int N, i
   }
 }
 
+// FP32: the column is rescaled by 2^k from its largest magnitude before the squares are summed,
+// so the sum of squares cannot overflow or lose the column to underflow.
+template <>
+__device__ inline void reflector_warp<ArithF32>(const Tile& S, int kind, int N, int np, int j, f32x2* sc) {
+  using E = f32x2;
+  const int lane = threadIdx.x & 31;
+  const int r_lo = first_row(kind, j, np);
+  float tmx = 0.f;
+  for (int r = r_lo + lane; r < N; r += 32) {
+    if (skip_row(kind, r, j, np)) continue;
+    tmx = fmaxf(tmx, fabsf(at<E>(S, r, j).hi));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tmx = fmaxf(tmx, __shfl_xor_sync(0xffffffffu, tmx, o));
+  const float alpha = at<E>(S, j, j).hi;
+  float beta = alpha, tau = 0.f, inv = 0.f;
+  const bool active = tmx != 0.f;
+  if (active) {
+    const float mx = fmaxf(tmx, fabsf(alpha));
+    const int bexp = (__float_as_int(mx) >> 23) & 0xff;
+    int k = 126 - bexp;  // mx * 2^k in [0.5, 1)
+    k = k < -126 ? -126 : (k > 126 ? 126 : k);
+    const float up = __int_as_float((127 + k) << 23);
+    float ss = 0.f;
+    for (int r = r_lo + lane; r < N; r += 32) {
+      if (skip_row(kind, r, j, np)) continue;
+      const float x = __fmul_rn(at<E>(S, r, j).hi, up);
+      ss = __fmaf_rn(x, x, ss);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss = __fadd_rn(ss, __shfl_xor_sync(0xffffffffu, ss, o));
+    const float as = __fmul_rn(alpha, up);
+    ss = __fmaf_rn(as, as, ss);
+    const float nrm = __fmul_rn(__fsqrt_rn(ss), __int_as_float((127 - k) << 23));
+    beta = alpha < 0.f ? nrm : -nrm;
+    tau = __fdiv_rn(__fsub_rn(beta, alpha), beta);
+    inv = __fdiv_rn(1.f, __fsub_rn(alpha, beta));
+  }
+  if (lane == 0) {
+    sc[0] = E{beta, 0.f};
+    sc[1] = E{tau, 0.f};
+    sc[2] = E{inv, 0.f};
+    sc[3] = E{active ? 1.f : 0.f, 0.f};
+  }
+}
+
 // Warp 0 builds the reflector of column j, then the block synchronises.
 template <class Ar>
 __device__ inline void make_reflector(const Tile& S, int kind, int N, int np, int j, typename Ar::E* sc) {

@@ -39,7 +39,7 @@ class Info(ctypes.Structure):
                 ("v", ctypes.c_void_p), ("ldv", ctypes.c_int64),
                 ("tau_leaf", ctypes.c_void_p), ("t_leaf", ctypes.c_void_p), ("node_y", ctypes.c_void_p),
                 ("node_tau", ctypes.c_void_p), ("node_t", ctypes.c_void_p), ("signs", ctypes.c_void_p),
-                ("panels", ctypes.c_int32)]
+                ("panels", ctypes.c_int32), ("dtype", ctypes.c_int32)]
 
 
 class TsqrError(RuntimeError):
@@ -205,18 +205,23 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _check_matrix(X, name):
+def _check_matrix(X, name, dtype=None):
     import torch
 
-    if not (X.is_cuda and X.dtype == torch.float64 and X.dim() == 2 and X.stride(1) == 1):
-        raise ValueError("%s must be a CUDA float64 matrix with unit column stride" % name)
+    ok = (torch.float64, torch.float32) if dtype is None else (dtype,)
+    if not (X.is_cuda and X.dtype in ok and X.dim() == 2 and X.stride(1) == 1):
+        raise ValueError("%s must be a CUDA %s matrix with unit column stride"
+                         % (name, " or ".join(str(t).replace("torch.", "") for t in ok)))
 
 
 class Factorization:
-    """TSQR of a CUDA float64 matrix A (m x n, row-major).  Holds R, the workspace and the handle.
+    """TSQR of a CUDA float64 or float32 matrix A (m x n, row-major).  Holds R, the workspace and
+    the handle.  A float32 A selects TSQR_F32 (FP32 storage and arithmetic); R, Q and the
+    matrices given to apply_qt / apply_q then are float32 too.
 
-    ``inplace=True`` lets the reflectors overwrite A (A must then stay alive).  Options:
-    leaf_h, chain, arity, precision (0 native FP64, 1 double-float; see tsqr_opts_t).
+    ``inplace=True`` lets the reflectors overwrite A (A must then stay alive; float64 only).
+    Options: leaf_h, chain, arity, precision (0 native FP64, 1 double-float, 2 Ozaki WY products;
+    see tsqr_opts_t).
     """
 
     def __init__(self, A, leaf_h=0, chain=0, arity=0, inplace=False, precision=0):
@@ -225,31 +230,33 @@ class Factorization:
         _check_matrix(A, "A")
         m, n = A.shape
         self.m, self.n = m, n
+        self.dtype = A.dtype
+        self.code = TSQR_F32 if A.dtype == torch.float32 else TSQR_F64
         self.opts = Opts(leaf_h=leaf_h, chain=chain, arity=arity, precision=precision, inplace=1 if inplace else 0)
-        nbytes = tsqr_workspace_size(TSQR_F64, m, n, self.opts)
+        nbytes = tsqr_workspace_size(self.code, m, n, self.opts)
         self.work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=A.device)
-        self.R = torch.empty((n, n), dtype=torch.float64, device=A.device)
+        self.R = torch.empty((n, n), dtype=A.dtype, device=A.device)
         self.A = A
-        self.handle = tsqr_factor(TSQR_F64, TSQR_ROW_MAJOR, m, n, A.data_ptr(), A.stride(0), self.R.data_ptr(), n,
+        self.handle = tsqr_factor(self.code, TSQR_ROW_MAJOR, m, n, A.data_ptr(), A.stride(0), self.R.data_ptr(), n,
                                   self.work.data_ptr(), nbytes, self.opts, _stream())
 
     def form_q(self, out=None):
         import torch
 
-        Q = out if out is not None else torch.empty((self.m, self.n), dtype=torch.float64, device=self.R.device)
-        _check_matrix(Q, "Q")
+        Q = out if out is not None else torch.empty((self.m, self.n), dtype=self.dtype, device=self.R.device)
+        _check_matrix(Q, "Q", self.dtype)
         tsqr_form_q(self.handle, Q.data_ptr(), Q.stride(0), _stream())
         return Q
 
     def apply_qt(self, B):
-        """B <- Q^T B in place (B: m x k CUDA float64, unit column stride)."""
-        _check_matrix(B, "B")
+        """B <- Q^T B in place (B: m x k CUDA matrix of A's dtype, unit column stride)."""
+        _check_matrix(B, "B", self.dtype)
         tsqr_apply_qt(self.handle, B.shape[1], B.data_ptr(), B.stride(0), _stream())
         return B
 
     def apply_q(self, B):
         """B <- Q B in place."""
-        _check_matrix(B, "B")
+        _check_matrix(B, "B", self.dtype)
         tsqr_apply_q(self.handle, B.shape[1], B.data_ptr(), B.stride(0), _stream())
         return B
 
@@ -290,7 +297,7 @@ class Batch:
         import torch
 
         for i, A in enumerate(mats):
-            _check_matrix(A, "A[%d]" % i)
+            _check_matrix(A, "A[%d]" % i, torch.float64)
         self.mats = list(mats)
         dev = self.mats[0].device
         self.m = [A.shape[0] for A in self.mats]

@@ -80,9 +80,17 @@ def test_factor_rejects_before_launch(lib):
                          ctypes.byref(h)) == 1
     assert L.tsqr_factor(0, 0, 100, 4, ctypes.c_void_p(0x1008), 4, fake, 4, fake, 1 << 20, ctypes.byref(inpl),
                          None, ctypes.byref(h)) == 1
-    # FP32 and column-major are not implemented
-    assert L.tsqr_factor(1, 0, 100, 4, fake, 4, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 2
+    # column-major is not implemented; FP32 keeps A read-only, runs precision 0 only, and checks
+    # its workspace and 4-byte alignment like FP64
     assert L.tsqr_factor(0, 1, 100, 4, fake, 4, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 2
+    assert L.tsqr_factor(1, 0, 100, 4, fake, 4, fake, 4, fake, 1 << 20, ctypes.byref(inpl), None,
+                         ctypes.byref(h)) == 2
+    assert L.tsqr_factor(1, 0, 100, 4, fake, 4, fake, 4, fake, 1 << 20, ctypes.byref(lib.Opts(precision=1)), None,
+                         ctypes.byref(h)) == 2
+    assert L.tsqr_factor(1, 0, 100, 4, fake, 4, fake, 4, fake, 16, None, None, ctypes.byref(h)) == 4
+    assert L.tsqr_factor(1, 0, 100, 4, ctypes.c_void_p(0x1002), 4, fake, 4, fake, 1 << 20, None, None,
+                         ctypes.byref(h)) == 1
+    assert L.tsqr_factor(7, 0, 100, 4, fake, 4, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 1
     # workspace too small
     assert L.tsqr_factor(0, 0, 100, 4, fake, 4, fake, 4, fake, 16, None, None, ctypes.byref(h)) == 4
     assert h.value is None
@@ -128,6 +136,20 @@ def test_panel_workspace(lib):
     assert two_inplace >= one + lib.tsqr_workspace_size(lib.TSQR_F64, m - 64, 64, {"inplace": 1})
     # a 65th column adds a narrow panel
     assert lib.tsqr_workspace_size(lib.TSQR_F64, m, 65, {"inplace": 1}) > one
+
+
+def test_f32_workspace(lib):
+    """FP32 storage: A is always widened into the workspace, so its size matches FP64's non-inplace
+    layout; batches and in-place factorizations stay FP64 only."""
+    for m, n in [(4096, 16), (100000, 64), (100000, 100)]:
+        assert lib.tsqr_workspace_size(lib.TSQR_F32, m, n) > 0
+    assert lib.tsqr_workspace_size(lib.TSQR_F32, 100000, 64) == lib.tsqr_workspace_size(lib.TSQR_F64, 100000, 64)
+    with pytest.raises(lib.TsqrError) as ei:
+        lib.tsqr_workspace_size(lib.TSQR_F32, 1000, 16, {"inplace": 1})
+    assert ei.value.status == 2
+    with pytest.raises(lib.TsqrError) as ei:
+        lib.tsqr_batch_workspace_size(lib.TSQR_F32, 1, [1000], [16])
+    assert ei.value.status == 2
 
 
 def test_panel_factor_rejects_before_launch(lib):

@@ -385,3 +385,95 @@ def test_autotune_returns_valid_plan(T):
     _, R, Q = run(T, A_h, leaf_h=o.leaf_h, chain=o.chain, arity=o.arity)
     check_against_oracle(A_h, R, Q)
     assert T.autotune(20000, 24) is not None  # cached
+
+
+# ---- FP32 storage (TSQR_F32): FP32-level bar, 5e-5 on backward error and orthogonality -------
+TOL_F32 = 5e-5
+U32 = 2.0 ** -24
+
+
+def run32(T, A64, lda=None, offset=0, **opts):
+    """Factor the float32 rounding of A64; returns the handle, R and Q as float64 arrays."""
+    import torch
+
+    m, n = A64.shape
+    lda = lda or n
+    buf = torch.zeros(m * lda + offset, dtype=torch.float32, device="cuda")
+    A = buf[offset:offset + m * lda].view(m, lda)[:, :n]
+    A.copy_(torch.from_numpy(A64.astype(np.float32)))
+    f = T.Factorization(A, **opts)
+    Q = f.form_q()
+    torch.cuda.synchronize()
+    assert f.status() == T.TSQR_OK
+    assert f.R.dtype == torch.float32 and Q.dtype == torch.float32
+    assert np.array_equal(A.cpu().numpy(), A64.astype(np.float32))  # A is read only
+    return f, f.R.cpu().numpy().astype(np.float64), Q.cpu().numpy().astype(np.float64)
+
+
+def check_f32(A32, R, Q, unique=True):
+    """A32: the float32 input as float64.  Measures against it; R and Q against the oracle's QR
+    of it within the perturbation bound 50 kappa n u with u = 2^-24."""
+    assert np.all(np.tril(R, -1) == 0.0)
+    assert np.all(np.diag(R) >= 0.0)
+    assert oracle.backward_error(A32, Q, R) <= TOL_F32
+    assert oracle.orthogonality(Q) <= TOL_F32
+    if unique:
+        ref = oracle.qr(A32)
+        kappa = np.linalg.cond(ref["R"])
+        bound = 50 * kappa * A32.shape[1] * U32
+        assert np.linalg.norm(R - ref["R"]) / np.linalg.norm(ref["R"]) <= bound
+        assert np.abs(Q - ref["Q"]).max() <= bound
+
+
+@pytest.mark.parametrize("m,n,opts", [(4096, 16, {"leaf_h": 256, "chain": 1, "arity": 2}),
+                                      (3000, 24, {"leaf_h": 128, "chain": 3, "arity": 3}),
+                                      (40000 + 13, 64, {}), (30000, 50, {}), (100000 + 3, 16, {}),
+                                      (60000 + 7, 32, {}), (777, 1, {"leaf_h": 16}), (65, 64, {"leaf_h": 64}),
+                                      (20000, 128, {}), (5000 + 33, 65, {"leaf_h": 128})])
+def test_f32_shapes(T, m, n, opts):
+    """FP32 storage and arithmetic on the tree shapes, default plans, ragged tails and panels."""
+    A64 = inputs.gaussian(m, n, inputs.seed_for(11, m + n))
+    A32 = A64.astype(np.float32).astype(np.float64)
+    f, R, Q = run32(T, A64, **opts)
+    assert f.info().dtype == T.TSQR_F32
+    check_f32(A32, R, Q)
+
+
+@pytest.mark.parametrize("lda_extra,offset", [(1, 0), (0, 1), (5, 3)])
+def test_f32_strided(T, lda_extra, offset):
+    A64 = inputs.gaussian(3001, 21, 912 + lda_extra)
+    A32 = A64.astype(np.float32).astype(np.float64)
+    _, R, Q = run32(T, A64, lda=21 + lda_extra, offset=offset)
+    check_f32(A32, R, Q)
+
+
+@pytest.mark.parametrize("k", [0, 4, 8])
+def test_f32_conditioning(T, k):
+    """kappa = 1, 1e4, 1e8 (the precision-form inputs); at 1e8 > 1/u the float32 matrix is
+    numerically rank deficient, so only backward error and orthogonality are checked."""
+    A64 = inputs.usv(1 << 15, 64, k, 57 + k)
+    A32 = A64.astype(np.float32).astype(np.float64)
+    _, R, Q = run32(T, A64)
+    check_f32(A32, R, Q, unique=(k <= 4))
+
+
+@pytest.mark.parametrize("n", [24, 100])
+def test_f32_apply(T, n):
+    import torch
+
+    m, k = 7001, 6
+    A64 = inputs.gaussian(m, n, 93 + n)
+    A32 = A64.astype(np.float32).astype(np.float64)
+    B32 = inputs.gaussian(m, k, 94).astype(np.float32)
+    f, R, Q = run32(T, A64)
+    B = torch.from_numpy(B32.copy()).cuda()
+    f.apply_qt(B)
+    QtB = B.cpu().numpy().astype(np.float64)
+    scale = np.linalg.norm(B32.astype(np.float64), axis=0).max()
+    assert np.abs(QtB[:n] - oracle.thin_qt(A32, B32.astype(np.float64))).max() <= 1e-4 * scale
+    f.apply_q(B)
+    assert np.abs(B.cpu().numpy() - B32).max() <= 1e-5 * scale
+    E = torch.zeros((m, n), dtype=torch.float32, device="cuda")
+    E[:n] = torch.eye(n, dtype=torch.float32, device="cuda")
+    f.apply_q(E)
+    assert np.abs(E.cpu().numpy() - Q).max() <= 100 * n * U32
