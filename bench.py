@@ -171,37 +171,47 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
         g = torch.Generator(device=dev).manual_seed(seed + i)
         mats.append(torch.randn((int(ms[i]), int(ns[i])), dtype=torch.float64, device=dev, generator=g))
     fl = float(sum(4.0 * m_ * n_ * n_ - 4.0 * n_ ** 3 / 3 for m_, n_ in zip(ms, ns)))
-    b = tsqr.Batch(mats)
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(torch.cuda.current_stream(dev))
-    with torch.cuda.stream(side):
-        for _ in range(2):
-            b.factor()
-            b.form_q()
-    torch.cuda.current_stream(dev).wait_stream(side)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        b.factor()
-        b.form_q()
-    for _ in range(2):
-        graph.replay()
-    torch.cuda.synchronize()
     steps = max(1, min(args.steps, 5))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        graph.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_batched = e0.elapsed_time(e1) / steps
-    ok = b.status() == tsqr.TSQR_OK
-    # accuracy of the largest matrix of the batch
     big = int(np.argmax(ms))
-    A, Q, R = mats[big], b.Q[big], b.R[big]
-    be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
-    orth = torch.linalg.norm(torch.eye(int(ns[big]), dtype=torch.float64, device=dev) - Q.T @ Q).item()
-    b.close()
+
+    def graph_run(batch_mats):
+        """Times the batch's factor + thin Q replayed from a CUDA graph; accuracy of the largest."""
+        b = tsqr.Batch(batch_mats)
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                b.factor()
+                b.form_q()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            b.factor()
+            b.form_q()
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / steps
+        good = b.status() == tsqr.TSQR_OK
+        A, Q, R = batch_mats[big].double(), b.Q[big].double(), b.R[big].double()
+        acc = ((torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item(),
+               torch.linalg.norm(torch.eye(int(ns[big]), dtype=torch.float64, device=dev) - Q.T @ Q).item())
+        b.close()
+        del b, graph
+        torch.cuda.empty_cache()
+        return t, good, acc
+
+    ms_batched, ok, (be, orth) = graph_run(mats)
+    mats32 = [A.float() for A in mats]
+    ms32, ok32, (be32, orth32) = graph_run(mats32)
+    del mats32
     # the same work as a loop of single-matrix launches (workspaces and outputs preallocated)
     items = []
     for A in mats:
@@ -235,7 +245,11 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
             "launch": "one factor launch + one thin-Q launch per tree depth + one chain launch, CUDA graph",
             "loop_value": fl / (ms_loop / 1e3) / 1e9, "loop_ms_per_step": ms_loop,
             "speedup_vs_loop": ms_loop / ms_batched, "status_ok": ok,
-            "largest": {"m": int(ms[big]), "n": int(ns[big]), "backward_error": be, "orthogonality": orth}}
+            "largest": {"m": int(ms[big]), "n": int(ns[big]), "backward_error": be, "orthogonality": orth},
+            "fp32": {"value": fl / (ms32 / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms32,
+                     "speedup_vs_fp64_batched": ms_batched / ms32, "status_ok": ok32,
+                     "note": "the same matrices rounded to float32, FP32 storage and arithmetic, CUDA graph",
+                     "largest": {"backward_error": be32, "orthogonality": orth32}}}
 
 
 def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, warmup=2):
@@ -284,27 +298,29 @@ def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, war
 
 def run_autograd(tsqr, torch, dev, args, batch=64, m=65536, n=32, seed=20085000):
     """Forward + backward of sum(W1*Q) + sum(W2*R) for a batch of 64 matrices of 65536 x 32
-    (FP64): time and peak extra memory when the backward keeps the implicit Q tree, when it
-    recomputes it from A, and for torch.linalg.qr (cuSOLVER and its autograd, which keeps an
-    explicit Q) as a library reference."""
+    (FP64, and the same data rounded to FP32): time and peak extra memory when the backward keeps
+    the implicit Q tree, when it recomputes it from A, and for torch.linalg.qr (cuSOLVER and its
+    autograd, which keeps an explicit Q) as a library reference."""
     g = torch.Generator(device=dev).manual_seed(seed)
     A0 = torch.randn((batch, m, n), dtype=torch.float64, device=dev, generator=g)
     W1 = torch.randn((batch, m, n), dtype=torch.float64, device=dev, generator=g)
     W2 = torch.randn((batch, n, n), dtype=torch.float64, device=dev, generator=g)
-    out = {"workload": "batch of %d x %d x %d fp64, loss sum(W1*Q)+sum(W2*R)" % (batch, m, n)}
+    out = {"workload": "batch of %d x %d x %d, fp64 and fp32, loss sum(W1*Q)+sum(W2*R)" % (batch, m, n)}
+    grads = {}
+    A032, W132, W232 = A0.float(), W1.float(), W2.float()
 
     def step(kind):
-        A = A0.detach().clone().requires_grad_(True)
-        if kind == "torch":
+        f32 = kind.endswith("_fp32")
+        A = (A032 if f32 else A0).detach().clone().requires_grad_(True)
+        if kind.startswith("torch"):
             Q, R = torch.linalg.qr(A)
         else:
-            Q, R = tsqr.qr_autograd(A, keep=kind)
-        L = (W1 * Q).sum() + (W2 * R).sum()
+            Q, R = tsqr.qr_autograd(A, keep=kind.replace("_fp32", ""))
+        L = ((W132 if f32 else W1) * Q).sum() + ((W232 if f32 else W2) * R).sum()
         L.backward()
         return A.grad
 
-    grads = {}
-    for kind in ("tree", "recompute", "torch"):
+    for kind in ("tree", "recompute", "torch", "tree_fp32", "torch_fp32"):
         step(kind)
         torch.cuda.synchronize()
         base = torch.cuda.memory_allocated(dev)
@@ -322,6 +338,8 @@ def run_autograd(tsqr, torch, dev, args, batch=64, m=65536, n=32, seed=20085000)
     # after normalising diag(R) >= 0 is not guaranteed there), compare gradient norms only
     out["tree_equals_recompute"] = bool(torch.equal(grads["tree"], grads["recompute"]))
     out["grad_norm_tsqr"] = torch.linalg.norm(grads["tree"]).item()
+    out["fp32_grad_rel_diff_vs_fp64"] = (torch.linalg.norm(grads["tree_fp32"].double() - grads["tree"]) /
+                                         torch.linalg.norm(grads["tree"])).item()
     return out
 
 

@@ -57,7 +57,7 @@ typedef enum {
  * TSQR_F32: A, R, Q and B are binary32 and every operation is binary32 (the FP32-level form of
  * the precision forms: backward error and loss of orthogonality of order n * 2^-24).  A is
  * widened into the workspace first (it is never overwritten: inplace is not supported), and
- * precision must be 0.  tsqr_backward and the batch calls take TSQR_F64 only. */
+ * precision must be 0.  Every call takes both; tsqr_backward then works in the same type. */
 typedef enum { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype_t;
 typedef enum { TSQR_ROW_MAJOR = 0, TSQR_COL_MAJOR = 1 } tsqr_layout_t;
 
@@ -150,7 +150,8 @@ tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info);
  * with Q^T Qbar and Q copyltu(M) applied from the implicit Q (tsqr_apply_qt, tsqr_apply_q):
  * no explicit Q is needed.  R (n x n, ldr >= n) is the R that tsqr_factor returned.  A must have
  * full column rank (the derivative does not exist otherwise; a zero R_jj gives Inf/NaN).  The
- * final solve keeps R in shared memory, so n > 154 returns TSQR_ERR_UNSUPPORTED. */
+ * final solve keeps R in shared memory, so n > 154 (FP64) or n > 224 (FP32) returns
+ * TSQR_ERR_UNSUPPORTED.  Every matrix has the factorization's dtype. */
 tsqr_status_t tsqr_backward(tsqr_handle_t h, const void* dQbar, int64_t ldqb, const void* dRbar, int64_t ldrb,
                             const void* dR, int64_t ldr, void* dAbar, int64_t ldab, tsqr_stream_t stream);
 

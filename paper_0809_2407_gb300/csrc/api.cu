@@ -28,6 +28,7 @@ struct tsqr_batch_s {
   size_t counters_bytes = 0;
   int* d_status = nullptr;
   bool has_q = false;
+  bool widen = false;  // FP32 storage: A is widened into V before the factorization
   struct Stage {
     const double* A;
     int64_t lda;
@@ -592,13 +593,15 @@ struct BatchPlan {
 };
 
 tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n, const tsqr_opts_t* opts,
-                              BatchPlan* bp) {
+                              BatchPlan* bp, bool f32 = false) {
   if (count < 1) return fail(TSQR_ERR_INVALID_ARG, "count must be >= 1");
   if (!m || !n) return fail(TSQR_ERR_INVALID_ARG, "m and n arrays must be non-NULL");
   tsqr_opts_t base{};
   if (opts) base = *opts;
   if (base.inplace) return fail(TSQR_ERR_UNSUPPORTED, "batches keep A read-only (inplace is not supported)");
   if (base.precision == 2) base.precision = 0;  // batched thin Q uses the FP64 kernels
+  if (f32 && base.precision != 0)
+    return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 runs FP32 arithmetic: precision must be 0");
   // shared chain length: about 16 waves of two blocks per SM over the whole batch; double-float
   // keeps chains of at most 18 leaves (its orthogonality grows with chain length)
   tsqr_opts_t probe = base;
@@ -606,7 +609,7 @@ tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n,
   int64_t total_leaves = 0;
   for (int i = 0; i < count; ++i) {
     Plan P;
-    tsqr_status_t s = make_plan(m[i], n[i], &probe, &P);
+    tsqr_status_t s = make_plan(m[i], n[i], &probe, &P, f32);
     if (s != TSQR_OK) return fail(s, "batch item " + std::to_string(i) + ": " + g_last_error);
     total_leaves += P.leaves;
   }
@@ -621,7 +624,7 @@ tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n,
   bp->layouts.resize(count);
   bp->item_off.resize(count);
   for (int i = 0; i < count; ++i) {
-    tsqr_status_t s = make_plan(m[i], n[i], &base, &bp->plans[i]);
+    tsqr_status_t s = make_plan(m[i], n[i], &base, &bp->plans[i], f32);
     if (s != TSQR_OK) return fail(s, "batch item " + std::to_string(i) + ": " + g_last_error);
     bp->layouts[i] = make_layout(bp->plans[i], false);
     bp->total_chains += bp->plans[i].chains;
@@ -652,9 +655,9 @@ extern "C" {
 tsqr_status_t tsqr_batch_workspace_size(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
                                         const tsqr_opts_t* opts, size_t* bytes) {
   if (!bytes) return fail(TSQR_ERR_INVALID_ARG, "bytes is NULL");
-  if (dtype != TSQR_F64) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_F64 is implemented");
+  if (dtype != TSQR_F64 && dtype != TSQR_F32) return fail(TSQR_ERR_INVALID_ARG, "unknown dtype");
   BatchPlan bp;
-  tsqr_status_t s = make_batch_plan(count, m, n, opts, &bp);
+  tsqr_status_t s = make_batch_plan(count, m, n, opts, &bp, dtype == TSQR_F32);
   if (s != TSQR_OK) return s;
   *bytes = bp.total;
   return TSQR_OK;
@@ -666,11 +669,12 @@ tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t
                                 const tsqr_opts_t* opts, tsqr_stream_t stream, tsqr_batch_t* out) {
   if (!out) return fail(TSQR_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (dtype != TSQR_F64) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_F64 is implemented");
+  if (dtype != TSQR_F64 && dtype != TSQR_F32) return fail(TSQR_ERR_INVALID_ARG, "unknown dtype");
+  const bool f32 = dtype == TSQR_F32;
   if (!dA || !lda || !dR || !ldr) return fail(TSQR_ERR_INVALID_ARG, "A, lda, R and ldr arrays must be non-NULL");
   if (dQ && !ldq) return fail(TSQR_ERR_INVALID_ARG, "ldq array must be given with Q");
   BatchPlan bp;
-  tsqr_status_t s = make_batch_plan(count, m, n, opts, &bp);
+  tsqr_status_t s = make_batch_plan(count, m, n, opts, &bp, f32);
   if (s != TSQR_OK) return s;
   if (!dWork || work_bytes < bp.total)
     return fail(TSQR_ERR_WORKSPACE, "batch workspace needs " + std::to_string(bp.total) + " bytes");
@@ -699,8 +703,9 @@ tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t
       delete b;
       return fail(TSQR_ERR_INVALID_ARG, "batch item " + std::to_string(i) + ": NULL matrix pointer");
     }
-    if (lda[i] < n[i] || ldr[i] < n[i] || (dQ && ldq[i] < n[i]) ||
-        (reinterpret_cast<uintptr_t>(dA[i]) & 7) != 0) {
+    const uintptr_t amask = f32 ? 3 : 7;
+    if (lda[i] < n[i] || ldr[i] < n[i] || (dQ && ldq[i] < n[i]) || (reinterpret_cast<uintptr_t>(dA[i]) & amask) != 0 ||
+        (reinterpret_cast<uintptr_t>(dR[i]) & amask) != 0 || (dQ && (reinterpret_cast<uintptr_t>(dQ[i]) & amask) != 0)) {
       delete b;
       return fail(TSQR_ERR_INVALID_ARG, "batch item " + std::to_string(i) + ": bad leading dimension or alignment");
     }
@@ -721,20 +726,25 @@ tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t
     st.counters = b->d_counters + counter_ints;
     counter_ints += (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1);
     st.status = b->d_status;
-    it.R = static_cast<double*>(dR[i]);
+    it.R = dR[i];
     it.ldr = ldr[i];
-    it.Q = dQ ? static_cast<double*>(dQ[i]) : nullptr;
+    it.Q = dQ ? dQ[i] : nullptr;
     it.ldq = dQ ? ldq[i] : 0;
     it.box_rows = P.h < 256 ? P.h : 256;
-    const bool stage = (lda[i] % 2 != 0) || !aligned16(dA[i]);
+    if (f32) {  // widened into V by one batched launch before each factorization
+      it.A32 = static_cast<const float*>(dA[i]);
+      it.lda32 = lda[i];
+      b->widen = true;
+    }
+    const bool stage = !f32 && ((lda[i] % 2 != 0) || !aligned16(dA[i]));
     if ((s = make_map(&it.mapV, st.v, m[i], n[i], st.ldv, it.box_rows)) != TSQR_OK) {
       delete b;
       return s;
     }
+    if (stage || f32) it.mapA = it.mapV;
     if (stage) {
-      it.mapA = it.mapV;
       b->stages.push_back({static_cast<const double*>(dA[i]), lda[i], st.v, st.ldv, m[i], (int)n[i]});
-    } else if ((s = make_map(&it.mapA, dA[i], m[i], n[i], lda[i], it.box_rows)) != TSQR_OK) {
+    } else if (!f32 && (s = make_map(&it.mapA, dA[i], m[i], n[i], lda[i], it.box_rows)) != TSQR_OK) {
       delete b;
       return s;
     }
@@ -788,6 +798,7 @@ tsqr_status_t tsqr_batch_factor(tsqr_batch_t b, tsqr_stream_t stream) {
     const auto& sg = b->stages[k];
     e = tsqr::launch_stage_copy(sg.A, sg.lda, sg.V, sg.ldv, sg.m, sg.n, cs);
   }
+  if (e == cudaSuccess && b->widen) e = tsqr::launch_stage_widen_batched(b->d_items, b->count, cs);
   if (e == cudaSuccess)
     e = tsqr::launch_factor_batched(b->d_items, b->d_chain_work, b->total_chains, b->precision, b->smem_factor, cs);
   if (e != cudaSuccess) return cuda_fail(e, "batched factor launch");

@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ char smem_raw[];
   const BatchWork w = work[blockIdx.x];
   const BatchItem& it = items[w.item];
-  formq_chain<Ar>(&it.mapV, it.plan, it.store, it.Q, it.ldq, it.box_rows, w.chain, smem_raw);
+  formq_chain<Ar>(&it.mapV, it.plan, it.store, static_cast<typename Ar::Out*>(it.Q), it.ldq, it.box_rows, w.chain,
+                  smem_raw);
 }
 
 template <class Ar>
@@ -257,7 +258,9 @@ static cudaError_t prepare_form_q_batched_t(size_t smem) {
 }
 
 cudaError_t prepare_form_q_batched(int precision, size_t smem) {
-  return precision == 1 ? prepare_form_q_batched_t<ArithDF>(smem) : prepare_form_q_batched_t<ArithF64>(smem);
+  if (precision == 1) return prepare_form_q_batched_t<ArithDF>(smem);
+  if (precision == 3) return prepare_form_q_batched_t<ArithF32>(smem);
+  return prepare_form_q_batched_t<ArithF64>(smem);
 }
 
 template <class Ar>
@@ -281,6 +284,9 @@ cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain
   if (precision == 1)
     return launch_form_q_batched_t<ArithDF>(items, chain_work, chain_blocks, level_work, level_blocks, depth, smem,
                                             stream);
+  if (precision == 3)
+    return launch_form_q_batched_t<ArithF32>(items, chain_work, chain_blocks, level_work, level_blocks, depth, smem,
+                                             stream);
   return launch_form_q_batched_t<ArithF64>(items, chain_work, chain_blocks, level_work, level_blocks, depth, smem,
                                            stream);
 }

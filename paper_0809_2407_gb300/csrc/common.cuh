@@ -63,10 +63,12 @@ struct __align__(64) BatchItem {
   CUtensorMap mapV;  // reflector storage
   Plan plan;
   Store store;
-  double* R;         // n x n, leading dimension ldr
+  void* R;           // n x n, leading dimension ldr (double, or float with FP32 storage)
   int64_t ldr;
-  double* Q;         // thin Q output of the batched form-Q, leading dimension ldq
+  void* Q;           // thin Q output of the batched form-Q, leading dimension ldq
   int64_t ldq;
+  const float* A32;  // FP32 storage: A (leading dimension lda32), widened into V before the factor
+  int64_t lda32;
   int box_rows;
 };
 // Block b of a batched launch works on chain `chain` (or tree node `chain` of a level) of item.

@@ -212,12 +212,15 @@ __global__ void __launch_bounds__(kThreads, 2)
   extern __shared__ char smem_raw[];
   const BatchWork w = work[blockIdx.x];
   const BatchItem& it = items[w.item];
-  factor_chain<Ar>(&it.mapA, &it.mapV, it.plan, it.store, it.R, it.ldr, it.box_rows, w.chain, smem_raw);
+  factor_chain<Ar>(&it.mapA, &it.mapV, it.plan, it.store, static_cast<typename Ar::Out*>(it.R), it.ldr, it.box_rows,
+                   w.chain, smem_raw);
 }
 
 cudaError_t prepare_factor_batched(int precision, size_t smem) {
   if (precision == 1)
     return cudaFuncSetAttribute(factor_batched_kernel<ArithDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (precision == 3)
+    return cudaFuncSetAttribute(factor_batched_kernel<ArithF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaFuncSetAttribute(factor_batched_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -225,8 +228,31 @@ cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work,
                                   size_t smem, cudaStream_t stream) {
   if (precision == 1)
     factor_batched_kernel<ArithDF><<<blocks, kThreads, smem, stream>>>(items, work);
+  else if (precision == 3)
+    factor_batched_kernel<ArithF32><<<blocks, kThreads, smem, stream>>>(items, work);
   else
     factor_batched_kernel<ArithF64><<<blocks, kThreads, smem, stream>>>(items, work);
+  return cudaGetLastError();
+}
+
+// FP32 storage in a batch: blocks (x, i) widen item i's A into its reflector storage.
+__global__ void stage_widen_batched_kernel(const BatchItem* __restrict__ items) {
+  const BatchItem& it = items[blockIdx.y];
+  const float* A = it.A32;
+  if (A == nullptr) return;
+  const int64_t m = it.plan.m, lda = it.lda32, ldv = it.store.ldv;
+  const int n = it.plan.n;
+  double* V = it.store.v;
+  const int64_t total = m * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / n;
+    const int c = (int)(i - r * n);
+    V[r * ldv + c] = (double)A[r * lda + c];
+  }
+}
+
+cudaError_t launch_stage_widen_batched(const BatchItem* items, int count, cudaStream_t stream) {
+  stage_widen_batched_kernel<<<dim3(16, (unsigned)count), 256, 0, stream>>>(items);
   return cudaGetLastError();
 }
 

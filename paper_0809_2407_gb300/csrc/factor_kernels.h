@@ -19,6 +19,7 @@ cudaError_t launch_stage_widen(const float* A, int64_t lda, double* V, int64_t l
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                           void* R_out, int64_t ldr, int box_rows, cudaStream_t stream);
 cudaError_t prepare_factor_batched(int precision, size_t smem);
+cudaError_t launch_stage_widen_batched(const BatchItem* items, int count, cudaStream_t stream);
 cudaError_t prepare_form_q_batched(int precision, size_t smem);
 cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work, int blocks, int precision,
                                   size_t smem, cudaStream_t stream);

@@ -279,7 +279,7 @@ class Factorization:
 
 
 def qr(A, **opts):
-    """Thin QR of a CUDA float64 matrix by TSQR: returns (Q, R), diag(R) >= 0."""
+    """Thin QR of a CUDA float64 or float32 matrix by TSQR: returns (Q, R), diag(R) >= 0."""
     f = Factorization(A, **opts)
     Q = f.form_q()
     R = f.R
@@ -288,29 +288,32 @@ def qr(A, **opts):
 
 
 class Batch:
-    """Many CUDA float64 tall-skinny matrices factored together (one launch for all R factors,
-    one launch per tree depth plus one for all thin Q factors).  The launches only enqueue work on
-    the current stream, so ``factor()`` and ``form_q()`` can be captured in a CUDA graph.
+    """Many CUDA float64 (or, all of them, float32) tall-skinny matrices factored together (one
+    launch for all R factors, one launch per tree depth plus one for all thin Q factors).  The
+    launches only enqueue work on the current stream, so ``factor()`` and ``form_q()`` can be
+    captured in a CUDA graph.
     """
 
     def __init__(self, mats, want_q=True, leaf_h=0, chain=0, arity=0, precision=0):
         import torch
 
+        dt = mats[0].dtype
         for i, A in enumerate(mats):
-            _check_matrix(A, "A[%d]" % i, torch.float64)
+            _check_matrix(A, "A[%d]" % i, dt)
         self.mats = list(mats)
         dev = self.mats[0].device
+        self.code = TSQR_F32 if dt == torch.float32 else TSQR_F64
         self.m = [A.shape[0] for A in self.mats]
         self.n = [A.shape[1] for A in self.mats]
         count = len(self.mats)
         self.opts = Opts(leaf_h=leaf_h, chain=chain, arity=arity, precision=precision, inplace=0)
-        nbytes = tsqr_batch_workspace_size(TSQR_F64, count, self.m, self.n, self.opts)
+        nbytes = tsqr_batch_workspace_size(self.code, count, self.m, self.n, self.opts)
         self.work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
-        self.R = [torch.empty((k, k), dtype=torch.float64, device=dev) for k in self.n]
-        self.Q = [torch.empty((mm, k), dtype=torch.float64, device=dev) for mm, k in zip(self.m, self.n)] \
+        self.R = [torch.empty((k, k), dtype=dt, device=dev) for k in self.n]
+        self.Q = [torch.empty((mm, k), dtype=dt, device=dev) for mm, k in zip(self.m, self.n)] \
             if want_q else None
         self.handle = tsqr_batch_create(
-            TSQR_F64, count, self.m, self.n, [A.data_ptr() for A in self.mats], [A.stride(0) for A in self.mats],
+            self.code, count, self.m, self.n, [A.data_ptr() for A in self.mats], [A.stride(0) for A in self.mats],
             [R.data_ptr() for R in self.R], [R.stride(0) for R in self.R],
             [Q.data_ptr() for Q in self.Q] if want_q else None, [Q.stride(0) for Q in self.Q] if want_q else None,
             self.work.data_ptr(), nbytes, self.opts, _stream())
@@ -439,7 +442,7 @@ def _qr_function():
             A, R = ctx.saved_tensors
             f = ctx.fact if ctx.fact is not None else Factorization(A, **ctx.opts)
             m, n = A.shape
-            Abar = torch.empty((m, n), dtype=torch.float64, device=A.device)
+            Abar = torch.empty((m, n), dtype=A.dtype, device=A.device)
             qb = Qbar.contiguous() if Qbar is not None else None
             rb = Rbar.contiguous() if Rbar is not None else None
             tsqr_backward(f.handle, qb.data_ptr() if qb is not None else None, n,
@@ -458,7 +461,7 @@ _QR = None
 
 
 def qr_autograd(A, keep="tree", **opts):
-    """Differentiable thin QR of a CUDA float64 matrix (or a batch: leading dimensions looped).
+    """Differentiable thin QR of a CUDA float64 or float32 matrix (or a batch: leading dimensions looped).
     Returns (Q, R) with diag(R) >= 0; gradients flow through tsqr_backward."""
     global _QR
     if _QR is None:

@@ -140,15 +140,16 @@ def test_panel_workspace(lib):
 
 def test_f32_workspace(lib):
     """FP32 storage: A is always widened into the workspace, so its size matches FP64's non-inplace
-    layout; batches and in-place factorizations stay FP64 only."""
+    layout; in-place factorizations and the other precision modes stay FP64 only."""
     for m, n in [(4096, 16), (100000, 64), (100000, 100)]:
         assert lib.tsqr_workspace_size(lib.TSQR_F32, m, n) > 0
     assert lib.tsqr_workspace_size(lib.TSQR_F32, 100000, 64) == lib.tsqr_workspace_size(lib.TSQR_F64, 100000, 64)
     with pytest.raises(lib.TsqrError) as ei:
         lib.tsqr_workspace_size(lib.TSQR_F32, 1000, 16, {"inplace": 1})
     assert ei.value.status == 2
+    assert lib.tsqr_batch_workspace_size(lib.TSQR_F32, 2, [1000, 5000], [16, 50]) > 0
     with pytest.raises(lib.TsqrError) as ei:
-        lib.tsqr_batch_workspace_size(lib.TSQR_F32, 1, [1000], [16])
+        lib.tsqr_batch_workspace_size(lib.TSQR_F32, 1, [1000], [16], {"precision": 1})
     assert ei.value.status == 2
 
 

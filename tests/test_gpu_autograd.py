@@ -116,3 +116,24 @@ def test_one_sided_losses_and_batch(T):
         W1 = np.zeros((3000, 12))
         W2 = np.eye(12)
         assert np.abs(A.grad[b].cpu().numpy() - reference_grad(A_h[b], W1, W2)).max() <= 1e-11
+
+
+@pytest.mark.parametrize("m,n", [(4096, 16), (20000, 64), (6000, 100)])
+def test_f32_against_cpu_reference(T, m, n):
+    """FP32 storage: the float32 gradient against the FP64 reference gradient of the float32 A,
+    within the FP32 perturbation bound 50 kappa n u, u = 2^-24 (kappa(A) = 10)."""
+    import torch
+
+    A32 = inputs.usv(m, n, 1.0, 800 + m).astype(np.float32)
+    rng = np.random.default_rng(m + n + 1)
+    W1 = rng.standard_normal((m, n)).astype(np.float32)
+    W2 = rng.standard_normal((n, n)).astype(np.float32)
+    A = torch.from_numpy(A32.copy()).cuda().requires_grad_(True)
+    Q, R = T.qr_autograd(A)
+    assert Q.dtype == torch.float32 and R.dtype == torch.float32
+    L = (torch.from_numpy(W1).cuda() * Q).sum() + (torch.from_numpy(W2).cuda() * R).sum()
+    L.backward()
+    assert A.grad.dtype == torch.float32
+    g = A.grad.double().cpu().numpy()
+    ref = reference_grad(A32.astype(np.float64), W1.astype(np.float64), W2.astype(np.float64))
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) <= 50 * 10 * n * 2.0 ** -24

@@ -477,3 +477,38 @@ def test_f32_apply(T, n):
     E[:n] = torch.eye(n, dtype=torch.float32, device="cuda")
     f.apply_q(E)
     assert np.abs(E.cpu().numpy() - Q).max() <= 100 * n * U32
+
+
+def test_f32_batched_uneven_and_graph(T):
+    """FP32 batch: uneven m and n in one persistent launch, widened on the device, replayed from a
+    CUDA graph with bitwise equal R."""
+    import torch
+
+    rng = np.random.default_rng(14)
+    ms = [int(x) for x in np.exp(rng.uniform(np.log(300), np.log(40000), 12)).astype(int)]
+    ns = [int(x) for x in rng.choice([8, 16, 32, 50, 64], 12)]
+    ms = [max(m_, n_) for m_, n_ in zip(ms, ns)]
+    hs = [inputs.gaussian(m_, n_, 7000 + i).astype(np.float32) for i, (m_, n_) in enumerate(zip(ms, ns))]
+    mats = [torch.from_numpy(a).cuda() for a in hs]
+    b = T.Batch(mats)
+    b.factor()
+    b.form_q()
+    torch.cuda.synchronize()
+    assert b.status() == T.TSQR_OK
+    R0 = [R.clone() for R in b.R]
+    for a, R, Q in zip(hs, b.R, b.Q):
+        assert R.dtype == torch.float32
+        check_f32(a.astype(np.float64), R.cpu().numpy().astype(np.float64), Q.cpu().numpy().astype(np.float64))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        b.factor()
+        b.form_q()
+    for R in b.R:
+        R.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for R, r0 in zip(b.R, R0):
+        assert torch.equal(R, r0)
+    b.close()
