@@ -361,6 +361,7 @@ def main():
     ap.add_argument("--no-shapes", action="store_true", help="skip the n = 16, 32, 128 shapes")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="arithmetic mode of the main line (0 native FP64; 1 and 2 are for profiling)")
+    ap.add_argument("--fp32", action="store_true", help="main line in FP32 storage (for profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -477,7 +478,7 @@ def main():
         return {"ms": ms, "ev": ev, "be": be, "orth": orth, "clocks": clocks, "opts": opts, "nbytes": nbytes,
                 "launches": launches}
 
-    main_mode = run_mode(args.precision, args.steps, args.warmup, True)
+    main_mode = run_mode(args.precision, args.steps, args.warmup, True, f32=args.fp32)
     ms = main_mode["ms"]
     ev = main_mode["ev"]
     clocks = main_mode["clocks"]
@@ -590,7 +591,7 @@ def main():
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": {0: "f64", 1: "f32x2", 2: "f64"}[args.precision], "data": "synthetic",
+               "vs_baseline": None, "dtype": "f32" if args.fp32 else {0: "f64", 1: "f32x2", 2: "f64"}[args.precision], "data": "synthetic",
                "config": {"workload": "tsqr factor + form_q + apply_qt(k=1), fp64, m=%d n=%d, A=U S V^T kappa=1"
                                       % (m, n), "m": m, "n": n, "k": 1, "leaf_h": None, "chain": "auto",
                           "arity": 2, "precision": args.precision, "l2": "inputs larger than L2 (A is %.1f GB)" % (8.0 * m * n / 1e9),

@@ -68,8 +68,9 @@ __device__ inline void chain_step(const FactorSmem<typename Ar::E>& f, const Pla
 template <class Ar>
 __device__ inline void convert_rows_in(const Tile& S, int r0, int rows, int np) {
   if constexpr (Ar::kPrecision != 0) {
+    const int lnp = __ffs(np) - 1;  // np is a power of two
     for (int i = threadIdx.x; i < rows * np; i += kThreads) {
-      double* p = S.ptr(r0 + i / np, i % np);
+      double* p = S.ptr(r0 + (i >> lnp), i & (np - 1));
       *reinterpret_cast<typename Ar::E*>(p) = Ar::from_f64(*p);
     }
     __syncthreads();
@@ -87,6 +88,7 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
   const Tile& S = f.S;
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, h = P.h;
+  const int lnp = __ffs(np) - 1;  // np is a power of two
   E* tau_leaf = reinterpret_cast<E*>(st.tau_leaf);
   E* t_leaf = reinterpret_cast<E*>(st.t_leaf);
   E* node_r = reinterpret_cast<E*>(st.node_r);
@@ -117,13 +119,13 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
     E* T_g = t_leaf + leaf * np * np;
     for (int i = tid; i < np; i += kThreads) tau_g[i] = f.tau_s[i];
     for (int i = tid; i < np * np; i += kThreads) {
-      const int a = i / np, b = i % np;
+      const int a = (i >> lnp), b = (i & (np - 1));
       T_g[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
     }
     tile_store_drain();
     if (plain) {  // rows 0..np-1 now carry R above the diagonal; clear the reflector part below
       for (int i = tid; i < np * np; i += kThreads) {
-        const int r = i / np, c = i % np;
+        const int r = (i >> lnp), c = (i & (np - 1));
         if (c < r) at<E>(S, r, c) = Ar::zero();
       }
       __syncthreads();
@@ -135,7 +137,7 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
   {
     E* Rg = node_r + (size_t)g * np * np;
     for (int i = tid; i < np * np; i += kThreads) {
-      const int r = i / np, c = i % np;
+      const int r = (i >> lnp), c = (i & (np - 1));
       Rg[i] = (c >= r) ? at<E>(S, r, c) : Ar::zero();
     }
   }
@@ -160,7 +162,7 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
     // stack the children's R factors in child order: child s at rows s*np..s*np+np-1
     for (int s = 0; s < q; ++s) {
       const double* Rc = st.node_r + (size_t)(P.level_offset[level] + first + s) * np * np;
-      for (int i = tid; i < np * np; i += kThreads) *S.ptr(s * np + i / np, i % np) = __ldcg(Rc + i);
+      for (int i = tid; i < np * np; i += kThreads) *S.ptr(s * np + (i >> lnp), (i & (np - 1))) = __ldcg(Rc + i);
     }
     __syncthreads();
     stacked_qr<Ar>(S, NODE, q * np, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
@@ -168,19 +170,19 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
     for (int s = 1; s < P.arity; ++s) {
       E* Ys = Y + (size_t)(s - 1) * np * np;
       for (int i = tid; i < np * np; i += kThreads) {
-        const int r = i / np, c = i % np;
+        const int r = (i >> lnp), c = (i & (np - 1));
         Ys[i] = (s < q && c >= r) ? at<E>(S, s * np + r, c) : Ar::zero();
       }
     }
     for (int i = tid; i < np; i += kThreads) reinterpret_cast<E*>(st.node_tau)[(size_t)tn * np + i] = f.tau_s[i];
     E* Tn = reinterpret_cast<E*>(st.node_t) + (size_t)tn * np * np;
     for (int i = tid; i < np * np; i += kThreads) {
-      const int a = i / np, b = i % np;
+      const int a = (i >> lnp), b = (i & (np - 1));
       Tn[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
     }
     E* Rp = node_r + (size_t)pid * np * np;
     for (int i = tid; i < np * np; i += kThreads) {
-      const int r = i / np, c = i % np;
+      const int r = (i >> lnp), c = (i & (np - 1));
       Rp[i] = (c >= r) ? at<E>(S, r, c) : Ar::zero();
     }
     idx = parent;
