@@ -252,6 +252,87 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
                      "largest": {"backward_error": be32, "orthogonality": orth32}}}
 
 
+def run_e2e(tsqr, torch, dev, stream, sptr, A_pin, b_h, A, Q, R, b, work, nbytes, opts, m, n, steps, world):
+    """The step through the C-ABI with host buffers: H2D of A and b from pinned memory, then
+    factor, thin Q and Q^T b, then D2H of R, Q and Q^T b, every step.  Timed two ways: serially on
+    one stream, and pipelined with two buffer sets, where the copies of neighbouring steps run on
+    two copy streams while the current step computes (what a caller streaming matrices does)."""
+    per_step = sum(flops(m, n).values())
+    R_h = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(2)]
+    Q_h = [torch.empty((m, n), dtype=torch.float64).pin_memory() for _ in range(2)]
+    bo_h = [torch.empty((m, 1), dtype=torch.float64).pin_memory() for _ in range(2)]
+    Ad, Qd, Rd, bd = [A, torch.empty_like(A)], [Q, torch.empty_like(Q)], [R, torch.empty_like(R)], [b, torch.empty_like(b)]
+
+    def step_on(j, s_ptr):
+        h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, Ad[j].data_ptr(), n, Rd[j].data_ptr(), n,
+                             work.data_ptr(), nbytes, opts, s_ptr)
+        tsqr.tsqr_form_q(h, Qd[j].data_ptr(), n, s_ptr)
+        tsqr.tsqr_apply_qt(h, 1, bd[j].data_ptr(), 1, s_ptr)
+        return h
+
+    def serial(K):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            Ad[0].copy_(A_pin, non_blocking=True)
+            bd[0].copy_(b_h, non_blocking=True)
+            h = step_on(0, sptr)
+            R_h[0].copy_(Rd[0], non_blocking=True)
+            Q_h[0].copy_(Qd[0], non_blocking=True)
+            bo_h[0].copy_(bd[0], non_blocking=True)
+            tsqr.tsqr_destroy(h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def pipelined(K):
+        torch.cuda.synchronize()
+        ev_in = [torch.cuda.Event() for _ in range(K)]
+        ev_c = [torch.cuda.Event() for _ in range(K)]
+        ev_out = [torch.cuda.Event() for _ in range(K)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s_in)
+        for i in range(K):
+            j = i % 2
+            if i >= 2:
+                s_in.wait_event(ev_out[i - 2])  # buffers j are free once step i-2's results left
+            with torch.cuda.stream(s_in):
+                Ad[j].copy_(A_pin, non_blocking=True)
+                bd[j].copy_(b_h, non_blocking=True)
+            ev_in[i].record(s_in)
+            stream.wait_event(ev_in[i])
+            h = step_on(j, sptr)
+            ev_c[i].record(stream)
+            s_out.wait_event(ev_c[i])
+            with torch.cuda.stream(s_out):
+                R_h[j].copy_(Rd[j], non_blocking=True)
+                Q_h[j].copy_(Qd[j], non_blocking=True)
+                bo_h[j].copy_(bd[j], non_blocking=True)
+            ev_out[i].record(s_out)
+            tsqr.tsqr_destroy(h)
+        e1.record(s_out)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    serial(1)
+    ser_ms = serial(max(1, min(steps, 3)))
+    pipelined(2)
+    K = max(3, min(steps, 6))
+    pipe_ms = pipelined(K)
+    ok = bool(torch.equal(Q_h[0], Q_h[1]) and torch.equal(R_h[0], R_h[1]))
+    return {"value": per_step * world / (pipe_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+            "h2d_bytes_per_step": 8 * m * n + 8 * m, "d2h_bytes_per_step": 8 * n * n + 8 * m * n + 8 * m,
+            "ms_per_step": pipe_ms, "steps": K,
+            "schedule": "pipelined: two device buffer sets; step i+1's H2D and step i-1's D2H run on two copy "
+                        "streams while step i computes; timed from the first H2D to the last D2H",
+            "results_identical_across_buffers": ok,
+            "serial": {"value": per_step * world / (ser_ms / 1e3) / 1e9, "ms_per_step": ser_ms,
+                       "schedule": "one stream: H2D, factor, thin Q, Q^T b, D2H"}}
+
+
 def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, warmup=2):
     """Plain FP64 TSQR (factor + thin Q + Q^T b) on the other column counts of the workload
     family, A = U Sigma V^T with kappa = 1: n = 16 and 32 are single TSQRs with taller leaves,
@@ -479,6 +560,11 @@ def main():
                 "launches": launches}
 
     main_mode = run_mode(args.precision, args.steps, args.warmup, True, f32=args.fp32)
+    # end to end right after the main line, before the other sections fill host and device memory
+    e2e = None
+    if not args.no_e2e and not args.fp32:
+        e2e = run_e2e(tsqr, torch, dev, stream, sptr, A_pin, b_h, A, Q, R, b, work_holder["t"],
+                      main_mode["nbytes"], main_mode["opts"], m, n, args.steps, world)
     ms = main_mode["ms"]
     ev = main_mode["ev"]
     clocks = main_mode["clocks"]
@@ -544,6 +630,26 @@ def main():
     if not args.no_batched and world == 1:
         batched = run_batched(tsqr, torch, dev, stream, sptr, args)
 
+    # context, not a target: the vendor library's QR of the same matrix (torch.linalg.qr, cuSOLVER)
+    library = None
+    if not args.no_forms and world == 1:
+        library = {"what": "torch.linalg.qr (cuSOLVER geqrf + orgqr) on the same A, explicit Q and R"}
+        for nm, X in (("fp64", A), ("fp32", A.float())):
+            torch.linalg.qr(X)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                Qc, Rc = torch.linalg.qr(X)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            c_ms = e0.elapsed_time(e1) / 2
+            fl2 = flops(m, n)
+            library[nm] = {"ms": c_ms, "value": (fl2["factor"] + fl2["form_q"]) / (c_ms / 1e3) / 1e9,
+                           "unit": "GFLOP/s (factor + thin Q)"}
+            del Qc, Rc, X
+        torch.cuda.empty_cache()
+
     shapes = None
     if not args.no_shapes and world == 1:
         shapes = run_shapes(tsqr, torch, dev, stream, sptr, m)
@@ -551,35 +657,6 @@ def main():
     autograd = None
     if not args.no_autograd and world == 1:
         autograd = run_autograd(tsqr, torch, dev, args)
-
-    # end to end through the C-ABI with host buffers: H2D of A and b, D2H of R, Q and Q^T b
-    e2e = None
-    if not args.no_e2e:
-        R_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        Q_h = torch.empty((m, n), dtype=torch.float64).pin_memory()
-        bo_h = torch.empty((m, 1), dtype=torch.float64).pin_memory()
-        e_steps = max(1, min(args.steps, 3))
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e_steps):
-            A.copy_(A_pin, non_blocking=True)
-            b.copy_(b_h, non_blocking=True)
-            h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
-                                 work.data_ptr(), nbytes, opts, sptr)
-            tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
-            tsqr.tsqr_apply_qt(h, 1, b.data_ptr(), 1, sptr)
-            R_h.copy_(R, non_blocking=True)
-            Q_h.copy_(Q, non_blocking=True)
-            bo_h.copy_(b, non_blocking=True)
-            tsqr.tsqr_destroy(h)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1) / e_steps
-        e2e = {"value": per_step * world / (e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
-               "h2d_bytes_per_step": 8 * m * n + 8 * m, "d2h_bytes_per_step": 8 * n * n + 8 * m * n + 8 * m,
-               "ms_per_step": e_ms, "steps": e_steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -599,7 +676,7 @@ def main():
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
                "roofline": roofline, "precision_forms": forms, "batched": batched, "shapes": shapes,
-               "autograd": autograd, "cpu_baseline": cpu, "e2e": e2e,
+               "autograd": autograd, "library_context": library, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": main_mode["launches"] * args.steps, "clocks": clocks}
         print(json.dumps(out), flush=True)
     if dist:
