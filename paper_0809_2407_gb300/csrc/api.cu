@@ -157,7 +157,8 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P, boo
   P->rows_cap = (rows_cap + 7) / 8 * 8;
   if (tsqr::factor_smem_bytes(*P) > kSmemLimit || tsqr::formq_smem_bytes(*P) > kSmemLimit ||
       tsqr::apply_smem_bytes(*P, 32) > kSmemLimit ||
-      (tsqr::ozaki_form_q_applies(*P) && tsqr::formq_ozaki_smem_bytes(*P) > kSmemLimit))
+      (tsqr::ozaki_form_q_applies(*P) && tsqr::formq_ozaki_smem_bytes(*P) > kSmemLimit) ||
+      (tsqr::bf16x3_form_q_applies(*P) && tsqr::formq_bf16x3_smem_bytes(*P) > kSmemLimit))
     return fail(TSQR_ERR_UNSUPPORTED, "leaf_h/arity too large for shared memory at this n");
   return TSQR_OK;
 }

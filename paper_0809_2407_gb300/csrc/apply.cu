@@ -1012,9 +1012,25 @@ static cudaError_t launch_form_q_ozaki(const CUtensorMap& mapV, const Plan& P, c
 
 bool ozaki_form_q_applies(const Plan& P) { return P.precision == 2 && P.np == 64 && P.h <= 128; }
 
+// FP32 storage: the tree levels on the FP32 pipe, the chains with bf16x3 tensor-core products.
+static cudaError_t launch_form_q_bf16x3(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q, int64_t ldq,
+                                        int box_rows, cudaStream_t stream) {
+  const size_t smem_tree = formq_smem_bytes(P);
+  cudaError_t e =
+      cudaFuncSetAttribute(formq_tree_kernel<ArithF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tree);
+  if (e != cudaSuccess) return e;
+  for (int level = P.depth; level >= 1; --level) {
+    formq_tree_kernel<ArithF32><<<P.level_count[level], kThreads, smem_tree, stream>>>(P, st, level);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return launch_formq_bf16x3_chains(mapV, P, st, static_cast<float*>(Q), ldq, box_rows, stream);
+}
+
 cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q, int64_t ldq,
                           int box_rows, cudaStream_t stream) {
   if (P.precision == 1) return launch_form_q_t<ArithDF>(mapV, P, st, Q, ldq, box_rows, stream);
+  if (bf16x3_form_q_applies(P)) return launch_form_q_bf16x3(mapV, P, st, Q, ldq, box_rows, stream);
   if (P.precision == 3) return launch_form_q_t<ArithF32>(mapV, P, st, Q, ldq, box_rows, stream);
   if (ozaki_form_q_applies(P)) return launch_form_q_ozaki(mapV, P, st, Q, ldq, box_rows, stream);
   return launch_form_q_t<ArithF64>(mapV, P, st, Q, ldq, box_rows, stream);

@@ -10,6 +10,11 @@ size_t formq_smem_bytes(const Plan& P);
 size_t apply_smem_bytes(const Plan& P, int kb);
 size_t formq_ozaki_smem_bytes(const Plan& P);
 bool ozaki_form_q_applies(const Plan& P);
+size_t formq_bf16x3_smem_bytes(const Plan& P);
+bool bf16x3_form_q_applies(const Plan& P);
+// chains of an FP32-storage thin Q with bf16x3 tensor-core WY products (after the tree levels)
+cudaError_t launch_formq_bf16x3_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, float* Q, int64_t ldq,
+                                       int box_rows, cudaStream_t stream);
 
 cudaError_t launch_stage_copy(const double* A, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
                               cudaStream_t stream);

@@ -512,3 +512,25 @@ def test_f32_batched_uneven_and_graph(T):
     for R, r0 in zip(b.R, R0):
         assert torch.equal(R, r0)
     b.close()
+
+
+def test_f32_full_size_properties(T):
+    """m = 2^22, n = 64 in FP32 storage (the benchmark's launch configuration: 144-leaf chains and
+    the bf16x3 tensor-core thin Q).  Long chains are where an inexact C recurrence would show;
+    backward error and orthogonality are checked with FP64 GEMMs on the device, R against the
+    Cholesky factor of the float32 A's Gram matrix within the FP32 perturbation bound."""
+    import torch
+
+    m, n = 1 << 22, 64
+    A32 = inputs.usv(m, n, 0.0, inputs.seed_for(2, 0)).astype(np.float32)
+    A = torch.from_numpy(A32).cuda()
+    f = T.Factorization(A)
+    Q = f.form_q()
+    torch.cuda.synchronize()
+    assert f.status() == T.TSQR_OK
+    Ad, Qd, Rd = A.double(), Q.double(), f.R.double()
+    be = (torch.linalg.norm(Ad - Qd @ Rd) / torch.linalg.norm(Ad)).item()
+    orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device="cuda") - Qd.T @ Qd).item()
+    assert be <= TOL_F32 and orth <= TOL_F32
+    Rc = np.linalg.cholesky(A32.astype(np.float64).T @ A32.astype(np.float64)).T
+    assert np.abs(Rd.cpu().numpy() - Rc).max() <= 50 * n * U32 * np.abs(Rc).max()
