@@ -534,3 +534,34 @@ def test_f32_full_size_properties(T):
     assert be <= TOL_F32 and orth <= TOL_F32
     Rc = np.linalg.cholesky(A32.astype(np.float64).T @ A32.astype(np.float64)).T
     assert np.abs(Rd.cpu().numpy() - Rc).max() <= 50 * n * U32 * np.abs(Rc).max()
+
+
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_precision_forms_conditioning(T, n):
+    """The precision forms on the conditioning sweep of their workload (A = U S V^T, kappa = 1,
+    1e4, 1e8, m = 2^20): every FP64-level form within 1e-12 on backward error and orthogonality,
+    the FP32 form within 5e-5, whatever kappa (Householder QR is backward stable)."""
+    import torch
+
+    m = 1 << 20
+    for k in (0, 4, 8):
+        A_h = inputs.usv(m, n, k, inputs.seed_for(12, 10 * n + k))
+        A = torch.from_numpy(A_h).cuda()
+        for prec in (0, 1, 2):
+            f = T.Factorization(A, precision=prec)
+            Q = f.form_q()
+            torch.cuda.synchronize()
+            assert f.status() == T.TSQR_OK
+            be = (torch.linalg.norm(A - Q @ f.R) / torch.linalg.norm(A)).item()
+            orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device="cuda") - Q.T @ Q).item()
+            assert be <= TOL_BACK and orth <= TOL_ORTH, (k, prec, be, orth)
+            f.close()
+        A32 = A.float()
+        f = T.Factorization(A32)
+        Q = f.form_q().double()
+        torch.cuda.synchronize()
+        Ad = A32.double()
+        be = (torch.linalg.norm(Ad - Q @ f.R.double()) / torch.linalg.norm(Ad)).item()
+        orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device="cuda") - Q.T @ Q).item()
+        assert be <= TOL_F32 and orth <= TOL_F32, (k, "f32", be, orth)
+        f.close()
