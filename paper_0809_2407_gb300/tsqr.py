@@ -454,21 +454,91 @@ def _qr_function():
             ctx.fact = None
             return Abar, None, None
 
-    return QR
+    class QRBatch(torch.autograd.Function):
+        """A batch of independent QRs (A: B x m x n).  Each matrix alone leaves most SMs idle
+        during its reduction tree, so the matrices are spread round-robin over a few CUDA streams
+        and their launches overlap; the calling stream waits for all of them.  keep as in QR."""
+
+        @staticmethod
+        def forward(ctx, A, keep, opts):
+            nb, m, n = A.shape
+            cur = torch.cuda.current_stream(A.device)
+            streams = _side_streams(A.device)
+            Q = torch.empty_like(A)
+            R = torch.empty((nb, n, n), dtype=A.dtype, device=A.device)
+            ready = torch.cuda.Event()
+            ready.record(cur)
+            facts = []
+            for i in range(nb):
+                s = streams[i % len(streams)]
+                s.wait_event(ready)
+                with torch.cuda.stream(s):
+                    f = Factorization(A[i], **opts)
+                    f.form_q(out=Q[i])
+                    R[i].copy_(f.R)
+                    if keep == "tree":
+                        facts.append(f)
+                    else:
+                        f.close()
+            for s in streams:
+                cur.wait_stream(s)
+            ctx.keep, ctx.opts, ctx.facts = keep, opts, facts
+            ctx.save_for_backward(A, R)
+            return Q, R
+
+        @staticmethod
+        def backward(ctx, Qbar, Rbar):
+            A, R = ctx.saved_tensors
+            nb, m, n = A.shape
+            cur = torch.cuda.current_stream(A.device)
+            streams = _side_streams(A.device)
+            Abar = torch.empty_like(A)
+            qb = Qbar.contiguous() if Qbar is not None else None
+            rb = Rbar.contiguous() if Rbar is not None else None
+            ready = torch.cuda.Event()
+            ready.record(cur)
+            for i in range(nb):
+                s = streams[i % len(streams)]
+                s.wait_event(ready)
+                with torch.cuda.stream(s):
+                    f = ctx.facts[i] if ctx.keep == "tree" else Factorization(A[i], **ctx.opts)
+                    tsqr_backward(f.handle, qb[i].data_ptr() if qb is not None else None, n,
+                                  rb[i].data_ptr() if rb is not None else None, n, R[i].data_ptr(), n,
+                                  Abar[i].data_ptr(), n, _stream())
+                    if ctx.keep != "tree":
+                        f.close()
+            for s in streams:
+                cur.wait_stream(s)
+            ctx.facts = None
+            return Abar, None, None
+
+    return QR, QRBatch
 
 
 _QR = None
+_QRB = None
+_SIDE = {}
+
+
+def _side_streams(device, count=8):
+    """The pool of CUDA streams a batch of factorizations is spread over (one pool per device)."""
+    import torch
+
+    key = torch.device(device).index
+    if key not in _SIDE:
+        _SIDE[key] = [torch.cuda.Stream(device) for _ in range(count)]
+    return _SIDE[key]
 
 
 def qr_autograd(A, keep="tree", **opts):
-    """Differentiable thin QR of a CUDA float64 or float32 matrix (or a batch: leading dimensions looped).
-    Returns (Q, R) with diag(R) >= 0; gradients flow through tsqr_backward."""
-    global _QR
+    """Differentiable thin QR of a CUDA float64 or float32 matrix, or of a batch (B x m x n, the
+    matrices factored concurrently on several streams).  Returns (Q, R) with diag(R) >= 0;
+    gradients flow through tsqr_backward."""
+    global _QR, _QRB
     if _QR is None:
-        _QR = _qr_function()
+        _QR, _QRB = _qr_function()
     if A.dim() == 2:
         return _QR.apply(A, keep, dict(opts))
-    import torch
-
-    outs = [_QR.apply(A[i], keep, dict(opts)) for i in range(A.shape[0])]
-    return torch.stack([q for q, _ in outs]), torch.stack([r for _, r in outs])
+    if A.dim() != 3:
+        raise ValueError("A must be m x n or B x m x n")
+    return _QRB.apply(A.contiguous(), keep, dict(opts))

@@ -137,3 +137,25 @@ def test_f32_against_cpu_reference(T, m, n):
     g = A.grad.double().cpu().numpy()
     ref = reference_grad(A32.astype(np.float64), W1.astype(np.float64), W2.astype(np.float64))
     assert np.linalg.norm(g - ref) / np.linalg.norm(ref) <= 50 * 10 * n * 2.0 ** -24
+
+
+@pytest.mark.parametrize("dtype,keep", [("float64", "tree"), ("float32", "tree"), ("float64", "recompute")])
+def test_batch_matches_single(T, dtype, keep):
+    """The batched function (matrices spread over CUDA streams) gives the per-matrix results
+    bitwise: forward Q, R and the gradient."""
+    import torch
+
+    tdt = getattr(torch, dtype)
+    A_h = np.stack([inputs.gaussian(4000 + 0, 24, 90 + i) for i in range(5)])
+    W = np.random.default_rng(91).standard_normal(A_h.shape)
+    A = torch.from_numpy(A_h).to(tdt).cuda().requires_grad_(True)
+    w = torch.from_numpy(W).to(tdt).cuda()
+    Q, R = T.qr_autograd(A, keep=keep)
+    ((w * Q).sum() + R.sum()).backward()
+    g_batch = A.grad.clone()
+    for i in range(A.shape[0]):
+        Ai = A.detach()[i].clone().requires_grad_(True)
+        Qi, Ri = T.qr_autograd(Ai, keep=keep)
+        ((w[i] * Qi).sum() + Ri.sum()).backward()
+        assert torch.equal(Qi, Q[i]) and torch.equal(Ri, R[i])
+        assert torch.equal(Ai.grad, g_batch[i])
