@@ -35,7 +35,7 @@ __device__ inline void tri_mul(const typename Ar::E* T, int ldt, const typename 
         for (int p = 0; p <= a; ++p) Ar::fma_acc(s, T[p * ldt + a], C[p * ldc + b]);
       }
     }
-    M[a * ldm + b] = Ar::add(s, Ar::zero());
+    M[a * ldm + b] = Ar::fin(s);
   }
 }
 
@@ -121,7 +121,7 @@ __device__ __forceinline__ void formq_tree_node(const Plan& P, const Store& st, 
         const int a = i / np, b = i % np;
         E v = Ar::zero();
         for (int p = a; p < n; ++p) Ar::fma_acc(v, f.X[a * ld + p], f.M[p * ld + b]);
-        out[i] = Ar::neg(Ar::add(v, Ar::zero()));
+        out[i] = Ar::neg(Ar::fin(v));
       }
       __syncthreads();
     }
@@ -182,7 +182,7 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
         for (int r = gown; r < rows_valid; r += G) {
           E v = Ar::zero();
           for (int a = 0; a < n; ++a) Ar::fma_acc(v, tat<E>(S, r, a), f.M[a * ld + cown]);
-          Q[(row0 + r) * ldq + cown] = -Ar::to_out(Ar::add(v, Ar::zero()));
+          Q[(row0 + r) * ldq + cown] = -Ar::to_out(Ar::fin(v));
         }
       }
       for (int i = tid; i < np * np; i += kThreads) {
@@ -198,7 +198,7 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
         if (a < n) {
           v = f.C[a * ld + b];
           for (int r = a + 1; r < n; ++r) Ar::fma_acc(v, tat<E>(S, r, a), f.C[r * ld + b]);
-          v = Ar::add(v, Ar::zero());
+          v = Ar::fin(v);
         }
         f.X[a * ld + b] = v;
       }
@@ -212,7 +212,7 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
           const int amax = (r < n) ? r : n;
           for (int a = 0; a < amax; ++a) Ar::fma_acc(acc, tat<E>(S, r, a), f.M[a * ld + cown]);
           if (r < n) Ar::fma_acc(acc, Ar::from_int(1), f.M[r * ld + cown]);
-          E v = Ar::neg(Ar::add(acc, Ar::zero()));
+          E v = Ar::neg(Ar::fin(acc));
           if (r < n) v = Ar::add(v, f.C[r * ld + cown]);
           Q[(row0 + r) * ldq + cown] = Ar::to_out(v);
         }
@@ -735,7 +735,7 @@ __device__ inline void wy_update(const Tile& S, bool plain, int h, int n, int np
     const int amax = plain ? (r < n ? r : n) : n;
     for (int a = 0; a < amax; ++a) Ar::fma_acc(acc, tat<E>(S, r, a), W2[a * kb + b]);
     if (plain && r < n) Ar::fma_acc(acc, Ar::from_int(1), W2[r * kb + b]);
-    B[o] = Ar::sub(B[o], Ar::add(acc, Ar::zero()));
+    B[o] = Ar::sub(B[o], Ar::fin(acc));
   }
   if (!plain)
     for (int o = threadIdx.x; o < np * kb; o += kThreads) C[o] = Ar::sub(C[o], W2[o]);
@@ -778,7 +778,7 @@ __device__ inline void node_apply(ApplySmem<typename Ar::E>& f, const Plan& P, c
       const int a = o / kb, b = o % kb;
       E v = f.W[o];
       for (int r = 0; r <= a && r < n; ++r) Ar::fma_acc(v, f.Y[r * ld + a], Cs[r * kb + b]);
-      f.W[o] = Ar::add(v, Ar::zero());
+      f.W[o] = Ar::fin(v);
     }
     __syncthreads();
   }
@@ -793,7 +793,7 @@ __device__ inline void node_apply(ApplySmem<typename Ar::E>& f, const Plan& P, c
       const int a = o / kb, b = o % kb;
       E acc = Ar::zero();
       for (int p = a; p < n; ++p) Ar::fma_acc(acc, f.Y[a * ld + p], f.W2[p * kb + b]);
-      Cs[o] = Ar::sub(Cs[o], Ar::add(acc, Ar::zero()));
+      Cs[o] = Ar::sub(Cs[o], Ar::fin(acc));
     }
     __syncthreads();
   }

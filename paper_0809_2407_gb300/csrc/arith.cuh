@@ -39,6 +39,8 @@ struct ArithF64 {
   __device__ __forceinline__ static Out to_out(E x) { return x; }
   __device__ __forceinline__ static E zero() { return 0.0; }
   __device__ __forceinline__ static E from_int(int v) { return (double)v; }
+  // an accumulated value in its final form (the double-float sums end unnormalised)
+  __device__ __forceinline__ static E fin(E x) { return x; }
   // s += a * b
   __device__ __forceinline__ static void fma_acc(E& s, E a, E b) { s = fma(a, b, s); }
   __device__ __forceinline__ static E add(E a, E b) { return a + b; }
@@ -105,6 +107,7 @@ struct ArithDF {
   }
   __device__ __forceinline__ static E neg(E a) { return E{-a.hi, -a.lo}; }
   __device__ __forceinline__ static E sub(E a, E b) { return add(a, neg(b)); }
+  __device__ __forceinline__ static E fin(E x) { return add(x, zero()); }
   __device__ __forceinline__ static E mul(E a, E b) {
     float p, e;
     prod(a, b, p, e);
@@ -162,6 +165,7 @@ struct ArithF32 {
   __device__ __forceinline__ static Out to_out(E x) { return x.hi; }
   __device__ __forceinline__ static E zero() { return mk(0.f); }
   __device__ __forceinline__ static E from_int(int v) { return mk((float)v); }
+  __device__ __forceinline__ static E fin(E x) { return x; }
   __device__ __forceinline__ static void fma_acc(E& s, E a, E b) { s.hi = __fmaf_rn(a.hi, b.hi, s.hi); }
   __device__ __forceinline__ static E add(E a, E b) { return mk(__fadd_rn(a.hi, b.hi)); }
   __device__ __forceinline__ static E sub(E a, E b) { return mk(__fsub_rn(a.hi, b.hi)); }

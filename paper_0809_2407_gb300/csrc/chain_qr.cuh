@@ -97,6 +97,9 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
       block_offsets(rc, j, oj);
       if (cown < n && cown != j) {
         // four independent partial sums so consecutive multiply-adds do not wait on each other
+        // on the FP32 pipe; FP64 keeps one: its pipe, not the latency, bounds the dots, and the
+        // three adds that join four sums are FP64 instructions too
+        constexpr int kAcc = Ar::kPrecision == 0 ? 1 : 4;
         E acc[4] = {Ar::zero(), Ar::zero(), Ar::zero(), Ar::zero()};
 #pragma unroll
         for (int bb = 0; bb < NBG; ++bb) {
@@ -105,10 +108,13 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
           for (int t = 0; t < 8; ++t) {
             const E x = *reinterpret_cast<const E*>(pb + oj[t]);
             const E a = *reinterpret_cast<const E*>(pb + oc[t]);
-            Ar::fma_acc(acc[t & 3], x, a);
+            Ar::fma_acc(acc[t % kAcc], x, a);
           }
         }
-        w.red[gown * NP + cown] = Ar::add(Ar::add(acc[0], acc[1]), Ar::add(acc[2], acc[3]));
+        if constexpr (kAcc == 1)
+          w.red[gown * NP + cown] = Ar::fin(acc[0]);
+        else
+          w.red[gown * NP + cown] = Ar::add(Ar::add(acc[0], acc[1]), Ar::add(acc[2], acc[3]));
       }
       __syncthreads();
       // ---- B: d_c = S(j,c) + inv D_c (c > j): pivot-row update and the update weight;
@@ -200,7 +206,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
         for (int p = 2 * b * k + b; p <= c2; ++p)
           Ar::fma_acc(v, T_s[tri_off(r1, NP) + (p - r1)], T_s[tri_off(p, NP) + (c2 - p)]);
       }
-      w.X[o] = Ar::add(v, Ar::zero());
+      w.X[o] = Ar::fin(v);
     }
     __syncthreads();
     // T12 = -T1 * X
@@ -211,7 +217,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
         E v = Ar::zero();
         for (int p = r1; p < 2 * b * k + b; ++p)
           Ar::fma_acc(v, T_s[tri_off(r1, NP) + (p - r1)], w.X[(k * b + (p - 2 * b * k)) * b + q]);
-        T_s[tri_off(r1, NP) + (c2 - r1)] = Ar::neg(Ar::add(v, Ar::zero()));
+        T_s[tri_off(r1, NP) + (c2 - r1)] = Ar::neg(Ar::fin(v));
       }
     }
     __syncthreads();

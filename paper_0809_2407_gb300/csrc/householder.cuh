@@ -91,8 +91,17 @@ __device__ inline void reflector_warp<ArithF64>(const Tile& S, int kind, int N, 
         }
       }
       beta = (alpha >= 0.0) ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      inv = 1.0 / (alpha - beta);
+      const double d = alpha - beta;  // |d| = |alpha| + |beta|, in [|beta|, 2 |beta|]
+      if (full >= 0x1p-900 && full <= 0x1p+900) {
+        // one division: q = 1/(beta d), with |beta d| in [full, 2 full] (no over- or underflow);
+        // then 1/d = beta q and tau = (beta - alpha)/beta = -d^2 q
+        const double q = 1.0 / (beta * d);
+        inv = beta * q;
+        tau = -(d * d) * q;
+      } else {
+        tau = (beta - alpha) / beta;
+        inv = 1.0 / d;
+      }
     }
     if (lane == 0) {
       sc[0] = beta;
@@ -270,7 +279,7 @@ __device__ inline void stacked_qr(const Tile& S, int kind, int N, int np, int n,
         const E* Ti = T_s + tri_off(tid, np) - tid;  // Ti[p] = T[tid][p]
         E s = Ar::zero();
         for (int p = tid; p < j; ++p) Ar::fma_acc(s, Ti[p], dvec[p]);
-        T_s[tri_off(tid, np) + (j - tid)] = Ar::neg(Ar::mul(tau, Ar::add(s, Ar::zero())));
+        T_s[tri_off(tid, np) + (j - tid)] = Ar::neg(Ar::mul(tau, Ar::fin(s)));
       }
       // trailing update S(r, c) -= tau d_c y_r.  Only the ac = n-1-j columns right of j take
       // part, so they are spread over all threads afresh for every j: an FP64 instruction costs
