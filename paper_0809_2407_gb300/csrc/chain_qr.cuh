@@ -197,16 +197,17 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
   // ---- T from the Gram entries by blocked merges (sizes b = 2^lb = 1, 2, 4, ... NP/2)
   for (int b = 1, lb = 0; b < n; b <<= 1, ++lb) {
     const int pairs = (n + 2 * b - 1) >> (lb + 1);
-    // X = G12 * T2 for every pair (G12 at rows blk1, cols blk2 of T_s; T2 upper)
+    // X = G12 * T2 for every pair (G12 at rows blk1, cols blk2 of T_s; T2 upper).  The row i
+    // varies fastest across the lanes so that the loop length (q + 1) is the same in a warp.
     for (int o = tid; o < (pairs << (2 * lb)); o += kThreads) {
-      const int k = o >> (2 * lb), i = (o >> lb) & (b - 1), q = o & (b - 1);
+      const int k = o >> (2 * lb), q = (o >> lb) & (b - 1), i = o & (b - 1);
       const int r1 = 2 * b * k + i, c2 = 2 * b * k + b + q;
       E v = Ar::zero();
       if (r1 < n && c2 < n) {
         for (int p = 2 * b * k + b; p <= c2; ++p)
           Ar::fma_acc(v, T_s[tri_off(r1, NP) + (p - r1)], T_s[tri_off(p, NP) + (c2 - p)]);
       }
-      w.X[o] = Ar::fin(v);
+      w.X[(k * b + i) * b + q] = Ar::fin(v);
     }
     __syncthreads();
     // T12 = -T1 * X
