@@ -39,6 +39,24 @@ def algorithmic_bytes(m, n, k=1):
     return {"factor": 16.0 * m * n, "form_q": 16.0 * m * n, "apply_qt": 8.0 * m * n + 16.0 * m * k}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (the slowest replica's time); x itself without a process
+    group.  Every rank gets the result."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_value(units_per_step_per_rank, world, ms_per_step):
+    """Whole-job throughput: every rank processes the same units per step (weak scaling), and the
+    job's step time is the slowest rank's."""
+    return units_per_step_per_rank * world / (ms_per_step / 1e3) / 1e9
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -548,10 +566,7 @@ def main():
         ev = {"factor": [mk[0].elapsed_time(mk[1]) for mk in all_marks],
               "form_q": [mk[1].elapsed_time(mk[2]) for mk in all_marks],
               "apply_qt": [mk[2].elapsed_time(mk[3]) for mk in all_marks]}
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = t.item()
+        ms = max_over_ranks(ms, dist, dev)
         Ad, Qd, Rd = A_.double(), Q_.double(), R_.double()
         be = (torch.linalg.norm(Ad - Qd @ Rd) / torch.linalg.norm(Ad)).item()
         orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Qd.T @ Qd).item()
@@ -576,7 +591,7 @@ def main():
     fl = flops(m, n)
     per_step = sum(fl.values())
     ms_step = ms / args.steps
-    value = per_step * world / (ms_step / 1e3) / 1e9
+    value = job_value(per_step, world, ms_step)
 
     # roofline of the dominant kernel (the factorization): FP64-pipe bound
     f_ms = statistics.mean(ev["factor"])
