@@ -652,27 +652,35 @@ struct ApplySmem {
   E* W;     // np x kb
   E* W2;    // np x kb
   E* T;     // np x (np+1)
-  E* Y;     // np x (np+1): one tree-node block
+  E* Y;     // np x (np+1): one tree-node block (shares the tile's region)
   E* red;   // kThreads
   uint64_t* bar;
   int* flag;
   int ldt, brows;
 };
 
+// The leaf tile and a tree node's Y block are never live together (the tree steps follow the
+// chain's leaves), so they share one region: the smaller footprint lets two blocks share an SM
+// when the column blocks are narrow.
+__host__ __device__ inline size_t apply_union_bytes(const Plan& P) {
+  const size_t s = (size_t)P.h * P.np * 8, y = (size_t)P.np * (P.np + 1) * 8;
+  return ((s > y ? s : y) + 15) & ~size_t(15);
+}
+
 template <class E>
 __device__ inline ApplySmem<E> carve_apply(char* raw, const Plan& P, int kb) {
   ApplySmem<E> f;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   f.S = Tile{base, P.h};
+  f.Y = reinterpret_cast<E*>(base);
   f.brows = max(P.h, P.arity * P.np);
   f.ldt = P.np + 1;
-  f.B = reinterpret_cast<E*>(base + (size_t)P.h * P.np * 8);
+  f.B = reinterpret_cast<E*>(base + apply_union_bytes(P));
   f.C = f.B + (size_t)f.brows * kb;
   f.W = f.C + P.np * kb;
   f.W2 = f.W + P.np * kb;
   f.T = f.W2 + P.np * kb;
-  f.Y = f.T + P.np * f.ldt;
-  f.red = f.Y + P.np * f.ldt;
+  f.red = f.T + P.np * f.ldt;
   f.bar = reinterpret_cast<uint64_t*>(f.red + kThreads);
   f.flag = reinterpret_cast<int*>(f.bar + 1);
   return f;
@@ -680,7 +688,7 @@ __device__ inline ApplySmem<E> carve_apply(char* raw, const Plan& P, int kb) {
 
 size_t apply_smem_bytes(const Plan& P, int kb) {
   const size_t brows = (size_t)(P.h > P.arity * P.np ? P.h : P.arity * P.np);
-  return 1024 + (size_t)P.h * P.np * 8 + brows * kb * 8 + 3 * (size_t)P.np * kb * 8 + 2 * (size_t)P.np * (P.np + 1) * 8 +
+  return 1024 + apply_union_bytes(P) + brows * kb * 8 + 3 * (size_t)P.np * kb * 8 + (size_t)P.np * (P.np + 1) * 8 +
          kThreads * 8 + 8 + 16;
 }
 
@@ -810,7 +818,7 @@ __device__ inline int64_t node_top_row(const Plan& P, int level, int idx) {
 
 // ---- Q^T B: chains leaves-first, then the tree bottom-up by last arrival, then D on the top.
 template <class Ar>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     apply_qt_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, int64_t k,
                     typename Ar::Out* __restrict__ Bg, int64_t ldb, int kb, int box_rows) {
   using E = typename Ar::E;
@@ -830,9 +838,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int64_t leaf = l0; leaf < l1; ++leaf) {
     const bool plain = (leaf == l0);
     const int64_t row0 = leaf * h;
-    load_square(st.t_leaf + leaf * np * np, f.T, np, f.ldt);
+    tile_load_start(f.S, &mapV, f.bar, np, row0, h, 0, box_rows);  // the reflector tile by TMA,
+    load_square(st.t_leaf + leaf * np * np, f.T, np, f.ldt);      // while T and B's rows load
     load_b<Ar>(Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
-    if (!tile_load(f.S, &mapV, f.bar, phase, np, row0, h, 0, box_rows, st.status, f.flag)) return;
+    if (!tile_load_finish(f.bar, phase, st.status, f.flag)) return;
     wy_inner<Ar>(f.S, plain, h, n, np, f.B, f.C, f.W, kb, f.red);
     __syncthreads();
     tri_mul<Ar>(f.T, f.ldt, f.W, kb, f.W2, kb, n, np, kb, true);
@@ -890,7 +899,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---- Q B, tree part: one launch per level, top-down; the root level first applies D.
 template <class Ar>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     apply_q_tree_kernel(const Plan P, const Store st, int level, int64_t k, typename Ar::Out* __restrict__ Bg,
                         int64_t ldb, int kb) {
   using E = typename Ar::E;
@@ -922,7 +931,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---- Q B, chains: last leaf first, the first leaf last.
 template <class Ar>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     apply_q_chain_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, int64_t k,
                          typename Ar::Out* __restrict__ Bg, int64_t ldb, int kb, int box_rows) {
   using E = typename Ar::E;
@@ -950,9 +959,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int64_t leaf = l1 - 1; leaf >= l0; --leaf) {
     const bool plain = (leaf == l0);
     const int64_t row0 = leaf * h;
+    tile_load_start(f.S, &mapV, f.bar, np, row0, h, 0, box_rows);
     load_square(st.t_leaf + leaf * np * np, f.T, np, f.ldt);
     load_b<Ar>(Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
-    if (!tile_load(f.S, &mapV, f.bar, phase, np, row0, h, 0, box_rows, st.status, f.flag)) return;
+    if (!tile_load_finish(f.bar, phase, st.status, f.flag)) return;
     if (plain)
       for (int o = tid; o < n * kb; o += kThreads) f.B[o] = f.C[o];
     __syncthreads();

@@ -181,6 +181,35 @@ __device__ inline bool tile_load(const Tile& t, const CUtensorMap* map, uint64_t
   return *flag == 0;
 }
 
+// tile_load split in two, so that other loads can proceed while the copy is in flight: start
+// issues it (all threads call; it synchronises the block first), finish waits for it (all
+// threads call; false in every thread on timeout, with the status word set).
+__device__ inline void tile_load_start(const Tile& t, const CUtensorMap* map, uint64_t* bar, int np, int64_t row0,
+                                       int rows, int dst_row, int box_rows) {
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)rows * (uint32_t)np * 8u);
+    for (int pnl = 0; pnl < np / 16; ++pnl)
+      for (int r = 0; r < rows; r += box_rows)
+        tma_load_2d(t.base + (size_t)pnl * t.rows_cap * 128 + (size_t)(dst_row + r) * 128, map, bar, pnl * 16,
+                    (int)(row0 + r));
+  }
+}
+__device__ inline bool tile_load_finish(uint64_t* bar, uint32_t& phase, int* status, int* flag) {
+  if (threadIdx.x == 0) {
+    const bool ok = mbar_wait_bounded(bar, phase, kWaitCycles);
+    *flag = ok ? 0 : 1;
+    if (!ok) {
+      atomicOr(status, kStatusTimeout);
+      mbar_wait_bounded(bar, phase, kWaitCycles);  // give the copy in flight one more bounded chance
+    }
+  }
+  phase ^= 1u;
+  __syncthreads();
+  return *flag == 0;
+}
+
 // Stores tile rows [src_row, src_row + rows) to matrix rows [row0, row0 + rows) (TMA clips
 // rows and columns outside the matrix).  Call after the tile is final; all threads.
 __device__ inline void tile_store(const Tile& t, const CUtensorMap* map, int np, int64_t row0, int rows, int src_row,
