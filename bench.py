@@ -458,7 +458,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-matrix batched workload")
     ap.add_argument("--no-autograd", action="store_true", help="skip the differentiable-QR workload")
     ap.add_argument("--no-shapes", action="store_true", help="skip the n = 16, 32, 128 shapes")
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 3],
                     help="arithmetic mode of the main line (0 native FP64; 1 and 2 are for profiling)")
     ap.add_argument("--fp32", action="store_true", help="main line in FP32 storage (for profiling)")
     args = ap.parse_args()
@@ -629,6 +629,14 @@ def main():
             "kernel_ms": {k: statistics.mean(v) for k, v in ozm["ev"].items()},
             "backward_error": ozm["be"], "orthogonality": ozm["orth"],
             "note": "native FP64 factor; thin-Q products T*C and Y*M on tcgen05 tensor cores as Ozaki splits"}
+        dzm = run_mode(3, args.steps, min(args.warmup, 3), False)
+        dz_ms = dzm["ms"] / args.steps
+        forms["df_ozaki_wy"] = {
+            "precision": 3, "dtype": "f32x2+bf16x8-split", "value": per_step * world / (dz_ms / 1e3) / 1e9,
+            "unit": "GFLOP/s", "ms_per_step": dz_ms, "speedup_vs_f64": ms_step / dz_ms,
+            "kernel_ms": {k: statistics.mean(v) for k, v in dzm["ev"].items()},
+            "backward_error": dzm["be"], "orthogonality": dzm["orth"],
+            "note": "double-float factor and Q^T b; thin-Q WY products as Ozaki splits on tcgen05"}
         f3 = run_mode(0, args.steps, min(args.warmup, 3), False, f32=True)
         s_ms = f3["ms"] / args.steps
         forms["fp32"] = {
@@ -683,7 +691,7 @@ def main():
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f32" if args.fp32 else {0: "f64", 1: "f32x2", 2: "f64"}[args.precision], "data": "synthetic",
+               "vs_baseline": None, "dtype": "f32" if args.fp32 else {0: "f64", 1: "f32x2", 2: "f64", 3: "f32x2"}[args.precision], "data": "synthetic",
                "config": {"workload": "tsqr factor + form_q + apply_qt(k=1), fp64, m=%d n=%d, A=U S V^T kappa=1"
                                       % (m, n), "m": m, "n": n, "k": 1, "leaf_h": None, "chain": "auto",
                           "arity": 2, "precision": args.precision, "l2": "inputs larger than L2 (A is %.1f GB)" % (8.0 * m * n / 1e9),

@@ -73,7 +73,14 @@ typedef struct {
                             of FP32 numbers (about 48 significant bits, unit roundoff ~2^-46) on
                             the FP32 pipe.  Magnitudes of A's and B's nonzero entries should lie
                             in about [2^-100, 2^100]; the stored factors (and A, with inplace)
-                            then hold (hi, lo) FP32 pairs in each 8-byte slot. */
+                            then hold (hi, lo) FP32 pairs in each 8-byte slot.
+                        2 = Ozaki WY: native FP64 reflectors, T and tree; the thin Q's compact-WY
+                            products T C and Y M as Ozaki splits (8 slices of 7 bits in bf16,
+                            exact FP32 group sums) on the tensor cores (n in 33..64, leaf_h <= 128;
+                            other shapes run mode 0).
+                        3 = double-float factorization and Q^T B / Q B, thin Q as in mode 2
+                            (other shapes run mode 1).
+                        Batches run mode 2 as 0 and mode 3 as 1. */
   int32_t inplace;   /* nonzero: the leaf reflectors overwrite A (Sec. 4.2 storage) and A's
                         upper triangles hold intermediate R factors; zero: A is read only */
 } tsqr_opts_t;

@@ -101,8 +101,9 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P, boo
   int np = 16;
   while (np < n) np *= 2;
   if (np > 64) return fail(TSQR_ERR_UNSUPPORTED, "n > 64 is not supported by this build");
-  if (o->precision < 0 || o->precision > 2)
-    return fail(TSQR_ERR_UNSUPPORTED, "precision must be 0 (native FP64), 1 (double-float) or 2 (Ozaki WY)");
+  if (o->precision < 0 || o->precision > 3)
+    return fail(TSQR_ERR_UNSUPPORTED,
+                "precision must be 0 (native FP64), 1 (double-float), 2 (Ozaki WY) or 3 (double-float + Ozaki WY)");
   if (f32 && o->precision != 0)
     return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 runs FP32 arithmetic: precision must be 0");
   if (f32 && o->inplace) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 keeps A read-only (inplace is not supported)");
@@ -118,7 +119,7 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P, boo
   P->np = np;
   P->h = h;
   P->arity = arity;
-  P->precision = f32 ? 3 : o->precision;
+  P->precision = f32 ? tsqr::kPrecF32 : o->precision;
   P->leaves = (m + h - 1) / h;
   int64_t chain = o->chain;
   if (chain == 0) {
@@ -126,7 +127,7 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P, boo
     // shorter chains, because the loss of orthogonality grows with the number of reflectors on
     // a row's path to the root (about sqrt(chain * n) units of roundoff), and the double-float
     // unit roundoff is 2^-46.
-    const int blocks = (o->precision == 1 ? 16 : 2) * device_sms();
+    const int blocks = (tsqr::prec_df(o->precision) ? 16 : 2) * device_sms();
     chain = (P->leaves + blocks - 1) / blocks;
   }
   if (chain > P->leaves) chain = P->leaves;
@@ -600,7 +601,10 @@ tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n,
   tsqr_opts_t base{};
   if (opts) base = *opts;
   if (base.inplace) return fail(TSQR_ERR_UNSUPPORTED, "batches keep A read-only (inplace is not supported)");
-  if (base.precision == 2) base.precision = 0;  // batched thin Q uses the FP64 kernels
+  // the batched thin Q runs on the FP64-pipe or FP32-pipe kernels: the Ozaki forms run as their
+  // factorization's arithmetic
+  if (base.precision == tsqr::kPrecOzaki) base.precision = tsqr::kPrecF64;
+  if (base.precision == tsqr::kPrecDFOzaki) base.precision = tsqr::kPrecDF;
   if (f32 && base.precision != 0)
     return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 runs FP32 arithmetic: precision must be 0");
   // shared chain length: about 16 waves of two blocks per SM over the whole batch; double-float
@@ -618,7 +622,7 @@ tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n,
     const int64_t blocks = 16LL * 2 * device_sms();
     int64_t c = (total_leaves + blocks - 1) / blocks;
     if (c < 1) c = 1;
-    if (base.precision == 1 && c > 18) c = 18;
+    if (tsqr::prec_df(base.precision) && c > 18) c = 18;
     base.chain = (int32_t)c;
   }
   bp->plans.resize(count);

@@ -172,8 +172,9 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
   for (int64_t leaf = l1 - 1; leaf >= l0; --leaf) {
     const bool plain = (leaf == l0);
     const int64_t row0 = leaf * h;
+    tile_load_start(S, mapV_p, f.bar, np, row0, h, 0, box_rows);  // the tile by TMA while T loads
     load_square(st.t_leaf + leaf * np * np, f.T, np, ld);
-    if (!tile_load(S, mapV_p, f.bar, phase, np, row0, h, 0, box_rows, st.status, f.flag)) return;
+    if (!tile_load_finish(f.bar, phase, st.status, f.flag)) return;
     const int64_t rows_valid = (P.m - row0 < h) ? (P.m - row0) : h;
     if (!plain) {
       tri_mul<Ar>(f.T, ld, f.C, ld, f.M, ld, n, np, np, false);
@@ -258,8 +259,8 @@ static cudaError_t prepare_form_q_batched_t(size_t smem) {
 }
 
 cudaError_t prepare_form_q_batched(int precision, size_t smem) {
-  if (precision == 1) return prepare_form_q_batched_t<ArithDF>(smem);
-  if (precision == 3) return prepare_form_q_batched_t<ArithF32>(smem);
+  if (prec_df(precision)) return prepare_form_q_batched_t<ArithDF>(smem);
+  if (precision == kPrecF32) return prepare_form_q_batched_t<ArithF32>(smem);
   return prepare_form_q_batched_t<ArithF64>(smem);
 }
 
@@ -281,10 +282,10 @@ static cudaError_t launch_form_q_batched_t(const BatchItem* items, const BatchWo
 cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain_work, int chain_blocks,
                                   const BatchWork* const* level_work, const int* level_blocks, int depth,
                                   int precision, size_t smem, cudaStream_t stream) {
-  if (precision == 1)
+  if (prec_df(precision))
     return launch_form_q_batched_t<ArithDF>(items, chain_work, chain_blocks, level_work, level_blocks, depth, smem,
                                             stream);
-  if (precision == 3)
+  if (precision == kPrecF32)
     return launch_form_q_batched_t<ArithF32>(items, chain_work, chain_blocks, level_work, level_blocks, depth, smem,
                                              stream);
   return launch_form_q_batched_t<ArithF64>(items, chain_work, chain_blocks, level_work, level_blocks, depth, smem,
@@ -349,6 +350,13 @@ __device__ __forceinline__ uint32_t slice_pair(uint64_t f0, uint64_t f1, int s) 
   const float x1 = __fsub_rn(__int_as_float(0x4B000000 | c1), 8388608.f);
   const uint32_t sg = ((uint32_t)(f0 >> 48) & 0x8000u) | ((uint32_t)(f1 >> 32) & 0x80000000u);
   return __byte_perm(__float_as_uint(x0), __float_as_uint(x1), 0x7632) | sg;
+}
+
+// *dst = max(*dst, e over the warp), for a full warp whose lanes all target dst (the callers'
+// index idx >> 6 is the same across 32 consecutive idx): one shared atomic per warp.
+__device__ __forceinline__ void warp_max_into(int* dst, int e) {
+  const int m = __reduce_max_sync(0xffffffffu, e);
+  if ((threadIdx.x & 31) == 0) atomicMax(dst, m);
 }
 
 // Waits (thread 0, bounded) for a barrier phase; every thread learns the outcome.
@@ -420,7 +428,7 @@ __device__ inline void ozaki_b_slices(const OzSmem& z, BVal bval) {
   const int tid = threadIdx.x;
   for (int j = tid; j < 64; j += kOzT) z.expB[j] = 0;
   __syncthreads();
-  for (int idx = tid; idx < 64 * 64; idx += kOzT) atomicMax(&z.expB[idx >> 6], oz::bexp(bval(idx >> 6, idx & 63)));
+  for (int idx = tid; idx < 64 * 64; idx += kOzT) warp_max_into(&z.expB[idx >> 6], oz::bexp(bval(idx >> 6, idx & 63)));
   __syncthreads();
   for (int idx = tid; idx < 64 * 32; idx += kOzT) {
     const int j = idx >> 5, k = (idx & 31) * 2;
@@ -480,6 +488,19 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
+// The value of an 8-byte workspace slot: a double, or a double-float (hi, lo) pair when the
+// factorization ran in double-float arithmetic (the sum is exact in FP64).
+template <bool kPairs>
+__device__ __forceinline__ double slot_val(double raw) {
+  if constexpr (kPairs) {
+    const f32x2 p = *reinterpret_cast<const f32x2*>(&raw);
+    return (double)p.hi + (double)p.lo;
+  } else {
+    return raw;
+  }
+}
+
+template <bool kPairs>
 __global__ void __launch_bounds__(kOzT, 1)
     formq_ozaki_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
                        int64_t ldq, int box_rows) {
@@ -504,7 +525,7 @@ __global__ void __launch_bounds__(kOzT, 1)
   for (int i = tid; i < np * np; i += kOzT) {
     const int a = i / np, b = i % np;
     z.C[a * kOzLd + b] = (P.depth == 0) ? ((a == b && a < n) ? __ldcg(st.signs + a) : 0.0)
-                                        : __ldcg(st.node_r + (size_t)g * np * np + i);
+                                        : slot_val<kPairs>(__ldcg(st.node_r + (size_t)g * np * np + i));
   }
   __syncthreads();
   const int64_t l0 = chain_first_leaf(P, g), l1 = chain_end_leaf(P, g);
@@ -539,9 +560,11 @@ __global__ void __launch_bounds__(kOzT, 1)
         }
       }
       long long* Tfix = reinterpret_cast<long long*>(z.M);
+      if constexpr (kPairs)
+        for (int idx = tid; idx < np * np; idx += kOzT) z.M[idx] = slot_val<true>(z.M[idx]);
       for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
       __syncthreads();
-      for (int idx = tid; idx < np * np; idx += kOzT) atomicMax(&z.expA[idx >> 6], oz::bexp(z.M[idx]));
+      for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], oz::bexp(z.M[idx]));
       __syncthreads();
       for (int idx = tid; idx < np * np; idx += kOzT) Tfix[idx] = (long long)oz::to_fixed(z.M[idx], z.expA[idx >> 6]);
       __syncthreads();
@@ -567,10 +590,15 @@ __global__ void __launch_bounds__(kOzT, 1)
           break;
         }
       }
+      if constexpr (kPairs)
+        for (int idx = tid; idx < h * np; idx += kOzT) {
+          double* p = z.Y.ptr(idx >> 6, idx & 63);
+          *p = slot_val<true>(*p);
+        }
       for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
       __syncthreads();
       for (int idx = tid; idx < h * np; idx += kOzT)
-        atomicMax(&z.expA[idx >> 6], oz::bexp(*z.Y.ptr(idx >> 6, idx & 63)));
+        warp_max_into(&z.expA[idx >> 6], oz::bexp(*z.Y.ptr(idx >> 6, idx & 63)));
       __syncthreads();
       for (int idx = tid; idx < h * np; idx += kOzT) {
         double* p = z.Y.ptr(idx >> 6, idx & 63);
@@ -589,10 +617,17 @@ __global__ void __launch_bounds__(kOzT, 1)
       // ---- first leaf, native FP64: Q_rows = [C; 0] - V (T (V_top^T C))
       double* T = reinterpret_cast<double*>(z.bsl);
       double* X = T + np * np;
-      for (int i = tid; i < np * np; i += kOzT) T[i] = __ldcg(Tg + i);
+      for (int i = tid; i < np * np; i += kOzT) T[i] = slot_val<kPairs>(__ldcg(Tg + i));
       if (!tile_load(z.Y, &mapV, z.bars, y_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
         alive = false;
         break;
+      }
+      if constexpr (kPairs) {
+        for (int idx = tid; idx < h * np; idx += kOzT) {
+          double* p = z.Y.ptr(idx >> 6, idx & 63);
+          *p = slot_val<true>(*p);
+        }
+        __syncthreads();
       }
       for (int o = tid; o < np * np; o += kOzT) {
         const int a = o / np, b = o % np;
@@ -1004,23 +1039,37 @@ static cudaError_t launch_form_q_t(const CUtensorMap& mapV, const Plan& P, const
 static cudaError_t launch_form_q_ozaki(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q_,
                                        int64_t ldq, int box_rows, cudaStream_t stream) {
   double* Q = static_cast<double*>(Q_);
+  const bool pairs = prec_df(P.precision);  // the factorization ran in double-float arithmetic
   const size_t smem_tree = formq_smem_bytes(P);
-  cudaError_t e =
-      cudaFuncSetAttribute(formq_tree_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tree);
+  cudaError_t e = pairs ? cudaFuncSetAttribute(formq_tree_kernel<ArithDF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem_tree)
+                        : cudaFuncSetAttribute(formq_tree_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem_tree);
   if (e != cudaSuccess) return e;
   for (int level = P.depth; level >= 1; --level) {
-    formq_tree_kernel<ArithF64><<<P.level_count[level], kThreads, smem_tree, stream>>>(P, st, level);
+    if (pairs)
+      formq_tree_kernel<ArithDF><<<P.level_count[level], kThreads, smem_tree, stream>>>(P, st, level);
+    else
+      formq_tree_kernel<ArithF64><<<P.level_count[level], kThreads, smem_tree, stream>>>(P, st, level);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   const size_t smem = formq_ozaki_smem_bytes(P);
-  e = cudaFuncSetAttribute(formq_ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  formq_ozaki_kernel<<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+  if (pairs) {
+    e = cudaFuncSetAttribute(formq_ozaki_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    formq_ozaki_kernel<true><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+  } else {
+    e = cudaFuncSetAttribute(formq_ozaki_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    formq_ozaki_kernel<false><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+  }
   return cudaGetLastError();
 }
 
-bool ozaki_form_q_applies(const Plan& P) { return P.precision == 2 && P.np == 64 && P.h <= 128; }
+bool ozaki_form_q_applies(const Plan& P) {
+  return (P.precision == kPrecOzaki || P.precision == kPrecDFOzaki) && P.np == 64 && P.h <= 128;
+}
 
 // FP32 storage: the tree levels on the FP32 pipe, the chains with bf16x3 tensor-core products.
 static cudaError_t launch_form_q_bf16x3(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q, int64_t ldq,
@@ -1039,10 +1088,10 @@ static cudaError_t launch_form_q_bf16x3(const CUtensorMap& mapV, const Plan& P, 
 
 cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q, int64_t ldq,
                           int box_rows, cudaStream_t stream) {
-  if (P.precision == 1) return launch_form_q_t<ArithDF>(mapV, P, st, Q, ldq, box_rows, stream);
-  if (bf16x3_form_q_applies(P)) return launch_form_q_bf16x3(mapV, P, st, Q, ldq, box_rows, stream);
-  if (P.precision == 3) return launch_form_q_t<ArithF32>(mapV, P, st, Q, ldq, box_rows, stream);
   if (ozaki_form_q_applies(P)) return launch_form_q_ozaki(mapV, P, st, Q, ldq, box_rows, stream);
+  if (prec_df(P.precision)) return launch_form_q_t<ArithDF>(mapV, P, st, Q, ldq, box_rows, stream);
+  if (bf16x3_form_q_applies(P)) return launch_form_q_bf16x3(mapV, P, st, Q, ldq, box_rows, stream);
+  if (P.precision == kPrecF32) return launch_form_q_t<ArithF32>(mapV, P, st, Q, ldq, box_rows, stream);
   return launch_form_q_t<ArithF64>(mapV, P, st, Q, ldq, box_rows, stream);
 }
 
@@ -1069,8 +1118,8 @@ static cudaError_t launch_apply_qt_t(const CUtensorMap& mapV, const Plan& P, con
 
 cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B,
                             int64_t ldb, int box_rows, cudaStream_t stream) {
-  if (P.precision == 1) return launch_apply_qt_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
-  if (P.precision == 3) return launch_apply_qt_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);
+  if (prec_df(P.precision)) return launch_apply_qt_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
+  if (P.precision == kPrecF32) return launch_apply_qt_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);
   return launch_apply_qt_t<ArithF64>(mapV, P, st, k, B, ldb, box_rows, stream);
 }
 
@@ -1104,8 +1153,8 @@ static cudaError_t launch_apply_q_t(const CUtensorMap& mapV, const Plan& P, cons
 
 cudaError_t launch_apply_q(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B,
                            int64_t ldb, int box_rows, cudaStream_t stream) {
-  if (P.precision == 1) return launch_apply_q_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
-  if (P.precision == 3) return launch_apply_q_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);
+  if (prec_df(P.precision)) return launch_apply_q_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
+  if (P.precision == kPrecF32) return launch_apply_q_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);
   return launch_apply_q_t<ArithF64>(mapV, P, st, k, B, ldb, box_rows, stream);
 }
 

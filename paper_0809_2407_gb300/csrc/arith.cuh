@@ -157,7 +157,7 @@ struct ArithDF {
 struct ArithF32 {
   using E = f32x2;  // lo == 0
   using Out = float;
-  static constexpr int kPrecision = 3;
+  static constexpr int kPrecision = 16;
   __device__ __forceinline__ static E mk(float v) { return E{v, 0.f}; }
   __device__ __forceinline__ static E from_f64(double x) { return mk(__double2float_rn(x)); }
   __device__ __forceinline__ static double to_f64(E x) { return (double)x.hi; }

@@ -12,7 +12,15 @@ constexpr int kThreads = 256;     // threads per block of every kernel
 constexpr int kMaxLevels = 40;    // tree levels above the chains
 constexpr int kMaxArity = 8;
 constexpr int kMaxColBlocks = 64; // column blocks of B per apply launch
-constexpr int kStatusTimeout = 1; // bit in the device status word
+constexpr int kStatusTimeout = 1;
+
+// Plan::precision: the arithmetic of a factorization.
+constexpr int kPrecF64 = 0;      // native FP64
+constexpr int kPrecDF = 1;       // double-float (FP32 pairs) everywhere
+constexpr int kPrecOzaki = 2;    // native FP64; thin-Q WY products as Ozaki splits on tcgen05
+constexpr int kPrecDFOzaki = 3;  // double-float factor and apply; thin Q as in kPrecOzaki
+constexpr int kPrecF32 = 16;     // FP32 storage and arithmetic
+__host__ __device__ inline bool prec_df(int p) { return p == kPrecDF || p == kPrecDFOzaki; } // bit in the device status word
 
 // Kinds of stacked matrices a Householder QR is taken of (rows that column j's reflector
 // touches, besides the pivot row j):

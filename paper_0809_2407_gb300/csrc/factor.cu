@@ -219,18 +219,18 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 cudaError_t prepare_factor_batched(int precision, size_t smem) {
-  if (precision == 1)
+  if (prec_df(precision))
     return cudaFuncSetAttribute(factor_batched_kernel<ArithDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (precision == 3)
+  if (precision == kPrecF32)
     return cudaFuncSetAttribute(factor_batched_kernel<ArithF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaFuncSetAttribute(factor_batched_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work, int blocks, int precision,
                                   size_t smem, cudaStream_t stream) {
-  if (precision == 1)
+  if (prec_df(precision))
     factor_batched_kernel<ArithDF><<<blocks, kThreads, smem, stream>>>(items, work);
-  else if (precision == 3)
+  else if (precision == kPrecF32)
     factor_batched_kernel<ArithF32><<<blocks, kThreads, smem, stream>>>(items, work);
   else
     factor_batched_kernel<ArithF64><<<blocks, kThreads, smem, stream>>>(items, work);
@@ -309,8 +309,8 @@ cudaError_t launch_stage_widen(const float* A, int64_t lda, double* V, int64_t l
 
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                           void* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
-  if (P.precision == 1) return launch_factor_t<ArithDF>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
-  if (P.precision == 3) return launch_factor_t<ArithF32>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
+  if (prec_df(P.precision)) return launch_factor_t<ArithDF>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
+  if (P.precision == kPrecF32) return launch_factor_t<ArithF32>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
   return launch_factor_t<ArithF64>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
 }
 

@@ -316,7 +316,7 @@ size_t formq_bf16x3_smem_bytes(const Plan& P) {
   return 1024 + ybytes + 3 * kTermA + 3 * kTermB + 64 * 64 * 8 + 2 * 64 * kLd * 4 + 3 * 8 + 8 + 16;
 }
 
-bool bf16x3_form_q_applies(const Plan& P) { return P.precision == 3 && P.np == 64 && P.h <= 128; }
+bool bf16x3_form_q_applies(const Plan& P) { return P.precision == kPrecF32 && P.np == 64 && P.h <= 128; }
 
 cudaError_t launch_formq_bf16x3_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, float* Q, int64_t ldq,
                                        int box_rows, cudaStream_t stream) {

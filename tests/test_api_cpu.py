@@ -51,13 +51,13 @@ def test_workspace_size_grows_with_m(lib):
     (10, 20, None, 1),                      # m < n
     (100, 0, None, 1),                      # n < 1
     (10000, 5000, None, 2),                 # n > 4096
-    (1000, 200, {"precision": 3}, 2),       # every panel's plan is checked
+    (1000, 200, {"precision": 4}, 2),       # every panel's plan is checked
     (1000, 16, {"arity": 1}, 1),
     (1000, 16, {"arity": 9}, 1),
     (1000, 16, {"leaf_h": 12}, 1),          # not a multiple of 8
     (1000, 16, {"leaf_h": 8}, 1),           # below padded n
     (1000, 16, {"leaf_h": 384}, 1),         # above 256 but not a multiple of 256
-    (1000, 16, {"precision": 3}, 2),
+    (1000, 16, {"precision": 4}, 2),
 ])
 def test_invalid_plans(lib, m, n, opts, status):
     with pytest.raises(lib.TsqrError) as ei:

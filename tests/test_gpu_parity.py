@@ -53,10 +53,10 @@ def run(T, A_h, lda=None, **opts):
     return f, f.R.cpu().numpy(), Q.cpu().numpy()
 
 
-UNIT = {0: 2.0 ** -53, 1: 2.0 ** -46, 2: 2.0 ** -50}
+UNIT = {0: 2.0 ** -53, 1: 2.0 ** -46, 2: 2.0 ** -50, 3: 2.0 ** -46}
 
 
-@pytest.fixture(params=[0, 1, 2], ids=["f64", "df", "ozaki"])
+@pytest.fixture(params=[0, 1, 2, 3], ids=["f64", "df", "ozaki", "df_ozaki"])
 def prec(request):
     return request.param
 
@@ -547,7 +547,7 @@ def test_precision_forms_conditioning(T, n):
     for k in (0, 4, 8):
         A_h = inputs.usv(m, n, k, inputs.seed_for(12, 10 * n + k))
         A = torch.from_numpy(A_h).cuda()
-        for prec in (0, 1, 2):
+        for prec in (0, 1, 2, 3):
             f = T.Factorization(A, precision=prec)
             Q = f.form_q()
             torch.cuda.synchronize()
