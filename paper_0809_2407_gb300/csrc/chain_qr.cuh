@@ -56,14 +56,14 @@ struct ChainScratch {
   typename Ar::E *red, *dvec, *wvec, *invs, *sc, *X;
 };
 
-// QR of [R; A_k] held in tile rows 0..NP-1 (R, strict lower part zero) and NP..NP+H-1 (A_k).
+// QR of [R; A_k] held in tile rows 0..NP-1 (R, strict lower part zero) and NP..NP+H-1 (A_k;
+// H = the leaf height of the default plan, or the padded height of a binary tree node).
 // Leaves R in rows 0..n-1, the scaled reflectors in rows NP.., tau in tau_s and T packed by
 // rows in T_s (tri_off).  All threads call.
-template <class Ar, int NP>
+template <class Ar, int NP, int H = ChainShape<NP>::H>
 __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename Ar::E* T_s,
                          const ChainScratch<Ar, NP>& w) {
   using E = typename Ar::E;
-  constexpr int H = ChainShape<NP>::H;
   constexpr int NB = H / 8;            // row blocks of the bottom part
   constexpr int G = kThreads / NP;     // row groups of the dot products
   constexpr int NBG = NB / G;          // blocks per group

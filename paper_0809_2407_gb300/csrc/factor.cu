@@ -63,6 +63,32 @@ __device__ inline void chain_step(const FactorSmem<typename Ar::E>& f, const Pla
   }
 }
 
+// A binary tree node (q <= 2 children) by the scheduled chain step: the second child's triangle
+// (zeros for a lone child) is the block under the first child's R, padded with zero rows to a
+// height the step's schedule takes (64 rows for np = 64 and 32, 128 for np = 16).  Rows that are
+// zero stay exactly zero under the reflectors, so the node's reflectors keep the structure of
+// eq. fact_2rs and the result equals the structured QR's.  False (nothing done) when the node
+// does not fit that form.
+template <class Ar>
+__device__ inline bool node_step(const FactorSmem<typename Ar::E>& f, const Plan& P, int q) {
+  using E = typename Ar::E;
+  const int np = P.np, n = P.n;
+  const int H = (np == 16) ? 128 : 64;
+  if (q > 2 || np < 16 || P.rows_cap < np + H) return false;
+  const int lnp = __ffs(np) - 1;
+  for (int i = threadIdx.x; i < (np + H - q * np) * np; i += kThreads)
+    at<E>(f.S, q * np + (i >> lnp), i & (np - 1)) = Ar::zero();
+  __syncthreads();
+  if (np == 64)
+    chain_qr<Ar, 64, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 64>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+  else if (np == 32)
+    chain_qr<Ar, 32, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 32>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+  else
+    chain_qr<Ar, 16, 128>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 16>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+  __syncthreads();
+  return true;
+}
+
 // Rows [r0, r0 + rows) of the tile arrive from TMA as FP64; in double-float mode they are split
 // into (hi, lo) pairs in place.
 template <class Ar>
@@ -165,7 +191,7 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
       for (int i = tid; i < np * np; i += kThreads) *S.ptr(s * np + (i >> lnp), (i & (np - 1))) = __ldcg(Rc + i);
     }
     __syncthreads();
-    stacked_qr<Ar>(S, NODE, q * np, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
+    if (!node_step<Ar>(f, P, q)) stacked_qr<Ar>(S, NODE, q * np, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
     E* Y = reinterpret_cast<E*>(st.node_y) + (size_t)tn * (P.arity - 1) * np * np;
     for (int s = 1; s < P.arity; ++s) {
       E* Ys = Y + (size_t)(s - 1) * np * np;
