@@ -299,7 +299,8 @@ cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain
 // 8 x 8 bf16 slice pairs on tcgen05 with exact FP32 accumulators in TMEM; C -= M in FP64.
 // The leaf's T arrives by a bulk copy and its reflector tile by TMA, both issued when the leaf
 // starts so that they overlap the T C product.  The first leaf of a chain (V unit lower
-// trapezoidal) takes the native FP64 route.  Needs np = 64 (33 <= n <= 64) and h <= 128.
+// trapezoidal) takes three passes: X = V_top^T C, M = T X, Q_rows = [C; 0] - V M.  Needs
+// np = 64 (33 <= n <= 64) and h <= 128.
 // 512 threads, one block per SM (all 512 TMEM columns).
 
 constexpr int kOzT = 512;
@@ -500,6 +501,18 @@ __device__ __forceinline__ double slot_val(double raw) {
   }
 }
 
+// Exponent and fixed-point form of a slot, straight from the pair's FP32 bits when kPairs.
+template <bool kPairs>
+__device__ __forceinline__ int slot_bexp(double raw) {
+  if constexpr (kPairs) return oz::bexp_pair(raw);
+  else return oz::bexp(raw);
+}
+template <bool kPairs>
+__device__ __forceinline__ uint64_t slot_fixed(double raw, int emax) {
+  if constexpr (kPairs) return oz::to_fixed_pair(raw, emax);
+  else return oz::to_fixed(raw, emax);
+}
+
 template <bool kPairs>
 __global__ void __launch_bounds__(kOzT, 1)
     formq_ozaki_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
@@ -560,13 +573,12 @@ __global__ void __launch_bounds__(kOzT, 1)
         }
       }
       long long* Tfix = reinterpret_cast<long long*>(z.M);
-      if constexpr (kPairs)
-        for (int idx = tid; idx < np * np; idx += kOzT) z.M[idx] = slot_val<true>(z.M[idx]);
       for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
       __syncthreads();
-      for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], oz::bexp(z.M[idx]));
+      for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], slot_bexp<kPairs>(z.M[idx]));
       __syncthreads();
-      for (int idx = tid; idx < np * np; idx += kOzT) Tfix[idx] = (long long)oz::to_fixed(z.M[idx], z.expA[idx >> 6]);
+      for (int idx = tid; idx < np * np; idx += kOzT)
+        Tfix[idx] = (long long)slot_fixed<kPairs>(z.M[idx], z.expA[idx >> 6]);
       __syncthreads();
       if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Tfix[r * 64 + k]; }, ph, st.status)) {
         alive = false;
@@ -590,19 +602,14 @@ __global__ void __launch_bounds__(kOzT, 1)
           break;
         }
       }
-      if constexpr (kPairs)
-        for (int idx = tid; idx < h * np; idx += kOzT) {
-          double* p = z.Y.ptr(idx >> 6, idx & 63);
-          *p = slot_val<true>(*p);
-        }
       for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
       __syncthreads();
       for (int idx = tid; idx < h * np; idx += kOzT)
-        warp_max_into(&z.expA[idx >> 6], oz::bexp(*z.Y.ptr(idx >> 6, idx & 63)));
+        warp_max_into(&z.expA[idx >> 6], slot_bexp<kPairs>(*z.Y.ptr(idx >> 6, idx & 63)));
       __syncthreads();
       for (int idx = tid; idx < h * np; idx += kOzT) {
         double* p = z.Y.ptr(idx >> 6, idx & 63);
-        *reinterpret_cast<uint64_t*>(p) = oz::to_fixed(*p, z.expA[idx >> 6]);
+        *reinterpret_cast<uint64_t*>(p) = slot_fixed<kPairs>(*p, z.expA[idx >> 6]);
       }
       __syncthreads();
       if (!ozaki_mma_pass(z, tmem, h, [&](int r, int k) { return *reinterpret_cast<const uint64_t*>(z.Y.ptr(r, k)); },
@@ -614,10 +621,8 @@ __global__ void __launch_bounds__(kOzT, 1)
         if (j < n) Q[(row0 + i) * ldq + j] = -v;
       });
     } else {
-      // ---- first leaf, native FP64: Q_rows = [C; 0] - V (T (V_top^T C))
-      double* T = reinterpret_cast<double*>(z.bsl);
-      double* X = T + np * np;
-      for (int i = tid; i < np * np; i += kOzT) T[i] = slot_val<kPairs>(__ldcg(Tg + i));
+      // ---- first leaf (V unit lower trapezoidal; the tile's rows 0..n-1 hold R above the
+      //      diagonal): Q_rows = [C; 0] - V (T (V_top^T C)) as three Ozaki passes
       if (!tile_load(z.Y, &mapV, z.bars, y_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
         alive = false;
         break;
@@ -629,37 +634,66 @@ __global__ void __launch_bounds__(kOzT, 1)
         }
         __syncthreads();
       }
-      for (int o = tid; o < np * np; o += kOzT) {
-        const int a = o / np, b = o % np;
-        double v = 0.0;
-        if (a < n) {
-          v = z.C[a * kOzLd + b];
-          for (int r = a + 1; r < n; ++r) v = fma(*z.Y.ptr(r, a), z.C[r * kOzLd + b], v);
-        }
-        X[a * np + b] = v;
+      // V's entry (r, a): 1 on the diagonal, the stored reflector below it, 0 above and past n
+      auto vval = [&](int r, int a) -> double {
+        return (a < n) ? (r > a ? *z.Y.ptr(r, a) : (r == a ? 1.0 : 0.0)) : 0.0;
+      };
+      long long* Afix = reinterpret_cast<long long*>(z.M);
+      // pass 1: X = V_top^T C; A = V_top^T (row a, k = r < n), B = C
+      ozaki_b_slices(z, [&](int j, int k) { return z.C[k * kOzLd + j]; });
+      ozaki_zero_a_rows(z, np, oz::kM);
+      for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
+      __syncthreads();
+      for (int idx = tid; idx < np * np; idx += kOzT) {
+        const int a = idx >> 6, r = idx & 63;
+        warp_max_into(&z.expA[a], oz::bexp(r < n ? vval(r, a) : 0.0));
       }
       __syncthreads();
-      for (int o = tid; o < np * np; o += kOzT) {  // M = T X, T upper triangular
-        const int a = o / np, b = o % np;
-        double v = 0.0;
-        for (int p = a; p < n; ++p) v = fma(T[a * np + p], X[p * np + b], v);
-        z.M[a * kOzLd + b] = v;
+      for (int idx = tid; idx < np * np; idx += kOzT) {
+        const int a = idx >> 6, r = idx & 63;
+        Afix[idx] = (long long)oz::to_fixed(r < n ? vval(r, a) : 0.0, z.expA[a]);
       }
       __syncthreads();
-      const int G = kOzT / np;
-      const int cown = tid & (np - 1), gown = tid / np;
-      if (cown < n) {
-        for (int r = gown; r < rows_valid; r += G) {
-          double acc = 0.0;
-          const int amax = (r < n) ? r : n;
-          for (int a = 0; a < amax; ++a) acc = fma(*z.Y.ptr(r, a), z.M[a * kOzLd + cown], acc);
-          if (r < n) acc += z.M[r * kOzLd + cown];
-          double v = -acc;
-          if (r < n) v += z.C[r * kOzLd + cown];
-          Q[(row0 + r) * ldq + cown] = v;
-        }
+      if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Afix[r * 64 + k]; }, ph, st.status)) {
+        alive = false;
+        break;
+      }
+      ozaki_epilogue(z, tmem, np, [&](int i, int j, double v) { z.M[i * kOzLd + j] = v; });  // X
+      // pass 2: M = T X; B = X, A = T
+      ozaki_b_slices(z, [&](int j, int k) { return z.M[k * kOzLd + j]; });
+      for (int i = tid; i < np * np; i += kOzT) z.M[i] = slot_val<kPairs>(__ldcg(Tg + i));
+      for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
+      __syncthreads();
+      for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], oz::bexp(z.M[idx]));
+      __syncthreads();
+      for (int idx = tid; idx < np * np; idx += kOzT) Afix[idx] = (long long)oz::to_fixed(z.M[idx], z.expA[idx >> 6]);
+      __syncthreads();
+      if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Afix[r * 64 + k]; }, ph, st.status)) {
+        alive = false;
+        break;
+      }
+      ozaki_epilogue(z, tmem, np, [&](int i, int j, double v) { z.M[i * kOzLd + j] = v; });  // M
+      // pass 3: Q_rows = [C; 0] - V M; B = M, A = V (rows of the leaf), in place in the tile
+      ozaki_b_slices(z, [&](int j, int k) { return z.M[k * kOzLd + j]; });
+      if (h < oz::kM) ozaki_zero_a_rows(z, h, oz::kM);
+      for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
+      __syncthreads();
+      for (int idx = tid; idx < h * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], oz::bexp(vval(idx >> 6, idx & 63)));
+      __syncthreads();
+      for (int idx = tid; idx < h * np; idx += kOzT) {
+        const int r = idx >> 6, a = idx & 63;
+        const double v = vval(r, a);  // reads only element (r, a), which it then replaces
+        *reinterpret_cast<uint64_t*>(z.Y.ptr(r, a)) = oz::to_fixed(v, z.expA[r]);
       }
       __syncthreads();
+      if (!ozaki_mma_pass(z, tmem, h, [&](int r, int k) { return *reinterpret_cast<const uint64_t*>(z.Y.ptr(r, k)); },
+                          ph, st.status)) {
+        alive = false;
+        break;
+      }
+      ozaki_epilogue(z, tmem, rows_valid, [&](int i, int j, double v) {
+        if (j < n) Q[(row0 + i) * ldq + j] = (i < n ? z.C[i * kOzLd + j] : 0.0) - v;
+      });
     }
   }
   // every pass waits for its commits; after a timeout, give the copies and MMAs in flight one

@@ -107,6 +107,30 @@ __device__ __forceinline__ uint64_t to_fixed(double v, int emax) {
     mag = (-d < 64) ? (m >> (-d)) : 0ull;
   return (b & 0x8000000000000000ull) | mag;
 }
+// The same for a double-float value (hi, lo) held in an 8-byte slot (hi in the low word), with
+// integer operations only.  bexp_pair: hi's exponent in the FP64 bias (0 for zero or an FP32
+// subnormal hi), an upper bound of the pair's (|lo| <= ulp(hi)/2 keeps hi + lo inside hi's
+// binade or just below it).  to_fixed_pair: hi and lo each in fixed point against emax, summed
+// (each term truncated, one unit of the fixed grid more than a single truncation).
+__device__ __forceinline__ int bexp_pair(double raw) {
+  const uint32_t hb = (uint32_t)(unsigned long long)__double_as_longlong(raw);
+  const int E = (int)((hb >> 23) & 0xFF);
+  return E == 0 ? 0 : E + (1023 - 127);
+}
+__device__ __forceinline__ long long fixed_f32(uint32_t b, int emax) {
+  const int E = (int)((b >> 23) & 0xFF);
+  if (E == 0) return 0;
+  const uint64_t m = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);  // |f| = m 2^(E - 150)
+  const int sh = E - emax + 928;                               // 2^(1078 - emax) scaling: <= 32
+  const uint64_t mag = (sh >= 0) ? (m << sh) : ((-sh < 64) ? (m >> (-sh)) : 0ull);
+  return (b & 0x80000000u) ? -(long long)mag : (long long)mag;
+}
+__device__ __forceinline__ uint64_t to_fixed_pair(double raw, int emax) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(raw);
+  const long long v = fixed_f32((uint32_t)u, emax) + fixed_f32((uint32_t)(u >> 32), emax);
+  return v < 0 ? (0x8000000000000000ull | (uint64_t)(-v)) : (uint64_t)v;
+}
+
 // bf16 bits of slice s (1-based) of a fixed-point value: sign * ((mag >> (56 - 7 s)) & 127).
 __device__ __forceinline__ uint32_t slice_bf16(uint64_t fx, int s) {
   const uint32_t c = (uint32_t)(fx >> (56 - 7 * s)) & 127u;
