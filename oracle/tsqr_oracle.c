@@ -138,14 +138,24 @@ void oracle_qr(int64_t m, int64_t n, const double* A, int64_t lda, double* V, do
 /* ||A - Q R||_F / ||A||_F for A, Q (m x n) and upper triangular R (n x n). */
 double oracle_backward_error(int64_t m, int64_t n, const double* A, int64_t lda, const double* Q,
                              int64_t ldq, const double* R, int64_t ldr) {
+  /* Both Frobenius norms are taken relative to the largest |A_ic|, so that neither underflows
+   * for tiny A nor overflows for huge A; the ratio is the same. */
+  double amax = 0.0;
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t c = 0; c < n; ++c) {
+      double a = fabs(A[i * lda + c]);
+      if (a > amax || a != a) amax = a;
+    }
+  const double scale = (amax > 0.0) ? 1.0 / amax : 1.0;
   double num = 0.0, den = 0.0;
   for (int64_t i = 0; i < m; ++i) {
     for (int64_t c = 0; c < n; ++c) {
       double s = 0.0;
-      for (int64_t p = 0; p <= c; ++p) s += Q[i * ldq + p] * R[p * ldr + c];
-      double d = A[i * lda + c] - s;
+      for (int64_t p = 0; p <= c; ++p) s += Q[i * ldq + p] * (R[p * ldr + c] * scale);
+      double a = A[i * lda + c] * scale;
+      double d = a - s;
       num += d * d;
-      den += A[i * lda + c] * A[i * lda + c];
+      den += a * a;
     }
   }
   return den > 0.0 ? sqrt(num / den) : sqrt(num);

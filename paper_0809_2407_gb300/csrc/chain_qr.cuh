@@ -9,9 +9,9 @@
 //   * look-ahead: while warps 1..7 apply reflector j to columns j+2.., warp 0 applies it to
 //     column j+1 and builds reflector j+1, so the serial norm/sqrt/division work overlaps the
 //     trailing update (three barriers per column instead of five);
-//   * the reflector column is left unscaled (x instead of v = x/(alpha-beta)) while the leaf
-//     is factored; products with it carry the factor inv_j = 1/(alpha-beta) instead, and the
-//     whole leaf is scaled once at the end;
+//   * warp 0 scales the new reflector column to v = x/(alpha-beta) right after building it,
+//     inside the look-ahead, so the dot products and the Gram entries need no extra factors
+//     (and no product of two tiny entries can underflow);
 //   * T is assembled after the leaf from the Gram entries g_pj = v_p^T v_j by the blocked
 //     Schreiber-Van Loan merge T = [T1, -T1 G12 T2; 0, T2], in parallel, instead of a
 //     column recurrence on the critical path of every reflector.
@@ -75,8 +75,20 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
   char* const bottom = S.base + (size_t)NP * 128;  // row NP starts block 0
   E* sc = w.sc;
 
+  // warp 0: v_c = x_c inv_c over the bottom rows, once reflector c is built
+  auto scale_column = [&](int c) {
+    __syncwarp();
+    const E s = w.invs[c];
+    for (int r = NP + lane; r < NP + H; r += 32) {
+      E& x = at<E>(S, r, c);
+      x = Ar::mul(x, s);
+    }
+  };
   // reflector of column 0 before the loop
-  if (warp == 0) chain_reflector<Ar>(S, NP, H, 0, sc, w.invs);
+  if (warp == 0) {
+    chain_reflector<Ar>(S, NP, H, 0, sc, w.invs);
+    scale_column(0);
+  }
   for (int j = tid + n; j < NP; j += kThreads) tau_s[j] = Ar::zero();
   __syncthreads();
 
@@ -87,12 +99,11 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
 
   for (int j = 0; j < n; ++j) {
     const E tau = sc[1];
-    const E inv = sc[2];
     const bool active = !Ar::is_zero(sc[3]);
     if (tid == j) tau_s[j] = tau;
     if (tid == j) T_s[tri_off(j, NP)] = tau;
     if (active) {
-      // ---- A: D_c = sum_r x_r a_rc over the bottom rows, every column c != j
+      // ---- A: D_c = sum_r v_r a_rc over the bottom rows, every column c != j
       uint32_t oj[8];
       block_offsets(rc, j, oj);
       if (cown < n && cown != j) {
@@ -117,25 +128,26 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
           w.red[gown * NP + cown] = Ar::add(Ar::add(acc[0], acc[1]), Ar::add(acc[2], acc[3]));
       }
       __syncthreads();
-      // ---- B: d_c = S(j,c) + inv D_c (c > j): pivot-row update and the update weight;
-      //         g_cj = inv_c inv D_c (c < j): Gram entries for T
+      // ---- B: d_c = S(j,c) + D_c (c > j): pivot-row update and the update weight tau d_c;
+      //         g_cj = D_c = v_c^T v_j (c < j): Gram entries for T (the top parts e_c, e_j are
+      //         orthogonal)
       if (tid < n && tid != j) {
         E D = w.red[tid];
 #pragma unroll
         for (int g = 1; g < G; ++g) D = Ar::add(D, w.red[g * NP + tid]);
         if (tid > j) {
           E& pr = at<E>(S, j, tid);
-          const E d = Ar::add(pr, Ar::mul(inv, D));
+          const E d = Ar::add(pr, D);
           pr = Ar::axpy(pr, tau, d);
-          w.wvec[tid] = Ar::mul(Ar::mul(tau, d), inv);  // weight on the unscaled x
+          w.wvec[tid] = Ar::mul(tau, d);
         } else {
-          T_s[tri_off(tid, NP) + (j - tid)] = Ar::mul(Ar::mul(w.invs[tid], inv), D);
+          T_s[tri_off(tid, NP) + (j - tid)] = D;
         }
       }
       if (tid == 0) at<E>(S, j, j) = sc[0];
       __syncthreads();
-      // ---- C: trailing update a_rc -= w_c x_r; warp 0 takes column j+1 and then builds
-      //         reflector j+1, warps 1..7 take columns j+2..n-1
+      // ---- C: trailing update a_rc -= w_c v_r; warp 0 takes column j+1 and then builds and
+      //         scales reflector j+1, warps 1..7 take columns j+2..n-1
       if (warp == 0) {
         if (j + 1 < n) {
           const int c = j + 1;
@@ -146,6 +158,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
           }
           __syncwarp();
           chain_reflector<Ar>(S, NP, H, j + 1, sc, w.invs);
+          scale_column(j + 1);
         }
       } else {
         const int ac = n - j - 2;
@@ -173,27 +186,14 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
     } else {
       // H_j = I: no update; Gram entries with column j are zero; build reflector j+1
       if (tid < j) T_s[tri_off(tid, NP) + (j - tid)] = Ar::zero();
-      if (warp == 0 && j + 1 < n) chain_reflector<Ar>(S, NP, H, j + 1, sc, w.invs);
+      if (warp == 0 && j + 1 < n) {
+        chain_reflector<Ar>(S, NP, H, j + 1, sc, w.invs);
+        scale_column(j + 1);
+      }
       __syncthreads();
     }
   }
 
-  // ---- scale the reflector columns: v = x * inv_c.  The two loop forms do the same work; on
-  // GB300 the FP64 kernel measured 1.6 % faster with the flat loop, the FP32-pipe policies
-  // faster with the column-owner loop that needs no division.
-  if constexpr (Ar::kPrecision == 0) {
-    for (int i = tid; i < H * n; i += kThreads) {
-      const int r = NP + i / n, c = i % n;
-      E& x = at<E>(S, r, c);
-      x = Ar::mul(x, w.invs[c]);
-    }
-  } else if (cown < n) {
-    const E ic = w.invs[cown];
-    for (int r = NP + gown; r < NP + H; r += G) {
-      E& x = at<E>(S, r, cown);
-      x = Ar::mul(x, ic);
-    }
-  }
   // ---- T from the Gram entries by blocked merges (sizes b = 2^lb = 1, 2, 4, ... NP/2)
   for (int b = 1, lb = 0; b < n; b <<= 1, ++lb) {
     const int pairs = (n + 2 * b - 1) >> (lb + 1);

@@ -41,23 +41,27 @@ template <class Ar>
 __device__ inline void reflector_warp(const Tile& S, int kind, int N, int np, int j, typename Ar::E* sc);
 
 // Native FP64: ||x|| from the plain sum of squares unless that sum leaves [2^-900, 2^900], in
-// which case every entry is rescaled by the largest magnitude first.
+// which case every entry is rescaled by the largest magnitude first.  Whether H = I is decided
+// from the entries themselves, not from their sum of squares, which underflows to zero for
+// entries below about 2^-537.
 template <>
 __device__ inline void reflector_warp<ArithF64>(const Tile& S, int kind, int N, int np, int j, double* sc) {
   const int lane = threadIdx.x & 31;
   {
     const int r_lo = first_row(kind, j, np);
     double ss = 0.0;
+    bool nz = false;  // some entry below the pivot is nonzero (its square may underflow)
     for (int r = r_lo + lane; r < N; r += 32) {
       if (skip_row(kind, r, j, np)) continue;
       const double x = at<double>(S, r, j);
       ss = fma(x, x, ss);
+      nz = nz || ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     const double alpha = at<double>(S, j, j);
     double beta = alpha, tau = 0.0, inv = 0.0;
-    const bool active = !(ss == 0.0);
+    const bool active = __any_sync(0xffffffffu, nz);
     if (active) {
       const double full = fma(alpha, alpha, ss);
       double nrm;

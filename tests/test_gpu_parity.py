@@ -565,3 +565,60 @@ def test_precision_forms_conditioning(T, n):
         orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device="cuda") - Q.T @ Q).item()
         assert be <= TOL_F32 and orth <= TOL_F32, (k, "f32", be, orth)
         f.close()
+
+
+@pytest.mark.parametrize("kind", ["zero_matrix", "zero_first_last", "zero_middle", "duplicate_columns"])
+def test_degenerate_inputs(T, kind, prec):
+    """Degenerate cases of the method: H = I reflectors (tau = 0) everywhere or in some columns,
+    and exact rank deficiency.  Householder QR stays backward stable and Q orthonormal.  R is
+    compared with the oracle where it is unique: a zero first column leaves q_0 = e_0 in both
+    (their first reflector is the identity), a zero last column has nothing to its right.  After
+    a zero middle column j, q_j and row j of R depend on the reflectors before it, which differ
+    between the tree and the oracle, so only the invariants are checked there."""
+    m, n = 5000, 40
+    A_h = inputs.gaussian(m, n, inputs.seed_for(14, n))
+    if kind == "zero_matrix":
+        A_h[:] = 0.0
+    elif kind == "zero_first_last":
+        A_h[:, [0, 39]] = 0.0
+    elif kind == "zero_middle":
+        A_h[:, 7] = 0.0
+    else:
+        A_h[:, 5] = A_h[:, 3]
+        A_h[:, 20] = 2.0 * A_h[:, 11]
+    f, R, Q = run(T, A_h, leaf_h=128, chain=3, precision=prec)
+    assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) >= 0.0)
+    assert oracle.orthogonality(Q) <= TOL_ORTH
+    if kind == "zero_matrix":
+        assert np.all(R == 0.0)
+        assert np.array_equal(Q[:n], np.eye(n)) and np.all(Q[n:] == 0.0)  # Q = [I; 0], the oracle's
+    else:
+        assert np.linalg.norm(A_h - Q @ R) <= TOL_BACK * np.linalg.norm(A_h)
+    if kind == "zero_first_last":
+        ref = oracle.qr(A_h)
+        assert np.abs(R - ref["R"]).max() <= 1e-10 * np.abs(ref["R"]).max()
+        assert R[0, 0] == 0.0 and R[39, 39] == 0.0
+
+
+@pytest.mark.parametrize("scale_exp", [-600, -90, 90, 600])
+def test_extreme_scaling(T, scale_exp, prec):
+    """Entries near the ends of the exponent range: the FP64 norms rescale by the largest
+    magnitude; double-float (modes 1 and 3) keeps full accuracy within about [2^-100, 2^100]
+    (its FP32 exponent range), so it is held to that range only."""
+    if prec in (1, 3) and abs(scale_exp) > 100:
+        pytest.skip("outside the double-float range the header states")
+    A_h = inputs.gaussian(3000, 24, inputs.seed_for(15, abs(scale_exp))) * 2.0 ** scale_exp
+    f, R, Q = run(T, A_h, leaf_h=128, precision=prec)
+    assert oracle.backward_error(A_h, Q, R) <= TOL_BACK
+    assert oracle.orthogonality(Q) <= TOL_ORTH
+    ref = oracle.qr(A_h)
+    s = 2.0 ** -scale_exp  # exact rescaling, so the norms below neither underflow nor overflow
+    assert np.linalg.norm((R - ref["R"]) * s) / np.linalg.norm(ref["R"] * s) <= TOL_R
+
+
+def test_nan_propagates_without_fault(T):
+    """NaN in A propagates to R (no check, no trap); the device status word stays clear."""
+    A_h = inputs.gaussian(2000, 16, 99)
+    A_h[1234, 5] = np.nan
+    f, R, Q = run(T, A_h, leaf_h=128)
+    assert np.isnan(R).any()

@@ -158,6 +158,22 @@ def test_zero_column_gives_identity_reflector(oracle_mod):
     assert np.all(f["R"][:, 3] == 0.0)
 
 
+@pytest.mark.parametrize("k", [-600, 600])
+def test_power_of_two_scaling_is_exact(oracle_mod, k):
+    """QR commutes with scaling by 2^k: every step (max-scaled norms, beta, tau, v, the
+    reflections) scales exactly when nothing over- or underflows, so R(2^k A) = 2^k R(A) and
+    Q(2^k A) = Q(A) bitwise; the backward error, a ratio of norms, is unchanged.  At k = -600 the
+    entries' squares underflow, so an unscaled norm or sum of squares would fail this."""
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((300, 12))
+    f = oracle_mod.qr(A)
+    g = oracle_mod.qr(A * 2.0 ** k)
+    assert np.array_equal(g["R"], f["R"] * 2.0 ** k)
+    assert np.array_equal(g["Q"], f["Q"])
+    assert oracle_mod.backward_error(A * 2.0 ** k, g["Q"], g["R"]) == oracle_mod.backward_error(A, f["Q"], f["R"])
+    assert oracle_mod.backward_error(A * 2.0 ** k, g["Q"], g["R"]) <= 10 * 12 * EPS
+
+
 def test_zero_padding_is_exact(oracle_mod):
     A = inputs.gaussian(100, 8, 9)
     f1 = oracle_mod.qr(A)
