@@ -653,6 +653,34 @@ def main():
     if not args.no_batched and world == 1:
         batched = run_batched(tsqr, torch, dev, stream, sptr, args)
 
+    # R alone (the paper times R alone and Q with R apart): no reflectors, T or tree factors
+    r_alone = None
+    if not args.no_forms and world == 1:
+        r_alone = {"flops": "2mn^2 - 2n^3/3 per factorization"}
+        for nm, prec, f32 in (("fp64", 0, False), ("double_float", 1, False), ("fp32", 0, True)):
+            X = A.float() if f32 else A
+            Rx = torch.empty((n, n), dtype=X.dtype, device=dev)
+            o = tsqr.Opts(precision=prec, r_only=1)
+            code = tsqr.TSQR_F32 if f32 else tsqr.TSQR_F64
+            nb = tsqr.tsqr_workspace_size(code, m, n, o)
+            wk = torch.empty(nb, dtype=torch.uint8, device=dev)
+            ts = []
+            for it in range(1 + max(2, min(args.steps, 5))):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h = tsqr.tsqr_factor(code, tsqr.TSQR_ROW_MAJOR, m, n, X.data_ptr(), n, Rx.data_ptr(), n,
+                                     wk.data_ptr(), nb, o, sptr)
+                e1.record(stream)
+                tsqr.tsqr_destroy(h)
+                torch.cuda.synchronize()
+                if it:
+                    ts.append(e0.elapsed_time(e1))
+            t = statistics.mean(ts)
+            r_alone[nm] = {"factor_ms": t, "value": fl["factor"] / (t / 1e3) / 1e9, "unit": "GFLOP/s",
+                           "workspace_bytes": nb}
+            del X, Rx, wk
+        torch.cuda.empty_cache()
+
     # context, not a target: the vendor library's QR of the same matrix (torch.linalg.qr, cuSOLVER)
     library = None
     if not args.no_forms and world == 1:
@@ -699,7 +727,8 @@ def main():
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
                "roofline": roofline, "precision_forms": forms, "batched": batched, "shapes": shapes,
-               "autograd": autograd, "library_context": library, "cpu_baseline": cpu, "e2e": e2e,
+               "autograd": autograd, "r_alone": r_alone, "library_context": library, "cpu_baseline": cpu,
+               "e2e": e2e,
                "gpu_launches": main_mode["launches"] * args.steps, "clocks": clocks}
         print(json.dumps(out), flush=True)
     if dist:

@@ -83,6 +83,11 @@ typedef struct {
                         Batches run mode 2 as 0 and mode 3 as 1. */
   int32_t inplace;   /* nonzero: the leaf reflectors overwrite A (Sec. 4.2 storage) and A's
                         upper triangles hold intermediate R factors; zero: A is read only */
+  int32_t r_only;    /* nonzero: compute R alone (the paper times R alone and Q with R apart,
+                        Sec. 7): no reflectors, T or tree factors are stored or built, A is
+                        read once and nothing else is written but R.  The handle then keeps no
+                        Q: tsqr_apply_qt, tsqr_apply_q, tsqr_form_q and tsqr_backward return
+                        TSQR_ERR_INVALID_ARG.  Not with inplace, n > 64 or a batch. */
 } tsqr_opts_t;
 
 /* Plan and storage of a factorization, for inspection and tests.  The pointers are device

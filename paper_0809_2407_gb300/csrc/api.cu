@@ -107,6 +107,7 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P, boo
   if (f32 && o->precision != 0)
     return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 runs FP32 arithmetic: precision must be 0");
   if (f32 && o->inplace) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 keeps A read-only (inplace is not supported)");
+  if (o->r_only && o->inplace) return fail(TSQR_ERR_INVALID_ARG, "r_only stores no reflectors: inplace does not apply");
   const int arity = o->arity ? o->arity : 2;
   if (arity < 2 || arity > tsqr::kMaxArity) return fail(TSQR_ERR_INVALID_ARG, "arity must be in 2..8");
   int h = o->leaf_h ? o->leaf_h : default_leaf_h(np);
@@ -120,6 +121,7 @@ tsqr_status_t make_plan(int64_t m, int64_t n, const tsqr_opts_t* o, Plan* P, boo
   P->h = h;
   P->arity = arity;
   P->precision = f32 ? tsqr::kPrecF32 : o->precision;
+  P->r_only = o->r_only ? 1 : 0;
   P->leaves = (m + h - 1) / h;
   int64_t chain = o->chain;
   if (chain == 0) {
@@ -181,13 +183,14 @@ Layout make_layout(const Plan& P, bool inplace) {
     off = align256(off + bytes);
     return at;
   };
+  const size_t q = P.r_only ? 0 : 1;  // R alone keeps no reflectors, tau or T (V only stages A)
   L.v = take(inplace ? 0 : (size_t)P.m * L.ldv * 8);
-  L.tau_leaf = take((size_t)P.leaves * np * 8);
-  L.t_leaf = take((size_t)P.leaves * np2 * 8);
+  L.tau_leaf = take(q * (size_t)P.leaves * np * 8);
+  L.t_leaf = take(q * (size_t)P.leaves * np2 * 8);
   L.node_r = take((size_t)P.total_nodes * np2 * 8);
-  L.node_y = take((size_t)P.tree_nodes * (P.arity - 1) * np2 * 8);
-  L.node_tau = take((size_t)P.tree_nodes * np * 8);
-  L.node_t = take((size_t)P.tree_nodes * np2 * 8);
+  L.node_y = take(q * (size_t)P.tree_nodes * (P.arity - 1) * np2 * 8);
+  L.node_tau = take(q * (size_t)P.tree_nodes * np * 8);
+  L.node_t = take(q * (size_t)P.tree_nodes * np2 * 8);
   L.signs = take(np * 8);
   L.counters = take((size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1) * tsqr::kMaxColBlocks * sizeof(int));
   L.status = take(256);
@@ -255,6 +258,7 @@ tsqr_opts_t panel_opts(const tsqr_opts_t* o) {
 // workspace (the FP32 factorization widens its input into it).
 tsqr_status_t make_panel_layout(int64_t m, int64_t n, const tsqr_opts_t* o, PanelLayout* L, bool f32 = false) {
   if (n > kMaxN) return fail(TSQR_ERR_UNSUPPORTED, "n > 4096 is not supported");
+  if (o && o->r_only) return fail(TSQR_ERR_UNSUPPORTED, "r_only needs n <= 64 (the panels' updates need Q)");
   if (f32 && o && o->inplace) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 keeps A read-only (inplace is not supported)");
   const bool inplace = o && o->inplace;
   L->count = (int)((n + kPanel - 1) / kPanel);
@@ -476,6 +480,7 @@ tsqr_status_t tsqr_form_q(tsqr_handle_t h, void* dQ, int64_t ldq, tsqr_stream_t 
     return TSQR_OK;
   }
   if (!dQ || ldq < h->P.n) return fail(TSQR_ERR_INVALID_ARG, "Q must be non-NULL with ldq >= n");
+  if (h->P.r_only) return fail(TSQR_ERR_INVALID_ARG, "the factorization computed R alone (r_only): no Q");
   cudaError_t e = tsqr::launch_form_q(h->mapV, h->P, h->st, dQ, ldq, h->box_rows,
                                       static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "form_q launch");
@@ -496,6 +501,7 @@ tsqr_status_t tsqr_apply_qt(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, t
     }
     return TSQR_OK;
   }
+  if (h->P.r_only) return fail(TSQR_ERR_INVALID_ARG, "the factorization computed R alone (r_only): no Q");
   cudaError_t e = tsqr::launch_apply_qt(h->mapV, h->P, h->st, k, dB, ldb, h->box_rows,
                                         static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "apply_qt launch");
@@ -516,6 +522,7 @@ tsqr_status_t tsqr_apply_q(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, ts
     }
     return TSQR_OK;
   }
+  if (h->P.r_only) return fail(TSQR_ERR_INVALID_ARG, "the factorization computed R alone (r_only): no Q");
   cudaError_t e = tsqr::launch_apply_q(h->mapV, h->P, h->st, k, dB, ldb, h->box_rows,
                                        static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "apply_q launch");
@@ -601,6 +608,7 @@ tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n,
   tsqr_opts_t base{};
   if (opts) base = *opts;
   if (base.inplace) return fail(TSQR_ERR_UNSUPPORTED, "batches keep A read-only (inplace is not supported)");
+  if (base.r_only) return fail(TSQR_ERR_UNSUPPORTED, "batches keep Q (r_only is not supported)");
   // the batched thin Q runs on the FP64-pipe or FP32-pipe kernels: the Ozaki forms run as their
   // factorization's arithmetic
   if (base.precision == tsqr::kPrecOzaki) base.precision = tsqr::kPrecF64;

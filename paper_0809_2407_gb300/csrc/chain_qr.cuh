@@ -58,11 +58,12 @@ struct ChainScratch {
 
 // QR of [R; A_k] held in tile rows 0..NP-1 (R, strict lower part zero) and NP..NP+H-1 (A_k;
 // H = the leaf height of the default plan, or the padded height of a binary tree node).
-// Leaves R in rows 0..n-1, the scaled reflectors in rows NP.., tau in tau_s and T packed by
-// rows in T_s (tri_off).  All threads call.
+// Leaves R in rows 0..n-1, the scaled reflectors in rows NP.., tau in tau_s and, with want_t,
+// T packed by rows in T_s (tri_off); without it the Gram entries and the merge are skipped (R
+// alone).  All threads call.
 template <class Ar, int NP, int H = ChainShape<NP>::H>
 __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename Ar::E* T_s,
-                         const ChainScratch<Ar, NP>& w) {
+                         const ChainScratch<Ar, NP>& w, bool want_t = true) {
   using E = typename Ar::E;
   constexpr int NB = H / 8;            // row blocks of the bottom part
   constexpr int G = kThreads / NP;     // row groups of the dot products
@@ -101,12 +102,12 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
     const E tau = sc[1];
     const bool active = !Ar::is_zero(sc[3]);
     if (tid == j) tau_s[j] = tau;
-    if (tid == j) T_s[tri_off(j, NP)] = tau;
+    if (want_t && tid == j) T_s[tri_off(j, NP)] = tau;
     if (active) {
       // ---- A: D_c = sum_r v_r a_rc over the bottom rows, every column c != j
       uint32_t oj[8];
       block_offsets(rc, j, oj);
-      if (cown < n && cown != j) {
+      if (cown < n && cown != j && (want_t || cown > j)) {
         // four independent partial sums so consecutive multiply-adds do not wait on each other
         // on the FP32 pipe; FP64 keeps one: its pipe, not the latency, bounds the dots, and the
         // three adds that join four sums are FP64 instructions too
@@ -140,7 +141,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
           const E d = Ar::add(pr, D);
           pr = Ar::axpy(pr, tau, d);
           w.wvec[tid] = Ar::mul(tau, d);
-        } else {
+        } else if (want_t) {
           T_s[tri_off(tid, NP) + (j - tid)] = D;
         }
       }
@@ -185,7 +186,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
       __syncthreads();
     } else {
       // H_j = I: no update; Gram entries with column j are zero; build reflector j+1
-      if (tid < j) T_s[tri_off(tid, NP) + (j - tid)] = Ar::zero();
+      if (want_t && tid < j) T_s[tri_off(tid, NP) + (j - tid)] = Ar::zero();
       if (warp == 0 && j + 1 < n) {
         chain_reflector<Ar>(S, NP, H, j + 1, sc, w.invs);
         scale_column(j + 1);
@@ -195,7 +196,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
   }
 
   // ---- T from the Gram entries by blocked merges (sizes b = 2^lb = 1, 2, 4, ... NP/2)
-  for (int b = 1, lb = 0; b < n; b <<= 1, ++lb) {
+  for (int b = 1, lb = 0; want_t && b < n; b <<= 1, ++lb) {
     const int pairs = (n + 2 * b - 1) >> (lb + 1);
     // X = G12 * T2 for every pair (G12 at rows blk1, cols blk2 of T_s; T2 upper).  The row i
     // varies fastest across the lanes so that the loop length (q + 1) is the same in a warp.

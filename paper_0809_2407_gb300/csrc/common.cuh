@@ -41,7 +41,8 @@ struct Plan {
   int level_offset[kMaxLevels + 1];
   int total_nodes, tree_nodes;
   int rows_cap;   // rows of the factor kernel's shared tile
-  int precision;  // 0: native FP64 arithmetic; 1: double-float (FP32 pairs), FP64 in and out
+  int precision;  // kPrec* below: the arithmetic of the factorization
+  int r_only;     // nonzero: R alone; no reflectors, T or tree factors are kept
 };
 
 __host__ __device__ inline int64_t chain_first_leaf(const Plan& p, int g) { return (int64_t)g * p.chain; }

@@ -52,14 +52,15 @@ size_t factor_smem_bytes(const Plan& P) {
 template <class Ar>
 __device__ inline void chain_step(const FactorSmem<typename Ar::E>& f, const Plan& P) {
   const int np = P.np, n = P.n, h = P.h;
+  const bool want_t = !P.r_only;
   if (np == 64 && h == ChainShape<64>::H) {
-    chain_qr<Ar, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 64>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+    chain_qr<Ar, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 64>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X}, want_t);
   } else if (np == 32 && h == ChainShape<32>::H) {
-    chain_qr<Ar, 32>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 32>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+    chain_qr<Ar, 32>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 32>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X}, want_t);
   } else if (np == 16 && h == ChainShape<16>::H) {
-    chain_qr<Ar, 16>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 16>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+    chain_qr<Ar, 16>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 16>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X}, want_t);
   } else {
-    stacked_qr<Ar>(f.S, CHAIN, np + h, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
+    stacked_qr<Ar>(f.S, CHAIN, np + h, np, n, f.tau_s, want_t ? f.T_s : nullptr, f.red, f.dvec, f.sc);
   }
 }
 
@@ -79,12 +80,16 @@ __device__ inline bool node_step(const FactorSmem<typename Ar::E>& f, const Plan
   for (int i = threadIdx.x; i < (np + H - q * np) * np; i += kThreads)
     at<E>(f.S, q * np + (i >> lnp), i & (np - 1)) = Ar::zero();
   __syncthreads();
+  const bool want_t = !P.r_only;
   if (np == 64)
-    chain_qr<Ar, 64, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 64>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+    chain_qr<Ar, 64, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 64>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X},
+                         want_t);
   else if (np == 32)
-    chain_qr<Ar, 32, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 32>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+    chain_qr<Ar, 32, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 32>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X},
+                         want_t);
   else
-    chain_qr<Ar, 16, 128>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 16>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X});
+    chain_qr<Ar, 16, 128>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 16>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X},
+                          want_t);
   __syncthreads();
   return true;
 }
@@ -137,18 +142,22 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
     }
     convert_rows_in<Ar>(S, dst, h, np);
     if (plain)
-      stacked_qr<Ar>(S, PLAIN, h, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
+      stacked_qr<Ar>(S, PLAIN, h, np, n, f.tau_s, P.r_only ? nullptr : f.T_s, f.red, f.dvec, f.sc);
     else
       chain_step<Ar>(f, P);
-    tile_store(S, mapV_p, np, row0, h, dst, box_rows);
-    E* tau_g = tau_leaf + leaf * np;
-    E* T_g = t_leaf + leaf * np * np;
-    for (int i = tid; i < np; i += kThreads) tau_g[i] = f.tau_s[i];
-    for (int i = tid; i < np * np; i += kThreads) {
-      const int a = (i >> lnp), b = (i & (np - 1));
-      T_g[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
+    if (!P.r_only) {  // the leaf's reflectors, tau and T: the reified tree (Sec. 4.1)
+      tile_store(S, mapV_p, np, row0, h, dst, box_rows);
+      E* tau_g = tau_leaf + leaf * np;
+      E* T_g = t_leaf + leaf * np * np;
+      for (int i = tid; i < np; i += kThreads) tau_g[i] = f.tau_s[i];
+      for (int i = tid; i < np * np; i += kThreads) {
+        const int a = (i >> lnp), b = (i & (np - 1));
+        T_g[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
+      }
+      tile_store_drain();
+    } else {
+      __syncthreads();
     }
-    tile_store_drain();
     if (plain) {  // rows 0..np-1 now carry R above the diagonal; clear the reflector part below
       for (int i = tid; i < np * np; i += kThreads) {
         const int r = (i >> lnp), c = (i & (np - 1));
@@ -191,20 +200,23 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
       for (int i = tid; i < np * np; i += kThreads) *S.ptr(s * np + (i >> lnp), (i & (np - 1))) = __ldcg(Rc + i);
     }
     __syncthreads();
-    if (!node_step<Ar>(f, P, q)) stacked_qr<Ar>(S, NODE, q * np, np, n, f.tau_s, f.T_s, f.red, f.dvec, f.sc);
-    E* Y = reinterpret_cast<E*>(st.node_y) + (size_t)tn * (P.arity - 1) * np * np;
-    for (int s = 1; s < P.arity; ++s) {
-      E* Ys = Y + (size_t)(s - 1) * np * np;
-      for (int i = tid; i < np * np; i += kThreads) {
-        const int r = (i >> lnp), c = (i & (np - 1));
-        Ys[i] = (s < q && c >= r) ? at<E>(S, s * np + r, c) : Ar::zero();
+    if (!node_step<Ar>(f, P, q))
+      stacked_qr<Ar>(S, NODE, q * np, np, n, f.tau_s, P.r_only ? nullptr : f.T_s, f.red, f.dvec, f.sc);
+    if (!P.r_only) {  // the node's reflectors (eq. fact_2rs), tau and T
+      E* Y = reinterpret_cast<E*>(st.node_y) + (size_t)tn * (P.arity - 1) * np * np;
+      for (int s = 1; s < P.arity; ++s) {
+        E* Ys = Y + (size_t)(s - 1) * np * np;
+        for (int i = tid; i < np * np; i += kThreads) {
+          const int r = (i >> lnp), c = (i & (np - 1));
+          Ys[i] = (s < q && c >= r) ? at<E>(S, s * np + r, c) : Ar::zero();
+        }
       }
-    }
-    for (int i = tid; i < np; i += kThreads) reinterpret_cast<E*>(st.node_tau)[(size_t)tn * np + i] = f.tau_s[i];
-    E* Tn = reinterpret_cast<E*>(st.node_t) + (size_t)tn * np * np;
-    for (int i = tid; i < np * np; i += kThreads) {
-      const int a = (i >> lnp), b = (i & (np - 1));
-      Tn[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
+      for (int i = tid; i < np; i += kThreads) reinterpret_cast<E*>(st.node_tau)[(size_t)tn * np + i] = f.tau_s[i];
+      E* Tn = reinterpret_cast<E*>(st.node_t) + (size_t)tn * np * np;
+      for (int i = tid; i < np * np; i += kThreads) {
+        const int a = (i >> lnp), b = (i & (np - 1));
+        Tn[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
+      }
     }
     E* Rp = node_r + (size_t)pid * np * np;
     for (int i = tid; i < np * np; i += kThreads) {

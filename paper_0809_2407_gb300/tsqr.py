@@ -28,7 +28,7 @@ EXPORTED = ("tsqr_workspace_size", "tsqr_factor", "tsqr_apply_qt", "tsqr_apply_q
 
 class Opts(ctypes.Structure):
     _fields_ = [("leaf_h", ctypes.c_int32), ("chain", ctypes.c_int32), ("arity", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("inplace", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("inplace", ctypes.c_int32), ("r_only", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -219,12 +219,13 @@ class Factorization:
     the handle.  A float32 A selects TSQR_F32 (FP32 storage and arithmetic); R, Q and the
     matrices given to apply_qt / apply_q then are float32 too.
 
-    ``inplace=True`` lets the reflectors overwrite A (A must then stay alive; float64 only).
-    Options: leaf_h, chain, arity, precision (0 native FP64, 1 double-float, 2 Ozaki WY products;
-    see tsqr_opts_t).
+    ``inplace=True`` lets the reflectors overwrite A (A must then stay alive; float64 only);
+    ``r_only=True`` computes R alone and keeps no Q.  Options: leaf_h, chain, arity, precision
+    (0 native FP64, 1 double-float, 2 Ozaki WY products, 3 double-float + Ozaki WY; see
+    tsqr_opts_t).
     """
 
-    def __init__(self, A, leaf_h=0, chain=0, arity=0, inplace=False, precision=0):
+    def __init__(self, A, leaf_h=0, chain=0, arity=0, inplace=False, precision=0, r_only=False):
         import torch
 
         _check_matrix(A, "A")
@@ -232,7 +233,8 @@ class Factorization:
         self.m, self.n = m, n
         self.dtype = A.dtype
         self.code = TSQR_F32 if A.dtype == torch.float32 else TSQR_F64
-        self.opts = Opts(leaf_h=leaf_h, chain=chain, arity=arity, precision=precision, inplace=1 if inplace else 0)
+        self.opts = Opts(leaf_h=leaf_h, chain=chain, arity=arity, precision=precision, inplace=1 if inplace else 0,
+                         r_only=1 if r_only else 0)
         nbytes = tsqr_workspace_size(self.code, m, n, self.opts)
         self.work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=A.device)
         self.R = torch.empty((n, n), dtype=A.dtype, device=A.device)

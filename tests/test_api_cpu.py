@@ -164,3 +164,20 @@ def test_panel_factor_rejects_before_launch(lib):
     # workspace too small
     assert L.tsqr_factor(0, 0, 1000, 100, fake, 100, fake, 100, fake, 1 << 10, None, None, ctypes.byref(h)) == 4
     assert h.value is None
+
+
+def test_r_only_plans(lib):
+    """R alone keeps no reflectors, tau or T: a smaller workspace; it excludes inplace, panels
+    and batches."""
+    m, n = 100000, 64
+    full = lib.tsqr_workspace_size(lib.TSQR_F64, m, n)
+    r = lib.tsqr_workspace_size(lib.TSQR_F64, m, n, {"r_only": 1})
+    assert 0 < r < full
+    assert full - r >= (m // 96) * 64 * 64 * 8  # the per-leaf T factors at least
+    for opts, n_, status in [({"r_only": 1, "inplace": 1}, 64, 1), ({"r_only": 1}, 100, 2)]:
+        with pytest.raises(lib.TsqrError) as ei:
+            lib.tsqr_workspace_size(lib.TSQR_F64, m, n_, opts)
+        assert ei.value.status == status
+    with pytest.raises(lib.TsqrError) as ei:
+        lib.tsqr_batch_workspace_size(lib.TSQR_F64, 1, [1000], [16], {"r_only": 1})
+    assert ei.value.status == 2

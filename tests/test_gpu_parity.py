@@ -622,3 +622,28 @@ def test_nan_propagates_without_fault(T):
     A_h[1234, 5] = np.nan
     f, R, Q = run(T, A_h, leaf_h=128)
     assert np.isnan(R).any()
+
+
+@pytest.mark.parametrize("m,n,opts", [(40000 + 13, 64, {}), (30000, 50, {}), (60000 + 7, 32, {}), (100000 + 3, 16, {}),
+                                      (3000, 24, {"leaf_h": 128, "chain": 5, "arity": 3}), (777, 1, {"leaf_h": 16})])
+def test_r_only_matches_full_factorization(T, m, n, opts, prec):
+    """R alone (no reflectors, T or tree factors built or stored) is bitwise the R of the full
+    factorization, and the handle refuses to apply or form a Q it does not have."""
+    import torch
+
+    A_h = inputs.gaussian(m, n, inputs.seed_for(16, m + n))
+    A = torch.from_numpy(A_h).cuda()
+    f_full = T.Factorization(A, precision=prec, **opts)
+    f_r = T.Factorization(A, precision=prec, r_only=True, **opts)
+    torch.cuda.synchronize()
+    assert f_r.status() == T.TSQR_OK
+    assert torch.equal(f_r.R, f_full.R)
+    assert f_r.work.numel() < f_full.work.numel()
+    with pytest.raises(T.TsqrError):
+        f_r.form_q()
+    with pytest.raises(T.TsqrError):
+        f_r.apply_qt(torch.zeros((m, 1), dtype=torch.float64, device="cuda"))
+    A32 = A.float()
+    g_full, g_r = T.Factorization(A32, **opts), T.Factorization(A32, r_only=True, **opts)
+    torch.cuda.synchronize()
+    assert torch.equal(g_r.R, g_full.R)
