@@ -12,10 +12,12 @@
  * or Q B (a broadcast), or expanded to the explicit thin Q (Sec. 7.2).
  *
  * Conventions shared by every call:
- *   - Matrices are row-major FP64 (or FP32 with TSQR_F32): element (i, j) of X with leading
- *     dimension ldx is X[i * ldx + j], aligned to its element size.  A is read by TMA, which
- *     needs a 16-byte aligned base and an even lda; any other A is first copied into the
- *     workspace by a staging kernel.
+ *   - Matrices are FP64 (or FP32 with TSQR_F32), aligned to their element size, row-major:
+ *     element (i, j) of X with leading dimension ldx is X[i * ldx + j] (ldx >= columns); or,
+ *     with TSQR_COL_MAJOR, column-major: X[j * ldx + i] (ldx >= rows).  The layout given to
+ *     tsqr_factor holds for that handle's R, Q and B too.  A is read by TMA, which needs a
+ *     row-major A with a 16-byte aligned base and an even lda; any other A (column-major ones
+ *     included, by a tiled transpose) is first copied into the workspace by a staging kernel.
  *   - Reflectors are H = I - tau v v^T with v_0 = 1; beta = -sign(alpha) ||x||, sign(0) = +1.
  *   - R is returned with a non-negative diagonal: D = diag(sign(R_jj)), R <- D R and the
  *     thin Q <- Q D (the QR is unique only up to these signs, Sec. 2).
@@ -59,6 +61,7 @@ typedef enum {
  * widened into the workspace first (it is never overwritten: inplace is not supported), and
  * precision must be 0.  Every call takes both; tsqr_backward then works in the same type. */
 typedef enum { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype_t;
+/* TSQR_COL_MAJOR: n <= 64, not with inplace; tsqr_backward and batches take row-major only. */
 typedef enum { TSQR_ROW_MAJOR = 0, TSQR_COL_MAJOR = 1 } tsqr_layout_t;
 
 /* Tuning knobs of the reduction tree (Sec. 2: TSQR works on any tree; Sec. 4.2: the leaf
@@ -108,6 +111,7 @@ typedef struct {
   const double* signs;    /* np: D = diag(sign(R_jj)) of the root, sign(0) = +1 */
   int32_t panels;         /* 64-column panels of the factorization (1 when n <= 64) */
   int32_t dtype;          /* tsqr_dtype_t of A, R, Q and B */
+  int32_t layout;         /* tsqr_layout_t of A, R, Q and B */
 } tsqr_info_t;
 
 /* Bytes of device workspace tsqr_factor needs for an m x n factorization with `opts`

@@ -386,11 +386,15 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
   *out = nullptr;
   if (dtype != TSQR_F64 && dtype != TSQR_F32) return fail(TSQR_ERR_INVALID_ARG, "unknown dtype");
   const bool f32 = dtype == TSQR_F32;
-  if (layout != TSQR_ROW_MAJOR) return fail(TSQR_ERR_UNSUPPORTED, "only TSQR_ROW_MAJOR is implemented");
+  if (layout != TSQR_ROW_MAJOR && layout != TSQR_COL_MAJOR) return fail(TSQR_ERR_INVALID_ARG, "unknown layout");
+  const bool col = layout == TSQR_COL_MAJOR;
   if (!dA || !dR) return fail(TSQR_ERR_INVALID_ARG, "A and R must be non-NULL");
   if (n < 1 || m < n) return fail(TSQR_ERR_INVALID_ARG, "need m >= n >= 1");
-  if (lda < n) return fail(TSQR_ERR_INVALID_ARG, "lda must be >= n");
+  if (lda < (col ? m : n)) return fail(TSQR_ERR_INVALID_ARG, col ? "lda must be >= m (column-major)" : "lda must be >= n");
   if (ldr < n) return fail(TSQR_ERR_INVALID_ARG, "ldr must be >= n");
+  if (col && n > kPanel) return fail(TSQR_ERR_UNSUPPORTED, "TSQR_COL_MAJOR needs n <= 64");
+  if (col && opts && opts->inplace)
+    return fail(TSQR_ERR_INVALID_ARG, "inplace needs a row-major A (the reflectors are stored row-major)");
   const uintptr_t amask = f32 ? 3 : 7;
   if ((reinterpret_cast<uintptr_t>(dA) & amask) != 0 || (reinterpret_cast<uintptr_t>(dR) & amask) != 0)
     return fail(TSQR_ERR_INVALID_ARG, f32 ? "A and R must be 4-byte aligned" : "A and R must be 8-byte aligned");
@@ -398,11 +402,12 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
   Plan P;
   tsqr_status_t s = make_plan(m, n, opts, &P, f32);
   if (s != TSQR_OK) return s;
+  P.col_major = col ? 1 : 0;
   const bool inplace = opts && opts->inplace;
   // TMA needs a 16-byte aligned base and a row stride that is a multiple of 16 bytes; any other A
   // is first copied into the reflector storage of the workspace (which then holds V as usual).
-  // FP32 input is always widened into it.
-  const bool stage = f32 || (lda % 2 != 0) || !aligned16(dA);
+  // FP32 input is always widened into it, column-major input transposed into it.
+  const bool stage = col || f32 || (lda % 2 != 0) || !aligned16(dA);
   if (stage && inplace)
     return fail(TSQR_ERR_INVALID_ARG, "inplace needs an even lda and a 16-byte aligned A");
   const Layout L = make_layout(P, inplace);
@@ -434,8 +439,9 @@ tsqr_status_t tsqr_factor(tsqr_dtype_t dtype, tsqr_layout_t layout, int64_t m, i
   cudaError_t e = cudaMemsetAsync(st.status, 0, sizeof(int), cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   if (stage) {
-    e = f32 ? tsqr::launch_stage_widen(static_cast<const float*>(dA), lda, st.v, st.ldv, m, (int)n, cs)
-            : tsqr::launch_stage_copy(static_cast<const double*>(dA), lda, st.v, st.ldv, m, (int)n, cs);
+    e = col   ? tsqr::launch_stage_transpose(dA, f32, lda, st.v, st.ldv, m, (int)n, cs)
+        : f32 ? tsqr::launch_stage_widen(static_cast<const float*>(dA), lda, st.v, st.ldv, m, (int)n, cs)
+              : tsqr::launch_stage_copy(static_cast<const double*>(dA), lda, st.v, st.ldv, m, (int)n, cs);
     if (e != cudaSuccess) return cuda_fail(e, "staging copy launch");
   }
   e = tsqr::launch_factor(mapA, mapV, P, st, dR, ldr, box_rows, cs);
@@ -479,7 +485,8 @@ tsqr_status_t tsqr_form_q(tsqr_handle_t h, void* dQ, int64_t ldq, tsqr_stream_t 
     }
     return TSQR_OK;
   }
-  if (!dQ || ldq < h->P.n) return fail(TSQR_ERR_INVALID_ARG, "Q must be non-NULL with ldq >= n");
+  if (!dQ || ldq < (h->P.col_major ? h->P.m : h->P.n))
+    return fail(TSQR_ERR_INVALID_ARG, "Q must be non-NULL with ldq >= n (row-major) or >= m (column-major)");
   if (h->P.r_only) return fail(TSQR_ERR_INVALID_ARG, "the factorization computed R alone (r_only): no Q");
   cudaError_t e = tsqr::launch_form_q(h->mapV, h->P, h->st, dQ, ldq, h->box_rows,
                                       static_cast<cudaStream_t>(stream));
@@ -492,6 +499,8 @@ tsqr_status_t tsqr_apply_qt(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, t
   if (k < 0) return fail(TSQR_ERR_INVALID_ARG, "k must be >= 0");
   if (k == 0) return TSQR_OK;
   if (!dB || ldb < k) return fail(TSQR_ERR_INVALID_ARG, "B must be non-NULL with ldb >= k");
+  if (h->panels.empty() && h->P.col_major && ldb < h->P.m)
+    return fail(TSQR_ERR_INVALID_ARG, "column-major B needs ldb >= m");
   if (!h->panels.empty()) {  // Q^T = ... diag(I, Q_1^T) Q_0^T: panel p acts on rows c_p..
     char* B = static_cast<char*>(dB);
     const int64_t es = h->f32 ? 4 : 8;
@@ -513,6 +522,8 @@ tsqr_status_t tsqr_apply_q(tsqr_handle_t h, int64_t k, void* dB, int64_t ldb, ts
   if (k < 0) return fail(TSQR_ERR_INVALID_ARG, "k must be >= 0");
   if (k == 0) return TSQR_OK;
   if (!dB || ldb < k) return fail(TSQR_ERR_INVALID_ARG, "B must be non-NULL with ldb >= k");
+  if (h->panels.empty() && h->P.col_major && ldb < h->P.m)
+    return fail(TSQR_ERR_INVALID_ARG, "column-major B needs ldb >= m");
   if (!h->panels.empty()) {  // Q = Q_0 diag(I, Q_1) ...: the last panel first
     char* B = static_cast<char*>(dB);
     const int64_t es = h->f32 ? 4 : 8;
@@ -558,6 +569,7 @@ tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info) {
   }
   info->panels = 1;
   info->dtype = h->f32 ? TSQR_F32 : TSQR_F64;
+  info->layout = h->P.col_major ? TSQR_COL_MAJOR : TSQR_ROW_MAJOR;
   const Plan& P = h->P;
   info->m = P.m;
   info->n = P.n;

@@ -183,7 +183,7 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
         for (int r = gown; r < rows_valid; r += G) {
           E v = Ar::zero();
           for (int a = 0; a < n; ++a) Ar::fma_acc(v, tat<E>(S, r, a), f.M[a * ld + cown]);
-          Q[(row0 + r) * ldq + cown] = -Ar::to_out(Ar::fin(v));
+          Q[gidx(P, row0 + r, cown, ldq)] = -Ar::to_out(Ar::fin(v));
         }
       }
       for (int i = tid; i < np * np; i += kThreads) {
@@ -215,7 +215,7 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
           if (r < n) Ar::fma_acc(acc, Ar::from_int(1), f.M[r * ld + cown]);
           E v = Ar::neg(Ar::fin(acc));
           if (r < n) v = Ar::add(v, f.C[r * ld + cown]);
-          Q[(row0 + r) * ldq + cown] = Ar::to_out(v);
+          Q[gidx(P, row0 + r, cown, ldq)] = Ar::to_out(v);
         }
       }
       __syncthreads();
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(kOzT, 1)
         break;
       }
       ozaki_epilogue(z, tmem, rows_valid, [&](int i, int j, double v) {
-        if (j < n) Q[(row0 + i) * ldq + j] = -v;
+        if (j < n) Q[gidx(P, row0 + i, j, ldq)] = -v;
       });
     } else {
       // ---- first leaf (V unit lower trapezoidal; the tile's rows 0..n-1 hold R above the
@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(kOzT, 1)
         break;
       }
       ozaki_epilogue(z, tmem, rows_valid, [&](int i, int j, double v) {
-        if (j < n) Q[(row0 + i) * ldq + j] = (i < n ? z.C[i * kOzLd + j] : 0.0) - v;
+        if (j < n) Q[gidx(P, row0 + i, j, ldq)] = (i < n ? z.C[i * kOzLd + j] : 0.0) - v;
       });
     }
   }
@@ -819,21 +819,21 @@ __device__ inline void wy_update(const Tile& S, bool plain, int h, int n, int np
 }
 
 template <class Ar>
-__device__ inline void load_b(const typename Ar::Out* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k,
+__device__ inline void load_b(const Plan& P, const typename Ar::Out* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k,
                               int64_t row0, int rows, int64_t col0, int kb, typename Ar::E* Bs) {
   for (int o = threadIdx.x; o < rows * kb; o += kThreads) {
     const int r = o / kb, b = o % kb;
     const int64_t gr = row0 + r, gc = col0 + b;
-    Bs[o] = (gr < m && gc < k) ? Ar::from_out(__ldcg(Bg + gr * ldb + gc)) : Ar::zero();
+    Bs[o] = (gr < m && gc < k) ? Ar::from_out(__ldcg(Bg + gidx(P, gr, gc, ldb))) : Ar::zero();
   }
 }
 template <class Ar>
-__device__ inline void store_b(typename Ar::Out* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k, int64_t row0,
+__device__ inline void store_b(const Plan& P, typename Ar::Out* __restrict__ Bg, int64_t ldb, int64_t m, int64_t k, int64_t row0,
                                int r_begin, int rows, int64_t col0, int kb, const typename Ar::E* Bs) {
   for (int o = threadIdx.x; o < (rows - r_begin) * kb; o += kThreads) {
     const int r = r_begin + o / kb, b = o % kb;
     const int64_t gr = row0 + r, gc = col0 + b;
-    if (gr < m && gc < k) Bg[gr * ldb + gc] = Ar::to_out(Bs[r * kb + b]);
+    if (gr < m && gc < k) Bg[gidx(P, gr, gc, ldb)] = Ar::to_out(Bs[r * kb + b]);
   }
 }
 
@@ -909,7 +909,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t row0 = leaf * h;
     tile_load_start(f.S, &mapV, f.bar, np, row0, h, 0, box_rows);  // the reflector tile by TMA,
     load_square(st.t_leaf + leaf * np * np, f.T, np, f.ldt);      // while T and B's rows load
-    load_b<Ar>(Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
+    load_b<Ar>(P, Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
     if (!tile_load_finish(f.bar, phase, st.status, f.flag)) return;
     wy_inner<Ar>(f.S, plain, h, n, np, f.B, f.C, f.W, kb, f.red);
     __syncthreads();
@@ -919,14 +919,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     if (plain) {  // rows 0..n-1 become the chain's top block
       for (int o = tid; o < np * kb; o += kThreads) f.C[o] = (o / kb < n) ? f.B[o] : Ar::zero();
-      store_b<Ar>(Bg, ldb, P.m, k, row0, n, h, col0, kb, f.B);
+      store_b<Ar>(P, Bg, ldb, P.m, k, row0, n, h, col0, kb, f.B);
     } else {
-      store_b<Ar>(Bg, ldb, P.m, k, row0, 0, h, col0, kb, f.B);
+      store_b<Ar>(P, Bg, ldb, P.m, k, row0, 0, h, col0, kb, f.B);
     }
     __syncthreads();
   }
   // publish the chain's top block
-  store_b<Ar>(Bg, ldb, P.m, k, chain_top_row(P, g), 0, n, col0, kb, f.C);
+  store_b<Ar>(P, Bg, ldb, P.m, k, chain_top_row(P, g), 0, n, col0, kb, f.C);
   int idx = g;
   for (int level = 0; level < P.depth; ++level) {
     const int parent = idx / P.arity;
@@ -947,14 +947,14 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int o = tid; o < np * kb; o += kThreads) {
         const int a = o / kb, b = o % kb;
         const int64_t gc = col0 + b;
-        f.B[(size_t)s * np * kb + o] = (a < n && gc < k) ? Ar::from_out(__ldcg(Bg + (top + a) * ldb + gc)) : Ar::zero();
+        f.B[(size_t)s * np * kb + o] = (a < n && gc < k) ? Ar::from_out(__ldcg(Bg + gidx(P, top + a, gc, ldb))) : Ar::zero();
       }
     }
     __syncthreads();
     node_apply<Ar>(f, P, st, tn, q, kb, true);
     __syncthreads();
     for (int s = 0; s < q; ++s)
-      store_b<Ar>(Bg, ldb, P.m, k, node_top_row(P, level, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
+      store_b<Ar>(P, Bg, ldb, P.m, k, node_top_row(P, level, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
     idx = parent;
   }
   // root: the thin part gets the signs (the top block is C without a tree, else child 0's)
@@ -962,7 +962,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const E* topblk = (P.depth == 0) ? f.C : f.B;
   for (int o = tid; o < n * kb; o += kThreads) {
     const int a = o / kb, b = o % kb;
-    if (col0 + b < k) Bg[(int64_t)a * ldb + col0 + b] = (typename Ar::Out)__ldcg(st.signs + a) * Ar::to_out(topblk[o]);
+    if (col0 + b < k) Bg[gidx(P, a, col0 + b, ldb)] = (typename Ar::Out)__ldcg(st.signs + a) * Ar::to_out(topblk[o]);
   }
 }
 
@@ -986,7 +986,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int o = tid; o < np * kb; o += kThreads) {
       const int a = o / kb, b = o % kb;
       const int64_t gc = col0 + b;
-      typename Ar::Out v = (a < n && gc < k) ? Bg[(top + a) * ldb + gc] : typename Ar::Out(0);
+      typename Ar::Out v = (a < n && gc < k) ? Bg[gidx(P, top + a, gc, ldb)] : typename Ar::Out(0);
       if (level == P.depth && s == 0 && a < n) v *= (typename Ar::Out)st.signs[a];
       f.B[(size_t)s * np * kb + o] = Ar::from_out(v);
     }
@@ -995,7 +995,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   node_apply<Ar>(f, P, st, tn, q, kb, false);
   __syncthreads();
   for (int s = 0; s < q; ++s)
-    store_b<Ar>(Bg, ldb, P.m, k, node_top_row(P, level - 1, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
+    store_b<Ar>(P, Bg, ldb, P.m, k, node_top_row(P, level - 1, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
 }
 
 // ---- Q B, chains: last leaf first, the first leaf last.
@@ -1018,7 +1018,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int o = tid; o < np * kb; o += kThreads) {
     const int a = o / kb, b = o % kb;
     const int64_t gc = col0 + b;
-    typename Ar::Out v = (a < n && gc < k) ? Bg[(top + a) * ldb + gc] : typename Ar::Out(0);
+    typename Ar::Out v = (a < n && gc < k) ? Bg[gidx(P, top + a, gc, ldb)] : typename Ar::Out(0);
     if (P.depth == 0 && a < n) v *= (typename Ar::Out)st.signs[a];
     f.C[o] = Ar::from_out(v);
   }
@@ -1030,7 +1030,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t row0 = leaf * h;
     tile_load_start(f.S, &mapV, f.bar, np, row0, h, 0, box_rows);
     load_square(st.t_leaf + leaf * np * np, f.T, np, f.ldt);
-    load_b<Ar>(Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
+    load_b<Ar>(P, Bg, ldb, P.m, k, row0, h, col0, kb, f.B);
     if (!tile_load_finish(f.bar, phase, st.status, f.flag)) return;
     if (plain)
       for (int o = tid; o < n * kb; o += kThreads) f.B[o] = f.C[o];
@@ -1041,7 +1041,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     wy_update<Ar>(f.S, plain, h, n, np, f.B, f.C, f.W2, kb);
     __syncthreads();
-    store_b<Ar>(Bg, ldb, P.m, k, row0, 0, h, col0, kb, f.B);
+    store_b<Ar>(P, Bg, ldb, P.m, k, row0, 0, h, col0, kb, f.B);
     __syncthreads();
   }
 }
@@ -1143,7 +1143,8 @@ static cudaError_t launch_apply_qt_t(const CUtensorMap& mapV, const Plan& P, con
     e = cudaMemsetAsync(st.counters, 0, sizeof(int) * (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1) * kMaxColBlocks,
                         stream);
     if (e != cudaSuccess) return e;
-    apply_qt_kernel<Ar><<<dim3(P.chains, ncb), kThreads, smem, stream>>>(mapV, P, st, kc, B + c0, ldb, kb, box_rows);
+    apply_qt_kernel<Ar><<<dim3(P.chains, ncb), kThreads, smem, stream>>>(mapV, P, st, kc, B + gidx(P, 0, c0, ldb), ldb,
+                                                                          kb, box_rows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1172,13 +1173,13 @@ static cudaError_t launch_apply_q_t(const CUtensorMap& mapV, const Plan& P, cons
     const int64_t kc = (k - c0 < (int64_t)kb * kMaxColBlocks) ? (k - c0) : (int64_t)kb * kMaxColBlocks;
     const int ncb = (int)((kc + kb - 1) / kb);
     for (int level = P.depth; level >= 1; --level) {
-      apply_q_tree_kernel<Ar><<<dim3(P.level_count[level], ncb), kThreads, smem, stream>>>(P, st, level, kc, B + c0,
-                                                                                            ldb, kb);
+      apply_q_tree_kernel<Ar><<<dim3(P.level_count[level], ncb), kThreads, smem, stream>>>(
+          P, st, level, kc, B + gidx(P, 0, c0, ldb), ldb, kb);
       e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
-    apply_q_chain_kernel<Ar><<<dim3(P.chains, ncb), kThreads, smem, stream>>>(mapV, P, st, kc, B + c0, ldb, kb,
-                                                                               box_rows);
+    apply_q_chain_kernel<Ar><<<dim3(P.chains, ncb), kThreads, smem, stream>>>(mapV, P, st, kc, B + gidx(P, 0, c0, ldb),
+                                                                               ldb, kb, box_rows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -123,6 +123,7 @@ extern "C" tsqr_status_t tsqr_backward(tsqr_handle_t h, const void* dQbar, int64
   if (s != TSQR_OK) return s;
   const int64_t m = info.m;
   const int n = (int)info.n;
+  if (info.layout != TSQR_ROW_MAJOR) return internal_fail(TSQR_ERR_UNSUPPORTED, "tsqr_backward takes row-major matrices");
   if (!dR || !dAbar) return internal_fail(TSQR_ERR_INVALID_ARG, "R and Abar must be non-NULL");
   if (ldr < n || ldab < n || (dQbar && ldqb < n) || (dRbar && ldrb < n))
     return internal_fail(TSQR_ERR_INVALID_ARG, "leading dimensions must be >= n");

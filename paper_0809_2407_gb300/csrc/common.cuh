@@ -43,7 +43,13 @@ struct Plan {
   int rows_cap;   // rows of the factor kernel's shared tile
   int precision;  // kPrec* below: the arithmetic of the factorization
   int r_only;     // nonzero: R alone; no reflectors, T or tree factors are kept
+  int col_major;  // the caller's A, R, Q and B are column-major (element (i, j) at X[j * ld + i])
 };
+
+// Offset of element (r, c) of a caller matrix with leading dimension ld, in the plan's layout.
+__host__ __device__ __forceinline__ int64_t gidx(const Plan& P, int64_t r, int64_t c, int64_t ld) {
+  return P.col_major ? c * ld + r : r * ld + c;
+}
 
 __host__ __device__ inline int64_t chain_first_leaf(const Plan& p, int g) { return (int64_t)g * p.chain; }
 __host__ __device__ inline int64_t chain_end_leaf(const Plan& p, int g) {

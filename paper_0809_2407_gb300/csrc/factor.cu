@@ -233,7 +233,7 @@ __device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CU
   for (int i = tid; i < n * n; i += kThreads) {
     const int r = i / n, c = i % n;
     const Out d = Ar::is_neg(at<E>(S, r, r)) ? Out(-1) : Out(1);
-    R_out[(int64_t)r * ldr + c] = (c >= r) ? d * Ar::to_out(at<E>(S, r, c)) : Out(0);
+    R_out[gidx(P, r, c, ldr)] = (c >= r) ? d * Ar::to_out(at<E>(S, r, c)) : Out(0);
   }
 }
 
@@ -342,6 +342,41 @@ __global__ void stage_widen_kernel(const float* __restrict__ A, int64_t lda, dou
 cudaError_t launch_stage_widen(const float* A, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
                                cudaStream_t stream) {
   stage_widen_kernel<<<152 * 8, 256, 0, stream>>>(A, lda, V, ldv, m, n);
+  return cudaGetLastError();
+}
+
+// Column-major A (element (i, j) at A[j * lda + i]) staged into V's row-major 8-byte slots,
+// through 32 x 32 shared tiles so that both the reads (down columns) and the writes (along rows)
+// are coalesced; FP32 input is widened.
+template <class T>
+__global__ void stage_transpose_kernel(const T* __restrict__ A, int64_t lda, double* __restrict__ V, int64_t ldv,
+                                       int64_t m, int n) {
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const int c0 = blockIdx.y * 32;
+  for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < m; r0 += (int64_t)gridDim.x * 32) {
+    for (int cc = ty; cc < 32; cc += 8) {  // read: lanes along the rows of column c0 + cc
+      const int64_t r = r0 + tx;
+      const int c = c0 + cc;
+      tile[cc][tx] = (r < m && c < n) ? (double)A[(int64_t)c * lda + r] : 0.0;
+    }
+    __syncthreads();
+    for (int rr = ty; rr < 32; rr += 8) {  // write: lanes along the columns of row r0 + rr
+      const int64_t r = r0 + rr;
+      const int c = c0 + tx;
+      if (r < m && c < n) V[r * ldv + c] = tile[tx][rr];
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_stage_transpose(const void* A, bool f32, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
+                                   cudaStream_t stream) {
+  const dim3 grid(152 * 4, (unsigned)((n + 31) / 32));
+  if (f32)
+    stage_transpose_kernel<float><<<grid, 256, 0, stream>>>(static_cast<const float*>(A), lda, V, ldv, m, n);
+  else
+    stage_transpose_kernel<double><<<grid, 256, 0, stream>>>(static_cast<const double*>(A), lda, V, ldv, m, n);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,8 @@ cudaError_t launch_stage_copy(const double* A, int64_t lda, double* V, int64_t l
                               cudaStream_t stream);
 cudaError_t launch_stage_widen(const float* A, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
                                cudaStream_t stream);
+cudaError_t launch_stage_transpose(const void* A, bool f32, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
+                                   cudaStream_t stream);
 // R_out, Q and B are double*, or float* when P.precision == 3 (FP32 storage)
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                           void* R_out, int64_t ldr, int box_rows, cudaStream_t stream);

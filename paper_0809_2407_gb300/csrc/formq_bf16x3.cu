@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kT3, 1)
         break;
       }
       epilogue(tmem, rows_valid, [&](int i, int j, float v) {
-        if (j < n) Q[(row0 + i) * ldq + j] = -v;
+        if (j < n) Q[gidx(P, row0 + i, j, ldq)] = -v;
       });
     } else {
       // ---- first leaf on the FP32 pipe: Q_rows = [C; 0] - V (T (V_top^T C))
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kT3, 1)
           if (r < n) acc = __fadd_rn(acc, z.M[r * kLd + cown]);
           float v = -acc;
           if (r < n) v = __fadd_rn(v, z.C[r * kLd + cown]);
-          Q[(row0 + r) * ldq + cown] = v;
+          Q[gidx(P, row0 + r, cown, ldq)] = v;
         }
       }
       __syncthreads();

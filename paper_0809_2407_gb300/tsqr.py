@@ -39,7 +39,7 @@ class Info(ctypes.Structure):
                 ("v", ctypes.c_void_p), ("ldv", ctypes.c_int64),
                 ("tau_leaf", ctypes.c_void_p), ("t_leaf", ctypes.c_void_p), ("node_y", ctypes.c_void_p),
                 ("node_tau", ctypes.c_void_p), ("node_t", ctypes.c_void_p), ("signs", ctypes.c_void_p),
-                ("panels", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+                ("panels", ctypes.c_int32), ("dtype", ctypes.c_int32), ("layout", ctypes.c_int32)]
 
 
 class TsqrError(RuntimeError):
@@ -205,19 +205,34 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _check_matrix(X, name, dtype=None):
+def _check_matrix(X, name, dtype=None, layout=None):
+    """Checks a CUDA matrix argument; returns (layout, leading dimension).  A unit column stride
+    means row-major, else a unit row stride means column-major; layout, if given, must match."""
     import torch
 
     ok = (torch.float64, torch.float32) if dtype is None else (dtype,)
-    if not (X.is_cuda and X.dtype in ok and X.dim() == 2 and X.stride(1) == 1):
-        raise ValueError("%s must be a CUDA %s matrix with unit column stride"
+    if not (X.is_cuda and X.dtype in ok and X.dim() == 2 and (X.stride(1) == 1 or X.stride(0) == 1)):
+        raise ValueError("%s must be a CUDA %s matrix with unit column or row stride"
                          % (name, " or ".join(str(t).replace("torch.", "") for t in ok)))
+    got = TSQR_ROW_MAJOR if X.stride(1) == 1 and (layout != TSQR_COL_MAJOR or X.stride(0) != 1) else TSQR_COL_MAJOR
+    if layout is not None and got != layout:
+        raise ValueError("%s must be %s like A" % (name, "row-major" if layout == TSQR_ROW_MAJOR else "column-major"))
+    return got, (X.stride(0) if got == TSQR_ROW_MAJOR else max(X.stride(1), X.shape[0]))
+
+
+def _empty_like_layout(rows, cols, dtype, device, layout):
+    import torch
+
+    if layout == TSQR_COL_MAJOR:
+        return torch.empty((cols, rows), dtype=dtype, device=device).t()
+    return torch.empty((rows, cols), dtype=dtype, device=device)
 
 
 class Factorization:
-    """TSQR of a CUDA float64 or float32 matrix A (m x n, row-major).  Holds R, the workspace and
-    the handle.  A float32 A selects TSQR_F32 (FP32 storage and arithmetic); R, Q and the
-    matrices given to apply_qt / apply_q then are float32 too.
+    """TSQR of a CUDA float64 or float32 matrix A (m x n, row-major, or column-major: a unit row
+    stride, e.g. the transpose of a contiguous n x m tensor).  Holds R, the workspace and the
+    handle.  A float32 A selects TSQR_F32 (FP32 storage and arithmetic); R, Q and the matrices
+    given to apply_qt / apply_q then have A's dtype and layout.
 
     ``inplace=True`` lets the reflectors overwrite A (A must then stay alive; float64 only);
     ``r_only=True`` computes R alone and keeps no Q.  Options: leaf_h, chain, arity, precision
@@ -228,7 +243,7 @@ class Factorization:
     def __init__(self, A, leaf_h=0, chain=0, arity=0, inplace=False, precision=0, r_only=False):
         import torch
 
-        _check_matrix(A, "A")
+        self.layout, lda = _check_matrix(A, "A")
         m, n = A.shape
         self.m, self.n = m, n
         self.dtype = A.dtype
@@ -237,29 +252,27 @@ class Factorization:
                          r_only=1 if r_only else 0)
         nbytes = tsqr_workspace_size(self.code, m, n, self.opts)
         self.work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=A.device)
-        self.R = torch.empty((n, n), dtype=A.dtype, device=A.device)
+        self.R = _empty_like_layout(n, n, A.dtype, A.device, self.layout)
         self.A = A
-        self.handle = tsqr_factor(self.code, TSQR_ROW_MAJOR, m, n, A.data_ptr(), A.stride(0), self.R.data_ptr(), n,
+        self.handle = tsqr_factor(self.code, self.layout, m, n, A.data_ptr(), lda, self.R.data_ptr(), n,
                                   self.work.data_ptr(), nbytes, self.opts, _stream())
 
     def form_q(self, out=None):
-        import torch
-
-        Q = out if out is not None else torch.empty((self.m, self.n), dtype=self.dtype, device=self.R.device)
-        _check_matrix(Q, "Q", self.dtype)
-        tsqr_form_q(self.handle, Q.data_ptr(), Q.stride(0), _stream())
+        Q = out if out is not None else _empty_like_layout(self.m, self.n, self.dtype, self.R.device, self.layout)
+        _, ldq = _check_matrix(Q, "Q", self.dtype, self.layout)
+        tsqr_form_q(self.handle, Q.data_ptr(), ldq, _stream())
         return Q
 
     def apply_qt(self, B):
-        """B <- Q^T B in place (B: m x k CUDA matrix of A's dtype, unit column stride)."""
-        _check_matrix(B, "B", self.dtype)
-        tsqr_apply_qt(self.handle, B.shape[1], B.data_ptr(), B.stride(0), _stream())
+        """B <- Q^T B in place (B: m x k CUDA matrix of A's dtype and layout)."""
+        _, ldb = _check_matrix(B, "B", self.dtype, self.layout)
+        tsqr_apply_qt(self.handle, B.shape[1], B.data_ptr(), ldb, _stream())
         return B
 
     def apply_q(self, B):
         """B <- Q B in place."""
-        _check_matrix(B, "B", self.dtype)
-        tsqr_apply_q(self.handle, B.shape[1], B.data_ptr(), B.stride(0), _stream())
+        _, ldb = _check_matrix(B, "B", self.dtype, self.layout)
+        tsqr_apply_q(self.handle, B.shape[1], B.data_ptr(), ldb, _stream())
         return B
 
     def info(self):
@@ -301,7 +314,7 @@ class Batch:
 
         dt = mats[0].dtype
         for i, A in enumerate(mats):
-            _check_matrix(A, "A[%d]" % i, dt)
+            _check_matrix(A, "A[%d]" % i, dt, TSQR_ROW_MAJOR)
         self.mats = list(mats)
         dev = self.mats[0].device
         self.code = TSQR_F32 if dt == torch.float32 else TSQR_F64
@@ -540,7 +553,7 @@ def qr_autograd(A, keep="tree", **opts):
     if _QR is None:
         _QR, _QRB = _qr_function()
     if A.dim() == 2:
-        return _QR.apply(A, keep, dict(opts))
+        return _QR.apply(A.contiguous(), keep, dict(opts))
     if A.dim() != 3:
         raise ValueError("A must be m x n or B x m x n")
     return _QRB.apply(A.contiguous(), keep, dict(opts))

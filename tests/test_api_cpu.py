@@ -80,9 +80,9 @@ def test_factor_rejects_before_launch(lib):
                          ctypes.byref(h)) == 1
     assert L.tsqr_factor(0, 0, 100, 4, ctypes.c_void_p(0x1008), 4, fake, 4, fake, 1 << 20, ctypes.byref(inpl),
                          None, ctypes.byref(h)) == 1
-    # column-major is not implemented; FP32 keeps A read-only, runs precision 0 only, and checks
-    # its workspace and 4-byte alignment like FP64
-    assert L.tsqr_factor(0, 1, 100, 4, fake, 4, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 2
+    # column-major needs lda >= m; FP32 keeps A read-only, runs precision 0 only, and checks its
+    # workspace and 4-byte alignment like FP64
+    assert L.tsqr_factor(0, 1, 100, 4, fake, 4, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 1
     assert L.tsqr_factor(1, 0, 100, 4, fake, 4, fake, 4, fake, 1 << 20, ctypes.byref(inpl), None,
                          ctypes.byref(h)) == 2
     assert L.tsqr_factor(1, 0, 100, 4, fake, 4, fake, 4, fake, 1 << 20, ctypes.byref(lib.Opts(precision=1)), None,
@@ -181,3 +181,18 @@ def test_r_only_plans(lib):
     with pytest.raises(lib.TsqrError) as ei:
         lib.tsqr_batch_workspace_size(lib.TSQR_F64, 1, [1000], [16], {"r_only": 1})
     assert ei.value.status == 2
+
+
+def test_column_major_checks(lib):
+    """Column-major A needs lda >= m, n <= 64 and no inplace; all rejected before any launch."""
+    L = lib.load()
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)
+    col = lib.TSQR_COL_MAJOR
+    assert L.tsqr_factor(0, col, 100, 4, fake, 99, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 1
+    assert L.tsqr_factor(0, col, 1000, 100, fake, 1000, fake, 100, fake, 1 << 30, None, None, ctypes.byref(h)) == 2
+    inpl = lib.Opts(inplace=1)
+    assert L.tsqr_factor(0, col, 100, 4, fake, 100, fake, 4, fake, 1 << 20, ctypes.byref(inpl), None,
+                         ctypes.byref(h)) == 1
+    assert L.tsqr_factor(0, 7, 100, 4, fake, 100, fake, 4, fake, 1 << 20, None, None, ctypes.byref(h)) == 1
+    assert h.value is None

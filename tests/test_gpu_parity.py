@@ -647,3 +647,38 @@ def test_r_only_matches_full_factorization(T, m, n, opts, prec):
     g_full, g_r = T.Factorization(A32, **opts), T.Factorization(A32, r_only=True, **opts)
     torch.cuda.synchronize()
     assert torch.equal(g_r.R, g_full.R)
+
+
+@pytest.mark.parametrize("m,n,dtype", [(40000 + 13, 64, "float64"), (3001, 21, "float64"), (50000, 33, "float32"),
+                                       (777, 1, "float64")])
+def test_column_major(T, m, n, dtype):
+    """TSQR_COL_MAJOR: A, R, Q and B column-major (a unit row stride, lda >= m).  The same
+    factorization as the row-major copy of A, bitwise (A is transposed into the same staging
+    buffer), with Q, R and Q^T B returned in column-major order."""
+    import torch
+
+    tdt = getattr(torch, dtype)
+    A_h = inputs.gaussian(m, n, inputs.seed_for(17, m + n))
+    A_row = torch.from_numpy(A_h).to(tdt).cuda()
+    lda = m + 5
+    buf = torch.zeros((n, lda), dtype=tdt, device="cuda")
+    buf[:, :m] = A_row.t()
+    A_col = buf[:, :m].t()  # m x n, strides (1, lda)
+    f_row, f_col = T.Factorization(A_row), T.Factorization(A_col)
+    Q_row, Q_col = f_row.form_q(), f_col.form_q()
+    torch.cuda.synchronize()
+    assert f_col.info().layout == T.TSQR_COL_MAJOR and f_col.status() == T.TSQR_OK
+    assert Q_col.stride(0) == 1 and f_col.R.stride(0) == 1
+    assert torch.equal(f_col.R, f_row.R) and torch.equal(Q_col, Q_row)
+    assert torch.equal(A_col, A_row)  # A is read only
+    B_h = inputs.gaussian(m, 3, 5)
+    B_row = torch.from_numpy(B_h).to(tdt).cuda()
+    B_col = torch.from_numpy(B_h.T.copy()).to(tdt).cuda().t()
+    f_row.apply_qt(B_row)
+    f_col.apply_qt(B_col)
+    assert torch.equal(B_col, B_row)
+    f_row.apply_q(B_row)
+    f_col.apply_q(B_col)
+    assert torch.equal(B_col, B_row)
+    with pytest.raises(ValueError):
+        f_col.apply_qt(torch.zeros((m, 3), dtype=tdt, device="cuda"))  # row-major B for a column-major handle
