@@ -66,9 +66,9 @@ def load_peaks():
 
 
 # DRAM bytes (read + write) of one factor_kernel<ArithF64> launch, from an ncu capture at
-# m = 524288, n = 64 (700.3 MB), scaled by rows to m = 4194304: A is read once and V and T are
+# m = 524288, n = 64 (700.4 MB), scaled by rows to m = 4194304: A is read once and V and T are
 # written once, so traffic grows in proportion to m.  Only valid for the kernel as captured.
-FACTOR_F64_TRAFFIC = {(4194304, 64): 8 * 700.27e6}
+FACTOR_F64_TRAFFIC = {(4194304, 64): 8 * 700.40e6}
 
 # FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
