@@ -351,26 +351,34 @@ def run_e2e(tsqr, torch, dev, stream, sptr, A_pin, b_h, A, Q, R, b, work, nbytes
                        "schedule": "one stream: H2D, factor, thin Q, Q^T b, D2H"}}
 
 
-def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, warmup=2):
+SHAPE_FORMS = {32: (("double_float", 1, False), ("fp32", 0, True)),
+               128: (("double_float", 1, False), ("ozaki_wy", 2, False), ("df_ozaki_wy", 3, False),
+                     ("fp32", 0, True))}
+
+
+def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, warmup=2, forms=SHAPE_FORMS):
     """Plain FP64 TSQR (factor + thin Q + Q^T b) on the other column counts of the workload
     family, A = U Sigma V^T with kappa = 1: n = 16 and 32 are single TSQRs with taller leaves,
-    n = 128 is the blocked QR over two 64-column TSQR panels."""
+    n = 128 is the blocked QR over two 64-column TSQR panels.  The precision forms run beside
+    FP64 at n = 32 and 128 (the Ozaki forms only differ from FP64 where np = 64: at n = 128 the
+    panels' thin Q and their trailing updates Q^T [A_2] and Q [0; Q_2] run on the tensor cores)."""
     import numpy as np
 
-    out = {}
-    for n in ns:
-        A = torch.from_numpy(make_input(m, n)).to(dev)
-        b = torch.from_numpy(np.random.default_rng(6).standard_normal((m, 1))).to(dev)
-        Q = torch.empty((m, n), dtype=torch.float64, device=dev)
-        R = torch.empty((n, n), dtype=torch.float64, device=dev)
-        nbytes = tsqr.tsqr_workspace_size(tsqr.TSQR_F64, m, n, None)
+    def time_form(A, n, precision, f32):
+        code = tsqr.TSQR_F32 if f32 else tsqr.TSQR_F64
+        A_ = A.float() if f32 else A
+        b = torch.from_numpy(np.random.default_rng(6).standard_normal((m, 1))).to(dev).to(A_.dtype)
+        Q = torch.empty((m, n), dtype=A_.dtype, device=dev)
+        R = torch.empty((n, n), dtype=A_.dtype, device=dev)
+        opts = tsqr.Opts(precision=precision)
+        nbytes = tsqr.tsqr_workspace_size(code, m, n, opts)
         work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         ev = {"factor": [], "form_q": [], "apply_qt": []}
         for it in range(warmup + steps):
             mk = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             mk[0].record(stream)
-            h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
-                                 work.data_ptr(), nbytes, None, sptr)
+            h = tsqr.tsqr_factor(code, tsqr.TSQR_ROW_MAJOR, m, n, A_.data_ptr(), n, R.data_ptr(), n,
+                                 work.data_ptr(), nbytes, opts, sptr)
             mk[1].record(stream)
             tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
             mk[2].record(stream)
@@ -384,13 +392,28 @@ def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, war
                     ev[k].append(mk[i].elapsed_time(mk[i + 1]))
         fl = flops(m, n)
         ms = sum(statistics.mean(v) for v in ev.values())
-        out["n%d" % n] = {
-            "m": m, "n": n, "panels": info.panels, "leaf_h": info.leaf_h, "chains": info.chains,
-            "value": sum(fl.values()) / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
-            "kernel_ms": {k: statistics.mean(v) for k, v in ev.items()},
-            "backward_error": (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item(),
-            "orthogonality": torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Q.T @ Q).item()}
-        del A, b, Q, R, work
+        Ad, Qd, Rd = A_.double(), Q.double(), R.double()
+        res = {"m": m, "n": n, "panels": info.panels, "leaf_h": info.leaf_h, "chains": info.chains,
+               "value": sum(fl.values()) / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
+               "kernel_ms": {k: statistics.mean(v) for k, v in ev.items()},
+               "backward_error": (torch.linalg.norm(Ad - Qd @ Rd) / torch.linalg.norm(Ad)).item(),
+               "orthogonality": torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Qd.T @ Qd).item()}
+        del Ad, Qd, Rd, A_, b, Q, R, work
+        torch.cuda.empty_cache()
+        return res
+
+    out = {}
+    for n in ns:
+        A = torch.from_numpy(make_input(m, n)).to(dev)
+        out["n%d" % n] = time_form(A, n, 0, False)
+        if forms and n in forms:
+            f64_ms = out["n%d" % n]["ms_per_step"]
+            out["n%d" % n]["forms"] = {}
+            for name, precision, f32 in forms[n]:
+                r = time_form(A, n, precision, f32)
+                r["speedup_vs_f64"] = f64_ms / r["ms_per_step"]
+                out["n%d" % n]["forms"][name] = r
+        del A
         torch.cuda.empty_cache()
     return out
 

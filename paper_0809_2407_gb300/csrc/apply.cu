@@ -11,7 +11,7 @@
 // workspace are in that policy's element format, B and Q are FP64 at the boundary.
 #include "arith.cuh"
 #include "factor_kernels.h"
-#include "ozaki.cuh"
+#include "ozaki_pass.cuh"
 
 namespace tsqr {
 
@@ -303,38 +303,6 @@ cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain
 // np = 64 (33 <= n <= 64) and h <= 128.
 // 512 threads, one block per SM (all 512 TMEM columns).
 
-constexpr int kOzT = 512;
-static constexpr int kOzLd = 65;
-
-struct OzSmem {
-  Tile Y;           // h x 64 FP64 leaf tile (TMA); converted in place to fixed point
-  char* bsl;        // 8 B slices, 8 KB each; FP64 scratch (T, X) for the first leaf
-  char* asl;        // 2 A slice buffers, 16 KB each
-  double* C;        // 64 x 65
-  double* M;        // 64 x 65; the leaf's T (64 x 64, bulk copy) then its fixed-point form
-  int* expA;        // 128
-  int* expB;        // 64
-  uint64_t* bars;   // 0: Y tile, 1: A buffer 0, 2: A buffer 1, 3: T
-  uint32_t* slot;   // TMEM base address
-  int* flag;
-};
-
-__device__ inline OzSmem carve_ozaki(char* raw, int h) {
-  OzSmem z;
-  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
-  const size_t ybytes = ((size_t)h * 64 * 8 + 1023) & ~size_t(1023);
-  z.Y = Tile{base, h};
-  z.bsl = base + ybytes;
-  z.asl = z.bsl + 8 * oz::kBSliceBytes;
-  z.C = reinterpret_cast<double*>(z.asl + 2 * oz::kASliceBytes);
-  z.M = z.C + 64 * kOzLd;
-  z.expA = reinterpret_cast<int*>(z.M + 64 * kOzLd);
-  z.expB = z.expA + 128;
-  z.bars = reinterpret_cast<uint64_t*>(z.expB + 64);
-  z.slot = reinterpret_cast<uint32_t*>(z.bars + 4);
-  z.flag = reinterpret_cast<int*>(z.slot + 2);
-  return z;
-}
 
 size_t formq_ozaki_smem_bytes(const Plan& P) {
   const size_t ybytes = ((size_t)P.h * 64 * 8 + 1023) & ~size_t(1023);
@@ -342,176 +310,6 @@ size_t formq_ozaki_smem_bytes(const Plan& P) {
          16;
 }
 
-// bf16 bits of slices s of two fixed-point values, packed low|high: the 7-bit integer is made an
-// exact FP32 by the 2^23 magic add, whose upper 16 bits are its bf16 form.
-__device__ __forceinline__ uint32_t slice_pair(uint64_t f0, uint64_t f1, int s) {
-  const uint32_t c0 = (uint32_t)(f0 >> (56 - 7 * s)) & 127u;
-  const uint32_t c1 = (uint32_t)(f1 >> (56 - 7 * s)) & 127u;
-  const float x0 = __fsub_rn(__int_as_float(0x4B000000 | c0), 8388608.f);
-  const float x1 = __fsub_rn(__int_as_float(0x4B000000 | c1), 8388608.f);
-  const uint32_t sg = ((uint32_t)(f0 >> 48) & 0x8000u) | ((uint32_t)(f1 >> 32) & 0x80000000u);
-  return __byte_perm(__float_as_uint(x0), __float_as_uint(x1), 0x7632) | sg;
-}
-
-// *dst = max(*dst, e over the warp), for a full warp whose lanes all target dst (the callers'
-// index idx >> 6 is the same across 32 consecutive idx): one shared atomic per warp.
-__device__ __forceinline__ void warp_max_into(int* dst, int e) {
-  const int m = __reduce_max_sync(0xffffffffu, e);
-  if ((threadIdx.x & 31) == 0) atomicMax(dst, m);
-}
-
-// Waits (thread 0, bounded) for a barrier phase; every thread learns the outcome.
-__device__ inline bool oz_wait_all(const OzSmem& z, uint64_t* bar, uint32_t parity, int* status) {
-  if (threadIdx.x == 0 && !oz::wait_bar(bar, parity)) {
-    atomicOr(status, kStatusTimeout);
-    *z.flag = 1;
-  }
-  __syncthreads();
-  return *z.flag == 0;
-}
-
-// One Ozaki product D (128 x 64) = A (a_rows x 64) B (64 x 64) into the 8 TMEM groups.  The B
-// slices must be in z.bsl and rows a_rows..127 of both A buffers zero; afix(r, k) gives the
-// fixed-point A entries.  All threads call.  False on timeout.
-template <class AFix>
-__device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows, AFix afix, uint32_t ph[2],
-                                      int* status) {
-  const int tid = threadIdx.x;
-  const uint32_t idesc = oz::idesc_bf16(oz::kM, oz::kN);
-  for (int s = 1; s <= oz::kSlices; ++s) {
-    const int b = (s - 1) & 1;
-    if (s >= 3) {
-      const bool ok = oz_wait_all(z, z.bars + 1 + b, ph[b], status);
-      ph[b] ^= 1u;
-      if (!ok) return false;
-    }
-    char* abuf = z.asl + b * oz::kASliceBytes;
-    for (int idx = tid; idx < a_rows * 32; idx += kOzT) {  // two k per thread: one 32-bit store
-      const int r = idx >> 5, k = (idx & 31) * 2;
-      *reinterpret_cast<uint32_t*>(abuf + oz::op_off(r, k)) = slice_pair(afix(r, k), afix(r, k + 1), s);
-    }
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      oz::fence_after_sync();
-      const uint64_t adesc = oz::sw128_desc(smem_u32(abuf));
-      for (int t = 1; t <= oz::kSlices + 1 - s; ++t) {
-        const uint32_t d = tmem + (uint32_t)(s + t - 2) * 64u;
-        const uint64_t bdesc = oz::sw128_desc(smem_u32(z.bsl + (t - 1) * oz::kBSliceBytes));
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)  // K step of 16 bf16 = 32 bytes = 2 descriptor units
-          oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (s > 1 || kk > 0) ? 1u : 0u);
-      }
-      oz::mma_commit(z.bars + 1 + b);
-    }
-  }
-  bool ok = oz_wait_all(z, z.bars + 1, ph[0], status);
-  ph[0] ^= 1u;
-  ok = oz_wait_all(z, z.bars + 2, ph[1], status) && ok;
-  ph[1] ^= 1u;
-  oz::fence_after_sync();
-  return ok;
-}
-
-// Rows r0..r1-1 of both A buffers set to zero (the MMA reads all 128 rows).
-__device__ inline void ozaki_zero_a_rows(const OzSmem& z, int r0, int r1) {
-  for (int i = threadIdx.x; i < 2 * (r1 - r0) * 8; i += kOzT) {
-    const int b = i / ((r1 - r0) * 8), rem = i % ((r1 - r0) * 8);
-    *reinterpret_cast<uint4*>(z.asl + b * oz::kASliceBytes + (size_t)(r0 + rem / 8) * 128 + (rem % 8) * 16) =
-        make_uint4(0, 0, 0, 0);
-  }
-}
-
-// B slices of the 64 x 64 matrix whose output column j and k-th entry is bval(j, k), against the
-// column exponents z.expB (computed here).  All threads call; ends with a barrier.
-template <class BVal>
-__device__ inline void ozaki_b_slices(const OzSmem& z, BVal bval) {
-  const int tid = threadIdx.x;
-  for (int j = tid; j < 64; j += kOzT) z.expB[j] = 0;
-  __syncthreads();
-  for (int idx = tid; idx < 64 * 64; idx += kOzT) warp_max_into(&z.expB[idx >> 6], oz::bexp(bval(idx >> 6, idx & 63)));
-  __syncthreads();
-  for (int idx = tid; idx < 64 * 32; idx += kOzT) {
-    const int j = idx >> 5, k = (idx & 31) * 2;
-    const uint64_t f0 = oz::to_fixed(bval(j, k), z.expB[j]);
-    const uint64_t f1 = oz::to_fixed(bval(j, k + 1), z.expB[j]);
-#pragma unroll
-    for (int s = 1; s <= oz::kSlices; ++s)
-      *reinterpret_cast<uint32_t*>(z.bsl + (s - 1) * oz::kBSliceBytes + oz::op_off(j, k)) = slice_pair(f0, f1, s);
-  }
-  fence_proxy_async_smem();
-  __syncthreads();
-}
-
-// Reads the 8 group accumulators back: out(i, j, value) for rows i < rows and all 64 columns.
-// Warp w reads TMEM lanes 32 (w & 3).. and columns 16 (w >> 2)..; warps without valid rows skip.
-template <class Out>
-__device__ inline void ozaki_epilogue(const OzSmem& z, uint32_t tmem, int rows, Out out) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int sp = warp & 3;
-  const int i = 32 * sp + lane;
-  const int c0 = 16 * (warp >> 2);
-  if (32 * sp < rows) {
-    const uint32_t tb = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)c0;
-    long long acc[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = 0;
-#pragma unroll 1
-    for (int g = 2; g <= oz::kSlices + 1; ++g) {
-      uint32_t v[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-            "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(tb + (uint32_t)(g - 2) * 64u));
-      oz::tmem_wait_ld();
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const long long G = (long long)__float2int_rn(__uint_as_float(v[c]));
-        acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
-      }
-    }
-    if (i < rows) {
-      const int ea = z.expA[i];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) out(i, c0 + c, oz::scale_int(acc[c], ea + z.expB[c0 + c] - 2100));
-    }
-  }
-  oz::fence_before_sync();
-  __syncthreads();
-  oz::fence_after_sync();
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-// The value of an 8-byte workspace slot: a double, or a double-float (hi, lo) pair when the
-// factorization ran in double-float arithmetic (the sum is exact in FP64).
-template <bool kPairs>
-__device__ __forceinline__ double slot_val(double raw) {
-  if constexpr (kPairs) {
-    const f32x2 p = *reinterpret_cast<const f32x2*>(&raw);
-    return (double)p.hi + (double)p.lo;
-  } else {
-    return raw;
-  }
-}
-
-// Exponent and fixed-point form of a slot, straight from the pair's FP32 bits when kPairs.
-template <bool kPairs>
-__device__ __forceinline__ int slot_bexp(double raw) {
-  if constexpr (kPairs) return oz::bexp_pair(raw);
-  else return oz::bexp(raw);
-}
-template <bool kPairs>
-__device__ __forceinline__ uint64_t slot_fixed(double raw, int emax) {
-  if constexpr (kPairs) return oz::to_fixed_pair(raw, emax);
-  else return oz::to_fixed(raw, emax);
-}
 
 template <bool kPairs>
 __global__ void __launch_bounds__(kOzT, 1)
@@ -998,6 +796,42 @@ __global__ void __launch_bounds__(kThreads, 2)
     store_b<Ar>(P, Bg, ldb, P.m, k, node_top_row(P, level - 1, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
 }
 
+// ---- Q^T B, tree part as separate launches (after a chain kernel that published each chain's
+//      top block): one launch per level, bottom-up; the root level then applies the signs.
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 2)
+    apply_qt_tree_kernel(const Plan P, const Store st, int level, int64_t k, typename Ar::Out* __restrict__ Bg,
+                         int64_t ldb, int kb) {
+  using E = typename Ar::E;
+  extern __shared__ char smem_raw[];
+  ApplySmem<E> f = carve_apply<E>(smem_raw, P, kb);
+  const int tid = threadIdx.x;
+  const int np = P.np, n = P.n;
+  const int node = blockIdx.x, cb = blockIdx.y;
+  const int64_t col0 = (int64_t)cb * kb;
+  const int first = node * P.arity;
+  const int q = min(P.arity, P.level_count[level - 1] - first);
+  const int tn = P.level_offset[level] + node - P.chains;
+  for (int s = 0; s < q; ++s) {
+    const int64_t top = node_top_row(P, level - 1, first + s);
+    for (int o = tid; o < np * kb; o += kThreads) {
+      const int a = o / kb, b = o % kb;
+      const int64_t gc = col0 + b;
+      f.B[(size_t)s * np * kb + o] = (a < n && gc < k) ? Ar::from_out(__ldcg(Bg + gidx(P, top + a, gc, ldb))) : Ar::zero();
+    }
+  }
+  __syncthreads();
+  node_apply<Ar>(f, P, st, tn, q, kb, true);
+  __syncthreads();
+  for (int s = (level == P.depth) ? 1 : 0; s < q; ++s)
+    store_b<Ar>(P, Bg, ldb, P.m, k, node_top_row(P, level - 1, first + s), 0, n, col0, kb, f.B + (size_t)s * np * kb);
+  if (level == P.depth)  // the root: child 0's block is the thin part, with the signs
+    for (int o = tid; o < n * kb; o += kThreads) {
+      const int a = o / kb, b = o % kb;
+      if (col0 + b < k) Bg[gidx(P, a, col0 + b, ldb)] = (typename Ar::Out)__ldcg(st.signs + a) * Ar::to_out(f.B[o]);
+    }
+}
+
 // ---- Q B, chains: last leaf first, the first leaf last.
 template <class Ar>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -1151,8 +985,60 @@ static cudaError_t launch_apply_qt_t(const CUtensorMap& mapV, const Plan& P, con
   return cudaSuccess;
 }
 
+// Tree levels of Q^T B bottom-up (after launch_apply_ozaki_chains).
+template <class Ar>
+static cudaError_t launch_apply_qt_tree_t(const Plan& P, const Store& st, int64_t k, void* B_, int64_t ldb,
+                                          cudaStream_t stream) {
+  typename Ar::Out* B = static_cast<typename Ar::Out*>(B_);
+  const int kb = pick_kb(k);
+  const size_t smem = apply_smem_bytes(P, kb);
+  cudaError_t e =
+      cudaFuncSetAttribute(apply_qt_tree_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t c0 = 0; c0 < k; c0 += (int64_t)kb * kMaxColBlocks) {
+    const int64_t kc = (k - c0 < (int64_t)kb * kMaxColBlocks) ? (k - c0) : (int64_t)kb * kMaxColBlocks;
+    const int ncb = (int)((kc + kb - 1) / kb);
+    for (int level = 1; level <= P.depth; ++level) {
+      apply_qt_tree_kernel<Ar><<<dim3(P.level_count[level], ncb), kThreads, smem, stream>>>(
+          P, st, level, kc, B + gidx(P, 0, c0, ldb), ldb, kb);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// Tree levels of Q B top-down (before launch_apply_ozaki_chains).
+template <class Ar>
+static cudaError_t launch_apply_q_tree_t(const Plan& P, const Store& st, int64_t k, void* B_, int64_t ldb,
+                                         cudaStream_t stream) {
+  typename Ar::Out* B = static_cast<typename Ar::Out*>(B_);
+  const int kb = pick_kb(k);
+  const size_t smem = apply_smem_bytes(P, kb);
+  cudaError_t e =
+      cudaFuncSetAttribute(apply_q_tree_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t c0 = 0; c0 < k; c0 += (int64_t)kb * kMaxColBlocks) {
+    const int64_t kc = (k - c0 < (int64_t)kb * kMaxColBlocks) ? (k - c0) : (int64_t)kb * kMaxColBlocks;
+    const int ncb = (int)((kc + kb - 1) / kb);
+    for (int level = P.depth; level >= 1; --level) {
+      apply_q_tree_kernel<Ar><<<dim3(P.level_count[level], ncb), kThreads, smem, stream>>>(
+          P, st, level, kc, B + gidx(P, 0, c0, ldb), ldb, kb);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B,
                             int64_t ldb, int box_rows, cudaStream_t stream) {
+  if (ozaki_apply_applies(P, k)) {  // chains on the tensor cores, then the tree levels
+    cudaError_t e = launch_apply_ozaki_chains(mapV, P, st, k, static_cast<double*>(B), ldb, box_rows, true, stream);
+    if (e != cudaSuccess) return e;
+    return prec_df(P.precision) ? launch_apply_qt_tree_t<ArithDF>(P, st, k, B, ldb, stream)
+                                : launch_apply_qt_tree_t<ArithF64>(P, st, k, B, ldb, stream);
+  }
   if (prec_df(P.precision)) return launch_apply_qt_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
   if (P.precision == kPrecF32) return launch_apply_qt_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);
   return launch_apply_qt_t<ArithF64>(mapV, P, st, k, B, ldb, box_rows, stream);
@@ -1188,6 +1074,12 @@ static cudaError_t launch_apply_q_t(const CUtensorMap& mapV, const Plan& P, cons
 
 cudaError_t launch_apply_q(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B,
                            int64_t ldb, int box_rows, cudaStream_t stream) {
+  if (ozaki_apply_applies(P, k)) {  // the tree levels, then the chains on the tensor cores
+    cudaError_t e = prec_df(P.precision) ? launch_apply_q_tree_t<ArithDF>(P, st, k, B, ldb, stream)
+                                         : launch_apply_q_tree_t<ArithF64>(P, st, k, B, ldb, stream);
+    if (e != cudaSuccess) return e;
+    return launch_apply_ozaki_chains(mapV, P, st, k, static_cast<double*>(B), ldb, box_rows, false, stream);
+  }
   if (prec_df(P.precision)) return launch_apply_q_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
   if (P.precision == kPrecF32) return launch_apply_q_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);
   return launch_apply_q_t<ArithF64>(mapV, P, st, k, B, ldb, box_rows, stream);

@@ -207,6 +207,82 @@ def test_apply_column_counts(T, k):
     assert np.abs(B.cpu().numpy() - B_h).max() <= 1e-12
 
 
+@pytest.mark.parametrize("m,n,k,opts", [
+    (20000, 64, 64, {}),                                # default plan (h = 96): W over 64 + 32 rows
+    (20000 + 37, 48, 100, {"leaf_h": 128, "chain": 3}),  # n < 64, 2 x 64 rows, ragged leaf, 64 + 36 columns
+    (9000, 64, 33, {"leaf_h": 64, "chain": 1}),          # one part of 64 rows; every leaf a chain's first
+    (700, 64, 129, {"leaf_h": 96, "chain": 64}),        # one chain: no tree, the signs in the chain kernel
+    (6000, 40, 32, {"leaf_h": 80, "chain": 2, "arity": 3}),  # ternary tree levels after the chains
+])
+def test_apply_ozaki(T, m, n, k, opts):
+    """Q^T B and Q B with the chains' WY products as Ozaki splits on the tensor cores (precision
+    modes 2 and 3 from 32 columns of B on).  Mode 2 factors in native FP64 exactly as mode 0
+    does, so its Q^T B and Q B must equal mode 0's FP64-pipe results over all m rows to the
+    accuracy of the split products (2^-50 relative to the rows and columns involved); mode 3 is
+    held to the oracle's thin part and the invariants Q^T A = [R; 0], Q Q^T B = B and
+    Q [I; 0] = thin Q."""
+    import torch
+
+    A_h = inputs.gaussian(m, n, inputs.seed_for(18, m + n + k))
+    B_h = inputs.gaussian(m, k, inputs.seed_for(19, m + k))
+    A = torch.from_numpy(A_h).cuda()
+    f0 = T.Factorization(A, precision=0, **opts)
+    B0 = torch.from_numpy(B_h.copy()).cuda()
+    f0.apply_qt(B0)
+    for prec in (2, 3):
+        f = T.Factorization(A, precision=prec, **opts)
+        Q = f.form_q()
+        R = f.R
+        B = torch.from_numpy(B_h.copy()).cuda()
+        f.apply_qt(B)
+        torch.cuda.synchronize()
+        assert f.status() == T.TSQR_OK
+        QtB = B.cpu().numpy()
+        assert np.abs(QtB[:n] - oracle.thin_qt(A_h, B_h)).max() <= 1e-10
+        if prec == 2:
+            assert torch.equal(R, f0.R)  # the same FP64 factorization
+            assert (B - B0).abs().max().item() <= 1e-12 * B0.abs().max().item()
+        Ad = A.clone()
+        f.apply_qt(Ad)
+        Rn = R.cpu().numpy()
+        QtA = Ad.cpu().numpy()
+        assert np.abs(QtA[:n] - Rn).max() <= 1e-10 * np.abs(Rn).max()
+        assert np.abs(QtA[n:]).max() <= 1e-10 * np.abs(Rn).max()
+        f.apply_q(B)
+        assert np.abs(B.cpu().numpy() - B_h).max() <= 1e-10
+        E = torch.zeros((m, max(n, 32)), dtype=torch.float64, device="cuda")
+        E[:n, :n] = torch.eye(n, dtype=torch.float64, device="cuda")
+        f.apply_q(E)
+        assert (E[:, :n] - Q).abs().max().item() <= 100 * n * UNIT[prec]
+        assert torch.all(E[:, n:] == 0)
+        f.close()
+    f0.close()
+
+
+def test_apply_ozaki_column_major(T):
+    """The Ozaki Q^T B and Q B read and write B in a column-major handle's layout: bitwise the
+    row-major results."""
+    import torch
+
+    m, n, k = 7000, 64, 70
+    A_h = inputs.gaussian(m, n, inputs.seed_for(20, 1))
+    B_h = inputs.gaussian(m, k, inputs.seed_for(20, 2))
+    A_row = torch.from_numpy(A_h).cuda()
+    A_col = torch.from_numpy(A_h.T.copy()).cuda().t()
+    f_row, f_col = T.Factorization(A_row, precision=2), T.Factorization(A_col, precision=2)
+    B_row = torch.from_numpy(B_h).cuda()
+    B_col = torch.from_numpy(B_h.T.copy()).cuda().t()
+    f_row.apply_qt(B_row)
+    f_col.apply_qt(B_col)
+    torch.cuda.synchronize()
+    assert torch.equal(B_col, B_row)
+    f_row.apply_q(B_row)
+    f_col.apply_q(B_col)
+    torch.cuda.synchronize()
+    assert torch.equal(B_col, B_row)
+    assert np.abs(B_row.cpu().numpy() - B_h).max() <= 1e-10
+
+
 @pytest.mark.parametrize("m,n,opts", [(20000, 128, {}), (5000 + 33, 65, {"leaf_h": 128}),
                                       (3001, 100, {"chain": 2, "arity": 3}), (2000, 200, {}), (300, 150, {}),
                                       (129, 129, {}), (64 * 9 + 7, 128, {"leaf_h": 64, "chain": 1})])
