@@ -1039,6 +1039,11 @@ cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store&
     return prec_df(P.precision) ? launch_apply_qt_tree_t<ArithDF>(P, st, k, B, ldb, stream)
                                 : launch_apply_qt_tree_t<ArithF64>(P, st, k, B, ldb, stream);
   }
+  if (bf16x3_apply_applies(P, k)) {
+    cudaError_t e = launch_apply_bf16x3_chains(mapV, P, st, k, static_cast<float*>(B), ldb, box_rows, true, stream);
+    if (e != cudaSuccess) return e;
+    return launch_apply_qt_tree_t<ArithF32>(P, st, k, B, ldb, stream);
+  }
   if (prec_df(P.precision)) return launch_apply_qt_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
   if (P.precision == kPrecF32) return launch_apply_qt_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);
   return launch_apply_qt_t<ArithF64>(mapV, P, st, k, B, ldb, box_rows, stream);
@@ -1079,6 +1084,11 @@ cudaError_t launch_apply_q(const CUtensorMap& mapV, const Plan& P, const Store& 
                                          : launch_apply_q_tree_t<ArithF64>(P, st, k, B, ldb, stream);
     if (e != cudaSuccess) return e;
     return launch_apply_ozaki_chains(mapV, P, st, k, static_cast<double*>(B), ldb, box_rows, false, stream);
+  }
+  if (bf16x3_apply_applies(P, k)) {
+    cudaError_t e = launch_apply_q_tree_t<ArithF32>(P, st, k, B, ldb, stream);
+    if (e != cudaSuccess) return e;
+    return launch_apply_bf16x3_chains(mapV, P, st, k, static_cast<float*>(B), ldb, box_rows, false, stream);
   }
   if (prec_df(P.precision)) return launch_apply_q_t<ArithDF>(mapV, P, st, k, B, ldb, box_rows, stream);
   if (P.precision == kPrecF32) return launch_apply_q_t<ArithF32>(mapV, P, st, k, B, ldb, box_rows, stream);

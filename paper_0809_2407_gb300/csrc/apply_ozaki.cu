@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kOzT, 1)
 }  // namespace
 
 bool ozaki_apply_applies(const Plan& P, int64_t k) {
-  return (P.precision == kPrecOzaki || P.precision == kPrecDFOzaki) && P.np == 64 && P.h <= 128 && k >= kOzApplyMinCols;
+  return (P.precision == kPrecOzaki || P.precision == kPrecDFOzaki) && P.np == 64 && P.h <= 128 && k >= kTcApplyMinCols;
 }
 
 cudaError_t launch_apply_ozaki_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,

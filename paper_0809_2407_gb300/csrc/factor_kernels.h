@@ -10,14 +10,18 @@ size_t formq_smem_bytes(const Plan& P);
 size_t apply_smem_bytes(const Plan& P, int kb);
 size_t formq_ozaki_smem_bytes(const Plan& P);
 bool ozaki_form_q_applies(const Plan& P);
-// Q^T B / Q B with the chains' WY products as Ozaki splits: precision modes 2 and 3, np = 64,
-// h <= 128, and at least this many columns of B (narrower B stays on the FP64 pipe)
-constexpr int64_t kOzApplyMinCols = 32;
+// Q^T B / Q B with the chains' WY products on the tensor cores (Ozaki splits in precision modes 2
+// and 3, bf16x3 terms in FP32 storage): np = 64, h <= 128, and at least this many columns of B
+// (narrower B stays on the FP64 / FP32 pipe)
+constexpr int64_t kTcApplyMinCols = 32;
 bool ozaki_apply_applies(const Plan& P, int64_t k);
 // the chain part only (Q^T: before the tree levels; Q: after them); B is double*
 cudaError_t launch_apply_ozaki_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, double* B,
                                       int64_t ldb, int box_rows, bool trans, cudaStream_t stream);
 size_t formq_bf16x3_smem_bytes(const Plan& P);
+bool bf16x3_apply_applies(const Plan& P, int64_t k);
+cudaError_t launch_apply_bf16x3_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, float* B,
+                                       int64_t ldb, int box_rows, bool trans, cudaStream_t stream);
 bool bf16x3_form_q_applies(const Plan& P);
 // chains of an FP32-storage thin Q with bf16x3 tensor-core WY products (after the tree levels)
 cudaError_t launch_formq_bf16x3_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, float* Q, int64_t ldq,

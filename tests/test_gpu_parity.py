@@ -259,6 +259,71 @@ def test_apply_ozaki(T, m, n, k, opts):
     f0.close()
 
 
+@pytest.mark.parametrize("m,n,k,opts", [
+    (20000, 64, 64, {}),
+    (20000 + 37, 48, 100, {"leaf_h": 128, "chain": 3}),
+    (9000, 64, 33, {"leaf_h": 64, "chain": 1}),
+    (700, 64, 129, {"leaf_h": 96, "chain": 64}),
+    (6000, 40, 32, {"leaf_h": 80, "chain": 2, "arity": 3}),
+])
+def test_apply_tc_matches_narrow(T, m, n, k, opts):
+    """From 32 columns of B on, Q^T B and Q B take the tensor-core chain kernels (Ozaki splits in
+    mode 3, bf16x3 terms in FP32 storage); narrower blocks run the FP64 / double-float / FP32
+    pipe kernels.  On the same factorization the two must agree column block by column block:
+    B in one call against B in slices of 16 columns, to the accuracy of the form (1e-12 relative
+    for mode 3; FP32: 50 n u with u = 2^-24)."""
+    import torch
+
+    A_h = inputs.gaussian(m, n, inputs.seed_for(21, m + n + k))
+    B_h = inputs.gaussian(m, k, inputs.seed_for(22, m + k))
+    for dt, prec, tol in ((torch.float64, 3, 1e-12), (torch.float32, 0, 50 * n * U32)):
+        A = torch.from_numpy(A_h).to(dt).cuda()
+        f = T.Factorization(A, precision=prec, **opts)
+        B = torch.from_numpy(B_h).to(dt).cuda()
+        Bn = B.clone()
+        f.apply_qt(B)
+        for c in range(0, k, 16):
+            blk = Bn[:, c:c + 16].contiguous()
+            f.apply_qt(blk)
+            Bn[:, c:c + 16] = blk
+        torch.cuda.synchronize()
+        assert f.status() == T.TSQR_OK
+        scale = B.abs().max().item()
+        assert (B - Bn).abs().max().item() <= tol * scale, (dt, (B - Bn).abs().max().item() / scale)
+        B_thin = B[:n].double().cpu().numpy()
+        ref = oracle.thin_qt(A.double().cpu().numpy(), B_h.astype(np.float64) if dt == torch.float64 else
+                             torch.from_numpy(B_h).float().double().numpy())
+        assert np.abs(B_thin - ref).max() <= (1e-10 if dt == torch.float64 else 50 * n * U32 * np.abs(ref).max())
+        f.apply_q(B)
+        for c in range(0, k, 16):
+            blk = Bn[:, c:c + 16].contiguous()
+            f.apply_q(blk)
+            Bn[:, c:c + 16] = blk
+        torch.cuda.synchronize()
+        assert (B - Bn).abs().max().item() <= tol * scale
+        B0 = torch.from_numpy(B_h).to(dt).cuda()
+        assert (B - B0).abs().max().item() <= tol * B0.abs().max().item()  # Q Q^T B = B
+        f.close()
+
+
+def test_apply_bf16x3_panels(T):
+    """FP32 storage with n > 64: the panels' trailing updates take the bf16x3 Q^T B / Q B (64
+    trailing columns at n = 128); backward error and orthogonality within the FP32 bar."""
+    import torch
+
+    m, n = 30000, 128
+    A32 = inputs.gaussian(m, n, inputs.seed_for(23, 1)).astype(np.float32)
+    A = torch.from_numpy(A32).cuda()
+    f = T.Factorization(A)
+    Q = f.form_q()
+    torch.cuda.synchronize()
+    assert f.status() == T.TSQR_OK and f.info().panels == 2
+    Qd, Rd = Q.double().cpu().numpy(), f.R.double().cpu().numpy()
+    assert oracle.backward_error(A32.astype(np.float64), Qd, Rd) <= TOL_F32
+    assert oracle.orthogonality(Qd) <= TOL_F32
+    f.close()
+
+
 def test_apply_ozaki_column_major(T):
     """The Ozaki Q^T B and Q B read and write B in a column-major handle's layout: bitwise the
     row-major results."""
