@@ -40,11 +40,24 @@ __device__ inline void tri_mul(const typename Ar::E* T, int ldt, const typename 
 }
 
 // Copies an np x np row-major matrix of 8-byte elements into shared memory (leading dim ld).
+// Each thread issues its loads in batches of 8 before storing any of them, so a 64 x 64 block
+// costs two memory round trips rather than one per element.
 template <class E>
 __device__ inline void load_square(const double* __restrict__ g, E* s, int np, int ld) {
-  for (int i = threadIdx.x; i < np * np; i += kThreads) {
-    const double v = __ldcg(g + i);
-    s[(i / np) * ld + (i % np)] = *reinterpret_cast<const E*>(&v);
+  constexpr int kBatch = 8;
+  const int total = np * np;
+  for (int i0 = threadIdx.x; i0 < total; i0 += kBatch * kThreads) {
+    double v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * kThreads;
+      v[u] = (i < total) ? __ldcg(g + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * kThreads;
+      if (i < total) s[(i / np) * ld + (i % np)] = *reinterpret_cast<const E*>(&v[u]);
+    }
   }
 }
 
