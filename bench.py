@@ -418,6 +418,49 @@ def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, war
     return out
 
 
+def run_apply_wide(tsqr, torch, dev, stream, sptr, A, m, n, k=64, steps=3):
+    """Q^T B then Q B for a 64-column B on one factorization of A, per form: 4mnk - 2n^2k flops
+    each way (the LAPACK count of applying n reflectors to k columns)."""
+    import numpy as np
+
+    out = {"k": k, "flops_each_way": 4.0 * m * n * k - 2.0 * n * n * k}
+    B_h = torch.from_numpy(np.random.default_rng(7).standard_normal((m, k)))
+    for name, precision, f32 in (("fp64", 0, False), ("ozaki_wy", 2, False), ("df_ozaki_wy", 3, False),
+                                 ("fp32", 0, True)):
+        code = tsqr.TSQR_F32 if f32 else tsqr.TSQR_F64
+        dt = torch.float32 if f32 else torch.float64
+        A_ = A.to(dt)
+        R = torch.empty((n, n), dtype=dt, device=dev)
+        B0 = B_h.to(dt).to(dev)
+        B = B0.clone()
+        opts = tsqr.Opts(precision=precision)
+        nbytes = tsqr.tsqr_workspace_size(code, m, n, opts)
+        work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        h = tsqr.tsqr_factor(code, tsqr.TSQR_ROW_MAJOR, m, n, A_.data_ptr(), n, R.data_ptr(), n,
+                             work.data_ptr(), nbytes, opts, sptr)
+        tq, tqt = [], []
+        for it in range(1 + steps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            tsqr.tsqr_apply_qt(h, k, B.data_ptr(), k, sptr)
+            e[1].record(stream)
+            tsqr.tsqr_apply_q(h, k, B.data_ptr(), k, sptr)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            if it:
+                tqt.append(e[0].elapsed_time(e[1]))
+                tq.append(e[1].elapsed_time(e[2]))
+        err = ((B - B0).abs().max() / B0.abs().max()).item()  # Q Q^T B = B
+        tsqr.tsqr_destroy(h)
+        a, b = statistics.mean(tqt), statistics.mean(tq)
+        out[name] = {"apply_qt_ms": a, "apply_q_ms": b,
+                     "value": 2 * out["flops_each_way"] / ((a + b) / 1e3) / 1e9, "unit": "GFLOP/s",
+                     "roundtrip_rel_err": err}
+        del A_, R, B0, B, work
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_autograd(tsqr, torch, dev, args, batch=64, m=65536, n=32, seed=20085000):
     """Forward + backward of sum(W1*Q) + sum(W2*R) for a batch of 64 matrices of 65536 x 32
     (FP64, and the same data rounded to FP32): time and peak extra memory when the backward keeps
@@ -481,6 +524,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-matrix batched workload")
     ap.add_argument("--no-autograd", action="store_true", help="skip the differentiable-QR workload")
     ap.add_argument("--no-shapes", action="store_true", help="skip the n = 16, 32, 128 shapes")
+    ap.add_argument("--apply-wide", action="store_true",
+                    help="time Q^T B / Q B with 64 columns even with --no-forms (for profiling)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 3],
                     help="arithmetic mode of the main line (0 native FP64; 1 and 2 are for profiling)")
     ap.add_argument("--fp32", action="store_true", help="main line in FP32 storage (for profiling)")
@@ -724,6 +769,12 @@ def main():
             del Qc, Rc, X
         torch.cuda.empty_cache()
 
+    # Q^T B and Q B with 64 columns on the benchmark's matrix: the WY products of the apply on the
+    # FP64 / FP32 pipes (mode 0) or on the tensor cores (modes 2 and 3, FP32 storage)
+    apply_wide = None
+    if (not args.no_forms or args.apply_wide) and world == 1:
+        apply_wide = run_apply_wide(tsqr, torch, dev, stream, sptr, A, m, n)
+
     shapes = None
     if not args.no_shapes and world == 1:
         shapes = run_shapes(tsqr, torch, dev, stream, sptr, m)
@@ -749,7 +800,8 @@ def main():
                           "parallelism": "replicas" if world > 1 else "single-gpu"},
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
-               "roofline": roofline, "precision_forms": forms, "batched": batched, "shapes": shapes,
+               "roofline": roofline, "precision_forms": forms, "apply_wide": apply_wide, "batched": batched,
+               "shapes": shapes,
                "autograd": autograd, "r_alone": r_alone, "library_context": library, "cpu_baseline": cpu,
                "e2e": e2e,
                "gpu_launches": main_mode["launches"] * args.steps, "clocks": clocks}

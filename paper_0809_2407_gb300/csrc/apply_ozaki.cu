@@ -10,7 +10,8 @@
 // exact FP32 group sums in TMEM.  W's inner dimension is the leaf height h (up to 128): it is
 // taken in parts of at most 64 rows, each against its own exponents and epilogued into an FP64
 // partial sum, so every group sum stays below 2^23 as in the thin-Q kernel.  M is computed as
-// its transpose, with W^T as the A operand, so that T's slices come from one bulk copy.  B is read
+// its transpose, with W^T (kept transposed from the epilogue on) as the A operand, so that T's
+// slices come from one bulk copy.  B is read
 // and written in the caller's layout; the reflector tile arrives by TMA and is loaded twice per
 // leaf (once converted with column exponents for W, once with row exponents for the update).
 // The tree levels run on the FP64 (or double-float) pipe in their own launches.
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(kOzT, 1)
   const uint32_t tmem = *z.slot;
   uint32_t ph[2] = {0u, 0u};
   uint32_t y_phase = 0, t_phase = 0;
-  double* const X = z.M;  // W, then T's fixed-point form, then M (64 x 65)
+  double* const X = z.M;  // W^T (row b holds W's column b), then M (64 x 65)
 
   // C: zero for Q^T (the first leaf's top rows fill it); for Q the chain's top block of B, the
   // signs applied when there is no tree
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(kOzT, 1)
       }
       fence_proxy_async_smem();
       __syncthreads();
-      if (!ozaki_mma_pass(
+      if (!ozaki_mma_pass<true>(  // lanes on a: the tile's row r0 + k is contiguous along a
               z, tmem, 64,
               [&](int a, int k) {
                 return (r0 + k < r1) ? *reinterpret_cast<const uint64_t*>(z.Y.ptr(r0 + k, a)) : 0ull;
@@ -132,9 +133,9 @@ __global__ void __launch_bounds__(kOzT, 1)
         break;
       }
       const bool first_part = (r0 == 0);
-      ozaki_epilogue(z, tmem, 64, [&](int a, int b, double v) {
-        const int o = a * kOzLd + b;
-        X[o] = first_part ? ((plain ? 0.0 : z.C[o]) + v) : (X[o] + v);
+      ozaki_epilogue(z, tmem, 64, [&](int a, int b, double v) {  // stored transposed: W^T
+        const int o = b * kOzLd + a;
+        X[o] = first_part ? ((plain ? 0.0 : z.C[a * kOzLd + b]) + v) : (X[o] + v);
       });
     }
     if (!alive) break;
@@ -150,12 +151,11 @@ __global__ void __launch_bounds__(kOzT, 1)
     //      columns of W) and W's fixed-point form in place.
     for (int j = tid; j < 128; j += kOzT) z.expA[j] = 0;
     __syncthreads();
-    for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], oz::bexp(X[(idx & 63) * kOzLd + (idx >> 6)]));
+    for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], oz::bexp(X[(idx >> 6) * kOzLd + (idx & 63)]));
     __syncthreads();
     for (int idx = tid; idx < np * np; idx += kOzT) {
-      const int b = idx >> 6, a = idx & 63;
-      double* p = X + a * kOzLd + b;
-      *reinterpret_cast<uint64_t*>(p) = oz::to_fixed(*p, z.expA[b]);
+      double* p = X + (idx >> 6) * kOzLd + (idx & 63);
+      *reinterpret_cast<uint64_t*>(p) = oz::to_fixed(*p, z.expA[idx >> 6]);
     }
     {
       const bool ok = oz_wait_all(z, z.bars + 3, t_phase, st.status);
@@ -166,12 +166,13 @@ __global__ void __launch_bounds__(kOzT, 1)
       }
     }
     const double* Ts = reinterpret_cast<const double*>(z.asl);
-    ozaki_b_slices(z, [&](int p, int k) {
-      return slot_val<kPairs>(kTrans ? Ts[k * np + p] : Ts[p * np + k]);
-    });
+    if (kTrans)  // T[k][p]: contiguous along p
+      ozaki_b_slices_jmajor(z, [&](int p, int k) { return slot_val<kPairs>(Ts[k * np + p]); });
+    else         // T[p][k]: contiguous along k
+      ozaki_b_slices(z, [&](int p, int k) { return slot_val<kPairs>(Ts[p * np + k]); });
     ozaki_zero_a_rows(z, 64, oz::kM);  // the copy of T overwrote the A buffers
     if (!ozaki_mma_pass(
-            z, tmem, 64, [&](int b, int a) { return *reinterpret_cast<const uint64_t*>(X + a * kOzLd + b); }, ph,
+            z, tmem, 64, [&](int b, int a) { return *reinterpret_cast<const uint64_t*>(X + b * kOzLd + a); }, ph,
             st.status)) {
       alive = false;
       break;

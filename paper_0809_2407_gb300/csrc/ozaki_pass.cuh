@@ -73,9 +73,10 @@ __device__ inline bool oz_wait_all(const OzSmem& z, uint64_t* bar, uint32_t pari
 // One Ozaki product D (128 x 64) = A (a_rows x 64) B (64 x 64) into the 8 TMEM groups.  The B
 // slices must be in z.bsl and rows a_rows..127 of both A buffers zero; afix(r, k) gives the
 // fixed-point A entries.  With accumulate, the groups keep their sums (a product over a longer
-// K in 64-deep parts, every part against the same exponents).  All threads call.  False on
-// timeout.
-template <class AFix>
+// K in 64-deep parts, every part against the same exponents).  kLanesOnRows puts the lanes of a
+// warp on consecutive rows r (for an afix source laid out with r contiguous); otherwise on
+// consecutive k.  All threads call.  False on timeout.
+template <bool kLanesOnRows = false, class AFix>
 __device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows, AFix afix, uint32_t ph[2],
                                       int* status, bool accumulate = false) {
   const int tid = threadIdx.x;
@@ -89,7 +90,8 @@ __device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows
     }
     char* abuf = z.asl + b * oz::kASliceBytes;
     for (int idx = tid; idx < a_rows * 32; idx += kOzT) {  // two k per thread: one 32-bit store
-      const int r = idx >> 5, k = (idx & 31) * 2;
+      const int r = kLanesOnRows ? idx % a_rows : idx >> 5;
+      const int k = kLanesOnRows ? (idx / a_rows) * 2 : (idx & 31) * 2;
       *reinterpret_cast<uint32_t*>(abuf + oz::op_off(r, k)) = slice_pair(afix(r, k), afix(r, k + 1), s);
     }
     fence_proxy_async_smem();
@@ -150,6 +152,32 @@ __device__ inline void ozaki_b_slices(const OzSmem& z, BVal bval) {
   for (int idx = tid; idx < 64 * 64; idx += kOzT) warp_max_into(&z.expB[idx >> 6], oz::bexp(bval(idx >> 6, idx & 63)));
   __syncthreads();
   ozaki_b_fill(z, bval);
+}
+
+// The same for a source laid out with j contiguous: the lanes of a warp take consecutive j, so
+// the reads of bval do not collide in the shared-memory banks.
+template <class BVal>
+__device__ inline void ozaki_b_slices_jmajor(const OzSmem& z, BVal bval) {
+  const int tid = threadIdx.x;
+  for (int j = tid; j < 64; j += kOzT) z.expB[j] = 0;
+  __syncthreads();
+  {  // column j's maximum over k, k strided by the kOzT / 64 groups
+    const int j = tid & 63, kg = tid >> 6;
+    int e = 0;
+    for (int k = kg; k < 64; k += kOzT / 64) e = max(e, oz::bexp(bval(j, k)));
+    atomicMax(&z.expB[j], e);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < 64 * 32; idx += kOzT) {
+    const int j = idx & 63, k = (idx >> 6) * 2;
+    const uint64_t f0 = oz::to_fixed(bval(j, k), z.expB[j]);
+    const uint64_t f1 = oz::to_fixed(bval(j, k + 1), z.expB[j]);
+#pragma unroll
+    for (int s = 1; s <= oz::kSlices; ++s)
+      *reinterpret_cast<uint32_t*>(z.bsl + (s - 1) * oz::kBSliceBytes + oz::op_off(j, k)) = slice_pair(f0, f1, s);
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
 }
 
 // Reads the 8 group accumulators back: out(i, j, value) for rows i < rows and all 64 columns.
