@@ -338,7 +338,7 @@ def run_e2e(tsqr, torch, dev, stream, sptr, A_pin, b_h, A, Q, R, b, work, nbytes
     serial(1)
     ser_ms = serial(max(1, min(steps, 3)))
     pipelined(2)
-    K = max(3, min(steps, 6))
+    K = max(3, min(steps, 10))
     pipe_ms = pipelined(K)
     ok = bool(torch.equal(Q_h[0], Q_h[1]) and torch.equal(R_h[0], R_h[1]))
     return {"value": per_step * world / (pipe_ms / 1e3) / 1e9, "unit": "GFLOP/s",

@@ -66,30 +66,47 @@ __device__ inline void load_square(const double* __restrict__ g, E* s, int np, i
 
 template <class E>
 struct FormQSmem {
-  Tile S;
-  E *C, *M, *T, *X;
-  uint64_t* bar;
+  Tile S, S2;  // the leaf tile; with double buffering a second one (the next leaf's), else S2 = S
+  E *C, *M, *T;
+  E* X;        // without double buffering its own block; with it, the idle tile buffer is used
+  uint64_t* bar;  // one barrier per tile buffer
   int* flag;
   int ld;
+  bool dbl;
 };
+
+// Maximum opt-in shared memory per block on GB300.
+constexpr size_t kFormqSmemCap = 232448;
+
+// The chain part double-buffers its leaf tile (the next leaf's tile and T load while the
+// current leaf computes) when two tiles and three np x (np + 1) blocks fit, and a tile can hold
+// the first leaf's scratch block X (h > np).
+__host__ __device__ inline bool formq_double_buffered(const Plan& P) {
+  const size_t tile = (size_t)P.h * P.np * 8, sq = (size_t)P.np * (P.np + 1) * 8;
+  return P.h > P.np && 1024 + 2 * tile + 3 * sq + 2 * 8 + 16 <= kFormqSmemCap;
+}
 
 template <class E>
 __device__ inline FormQSmem<E> carve_formq(char* raw, const Plan& P) {
   FormQSmem<E> f;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  const size_t tile = (size_t)P.h * P.np * 8;
+  f.dbl = formq_double_buffered(P);
   f.S = Tile{base, P.h};
+  f.S2 = f.dbl ? Tile{base + tile, P.h} : f.S;
   f.ld = P.np + 1;
-  f.C = reinterpret_cast<E*>(base + (size_t)P.h * P.np * 8);
+  f.C = reinterpret_cast<E*>(base + (f.dbl ? 2 : 1) * tile);
   f.M = f.C + P.np * f.ld;
   f.T = f.M + P.np * f.ld;
-  f.X = f.T + P.np * f.ld;
-  f.bar = reinterpret_cast<uint64_t*>(f.X + P.np * f.ld);
-  f.flag = reinterpret_cast<int*>(f.bar + 1);
+  f.X = f.dbl ? reinterpret_cast<E*>(f.S2.base) : f.T + P.np * f.ld;
+  f.bar = reinterpret_cast<uint64_t*>(f.T + (f.dbl ? 1 : 2) * P.np * f.ld);
+  f.flag = reinterpret_cast<int*>(f.bar + 2);
   return f;
 }
 
 size_t formq_smem_bytes(const Plan& P) {
-  return 1024 + (size_t)P.h * P.np * 8 + 4 * (size_t)P.np * (P.np + 1) * 8 + 8 + 16;
+  const size_t tile = (size_t)P.h * P.np * 8, sq = (size_t)P.np * (P.np + 1) * 8;
+  return formq_double_buffered(P) ? 1024 + 2 * tile + 3 * sq + 2 * 8 + 16 : 1024 + tile + 4 * sq + 2 * 8 + 16;
 }
 
 // One level of the thin-Q broadcast (Sec. 4.1): node (level, idx) holds its block C of
@@ -149,17 +166,19 @@ __global__ void __launch_bounds__(kThreads, 1) formq_tree_kernel(const Plan P, c
 
 // Q rows of chain g, last leaf first.  chain step (V = [I; Y]): Q_rows = -Y M with M = T C,
 // then C -= M.  first leaf (V unit lower trapezoidal): Q_rows = [C; 0] - V (T (V_top^T C)).
+// With double buffering, the next leaf's tile (TMA) and T (register loads) are in flight while
+// the current leaf computes.
 template <class Ar>
 __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Plan& P, const Store& st,
                                             typename Ar::Out* __restrict__ Q, int64_t ldq, int box_rows, int g,
                                             char* smem_raw) {
   using E = typename Ar::E;
   FormQSmem<E> f = carve_formq<E>(smem_raw, P);
-  const Tile& S = f.S;
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, h = P.h, ld = f.ld;
   if (tid == 0) {
     mbar_init(f.bar, 1);
+    mbar_init(f.bar + 1, 1);
     fence_mbar_init();
   }
   // C = this chain's block of Q_tree [D; 0], left by the tree levels (or D without a tree)
@@ -176,18 +195,56 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
     }
   }
   __syncthreads();
-  uint32_t phase = 0;
+  uint32_t phase[2] = {0u, 0u};
+
+  // T of the next leaf in registers: np * np / kThreads <= 16 slots per thread
+  constexpr int kTReg = 16;
+  double treg[kTReg];
+  auto t_fetch = [&](int64_t leaf) {
+    const double* Tg = st.t_leaf + leaf * np * np;
+#pragma unroll
+    for (int u = 0; u < kTReg; ++u) {
+      const int i = tid + u * kThreads;
+      treg[u] = (i < np * np) ? __ldcg(Tg + i) : 0.0;
+    }
+  };
+  auto t_store = [&]() {
+#pragma unroll
+    for (int u = 0; u < kTReg; ++u) {
+      const int i = tid + u * kThreads;
+      if (i < np * np) f.T[(i / np) * ld + (i % np)] = *reinterpret_cast<const E*>(&treg[u]);
+    }
+  };
 
   // ---- unwind the chain from its last leaf to its first
   const int64_t l0 = chain_first_leaf(P, g), l1 = chain_end_leaf(P, g);
   const int G = kThreads / np;
   const int cown = tid & (np - 1), gown = tid / np;
+  int buf = 0;
+  if (f.dbl) {
+    tile_load_start(f.S, mapV_p, f.bar, np, (l1 - 1) * h, h, 0, box_rows);
+    t_fetch(l1 - 1);
+  }
   for (int64_t leaf = l1 - 1; leaf >= l0; --leaf) {
     const bool plain = (leaf == l0);
     const int64_t row0 = leaf * h;
-    tile_load_start(S, mapV_p, f.bar, np, row0, h, 0, box_rows);  // the tile by TMA while T loads
-    load_square(st.t_leaf + leaf * np * np, f.T, np, ld);
-    if (!tile_load_finish(f.bar, phase, st.status, f.flag)) return;
+    const Tile& S = buf ? f.S2 : f.S;
+    E* X = f.X;
+    if (f.dbl) {
+      if (!tile_load_finish(f.bar + buf, phase[buf], st.status, f.flag)) return;
+      t_store();
+      if (!plain) {  // the next leaf's loads go into the idle buffer (its barrier orders t_store too)
+        tile_load_start(buf ? f.S : f.S2, mapV_p, f.bar + (buf ^ 1), np, (leaf - 1) * h, h, 0, box_rows);
+        t_fetch(leaf - 1);
+      } else {
+        __syncthreads();
+        X = reinterpret_cast<E*>(buf ? f.S.base : f.S2.base);  // the idle buffer
+      }
+    } else {
+      tile_load_start(S, mapV_p, f.bar, np, row0, h, 0, box_rows);  // the tile by TMA while T loads
+      load_square(st.t_leaf + leaf * np * np, f.T, np, ld);
+      if (!tile_load_finish(f.bar, phase[0], st.status, f.flag)) return;
+    }
     const int64_t rows_valid = (P.m - row0 < h) ? (P.m - row0) : h;
     if (!plain) {
       tri_mul<Ar>(f.T, ld, f.C, ld, f.M, ld, n, np, np, false);
@@ -214,10 +271,10 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
           for (int r = a + 1; r < n; ++r) Ar::fma_acc(v, tat<E>(S, r, a), f.C[r * ld + b]);
           v = Ar::fin(v);
         }
-        f.X[a * ld + b] = v;
+        X[a * ld + b] = v;
       }
       __syncthreads();
-      tri_mul<Ar>(f.T, ld, f.X, ld, f.M, ld, n, np, np, false);
+      tri_mul<Ar>(f.T, ld, X, ld, f.M, ld, n, np, np, false);
       __syncthreads();
       if (cown < n) {
         for (int r = gown; r < rows_valid; r += G) {
@@ -233,6 +290,7 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
       }
       __syncthreads();
     }
+    if (f.dbl) buf ^= 1;
   }
 }
 
