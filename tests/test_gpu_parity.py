@@ -324,19 +324,21 @@ def test_apply_bf16x3_panels(T):
     f.close()
 
 
-def test_apply_ozaki_column_major(T):
-    """The Ozaki Q^T B and Q B read and write B in a column-major handle's layout: bitwise the
-    row-major results."""
+@pytest.mark.parametrize("dtype,prec", [("float64", 2), ("float32", 0)])
+def test_apply_tc_column_major(T, dtype, prec):
+    """The tensor-core Q^T B and Q B (Ozaki in mode 2, bf16x3 in FP32 storage) read and write B in
+    a column-major handle's layout: bitwise the row-major results."""
     import torch
 
+    tdt = getattr(torch, dtype)
     m, n, k = 7000, 64, 70
     A_h = inputs.gaussian(m, n, inputs.seed_for(20, 1))
     B_h = inputs.gaussian(m, k, inputs.seed_for(20, 2))
-    A_row = torch.from_numpy(A_h).cuda()
-    A_col = torch.from_numpy(A_h.T.copy()).cuda().t()
-    f_row, f_col = T.Factorization(A_row, precision=2), T.Factorization(A_col, precision=2)
-    B_row = torch.from_numpy(B_h).cuda()
-    B_col = torch.from_numpy(B_h.T.copy()).cuda().t()
+    A_row = torch.from_numpy(A_h).to(tdt).cuda()
+    A_col = torch.from_numpy(A_h.T.copy()).to(tdt).cuda().t()
+    f_row, f_col = T.Factorization(A_row, precision=prec), T.Factorization(A_col, precision=prec)
+    B_row = torch.from_numpy(B_h).to(tdt).cuda()
+    B_col = torch.from_numpy(B_h.T.copy()).to(tdt).cuda().t()
     f_row.apply_qt(B_row)
     f_col.apply_qt(B_col)
     torch.cuda.synchronize()
@@ -345,7 +347,8 @@ def test_apply_ozaki_column_major(T):
     f_col.apply_q(B_col)
     torch.cuda.synchronize()
     assert torch.equal(B_col, B_row)
-    assert np.abs(B_row.cpu().numpy() - B_h).max() <= 1e-10
+    tol = 1e-10 if dtype == "float64" else 50 * n * U32 * np.abs(B_h).max()
+    assert np.abs(B_row.double().cpu().numpy() - torch.from_numpy(B_h).to(tdt).double().numpy()).max() <= tol
 
 
 @pytest.mark.parametrize("m,n,opts", [(20000, 128, {}), (5000 + 33, 65, {"leaf_h": 128}),
