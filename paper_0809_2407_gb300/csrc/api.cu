@@ -774,7 +774,7 @@ tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t
       return s;
     }
     b->smem_factor = std::max(b->smem_factor, tsqr::factor_smem_bytes(P));
-    b->smem_formq = std::max(b->smem_formq, tsqr::formq_smem_bytes(P));
+    b->smem_formq = std::max(b->smem_formq, tsqr::formq_smem_bytes(P, true));  // the chain kernel double-buffers
     for (int g = 0; g < P.chains; ++g) chain_work.push_back({i, g, 0});
   }
   // tree steps of the batched thin Q, by distance d from each item's root

@@ -20,22 +20,53 @@ __device__ __forceinline__ E& tat(const Tile& S, int r, int c) {
   return *reinterpret_cast<E*>(S.ptr(r, c));
 }
 
+// Lanes per output when there are fewer outputs than threads: the largest power of two up to 8
+// with outputs x lanes <= kThreads and a whole number of warps (the lanes of one output are
+// adjacent and combine their partial sums with shuffles).
+__device__ __forceinline__ int split_lanes(int outputs) {
+  int s = 1;
+  while (s < 8 && 2 * s * outputs <= kThreads && (2 * s * outputs) % 32 == 0) s *= 2;
+  return s;
+}
+
 // M (np x kb) = T * C (trans = false) or T^T * C (trans = true), T upper triangular n x n.
 template <class Ar>
 __device__ inline void tri_mul(const typename Ar::E* T, int ldt, const typename Ar::E* C, int ldc,
                                typename Ar::E* M, int ldm, int n, int np, int kb, bool trans) {
   using E = typename Ar::E;
-  for (int o = threadIdx.x; o < np * kb; o += kThreads) {
+  const int S = split_lanes(np * kb);
+  if (S == 1) {
+    for (int o = threadIdx.x; o < np * kb; o += kThreads) {
+      const int a = o / kb, b = o % kb;
+      E s = Ar::zero();
+      if (a < n) {
+        if (!trans) {
+          for (int p = a; p < n; ++p) Ar::fma_acc(s, T[a * ldt + p], C[p * ldc + b]);
+        } else {
+          for (int p = 0; p <= a; ++p) Ar::fma_acc(s, T[p * ldt + a], C[p * ldc + b]);
+        }
+      }
+      M[a * ldm + b] = Ar::fin(s);
+    }
+    return;
+  }
+  // few outputs: S adjacent lanes per output, each a strided part of the sum (one pass)
+  const int lS = __ffs(S) - 1;
+  const int o0 = threadIdx.x;
+  if (o0 < (np * kb) << lS) {
+    const int o = o0 >> lS, part = o0 & (S - 1);
     const int a = o / kb, b = o % kb;
     E s = Ar::zero();
     if (a < n) {
       if (!trans) {
-        for (int p = a; p < n; ++p) Ar::fma_acc(s, T[a * ldt + p], C[p * ldc + b]);
+        for (int p = a + part; p < n; p += S) Ar::fma_acc(s, T[a * ldt + p], C[p * ldc + b]);
       } else {
-        for (int p = 0; p <= a; ++p) Ar::fma_acc(s, T[p * ldt + a], C[p * ldc + b]);
+        for (int p = part; p <= a; p += S) Ar::fma_acc(s, T[p * ldt + a], C[p * ldc + b]);
       }
     }
-    M[a * ldm + b] = Ar::fin(s);
+    s = Ar::fin(s);
+    for (int off = 1; off < S; off <<= 1) s = Ar::add(s, Ar::shfl_xor(s, off));
+    if (part == 0) M[a * ldm + b] = s;
   }
 }
 
@@ -86,12 +117,14 @@ __host__ __device__ inline bool formq_double_buffered(const Plan& P) {
   return P.h > P.np && 1024 + 2 * tile + 3 * sq + 2 * 8 + 16 <= kFormqSmemCap;
 }
 
+// allow_dbl: the layout of a chain kernel built with double buffering (the tree steps and the
+// other chain kernels use the single-buffer layout).
 template <class E>
-__device__ inline FormQSmem<E> carve_formq(char* raw, const Plan& P) {
+__device__ inline FormQSmem<E> carve_formq(char* raw, const Plan& P, bool allow_dbl = false) {
   FormQSmem<E> f;
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   const size_t tile = (size_t)P.h * P.np * 8;
-  f.dbl = formq_double_buffered(P);
+  f.dbl = allow_dbl && formq_double_buffered(P);
   f.S = Tile{base, P.h};
   f.S2 = f.dbl ? Tile{base + tile, P.h} : f.S;
   f.ld = P.np + 1;
@@ -104,9 +137,10 @@ __device__ inline FormQSmem<E> carve_formq(char* raw, const Plan& P) {
   return f;
 }
 
-size_t formq_smem_bytes(const Plan& P) {
+size_t formq_smem_bytes(const Plan& P, bool allow_dbl) {
   const size_t tile = (size_t)P.h * P.np * 8, sq = (size_t)P.np * (P.np + 1) * 8;
-  return formq_double_buffered(P) ? 1024 + 2 * tile + 3 * sq + 2 * 8 + 16 : 1024 + tile + 4 * sq + 2 * 8 + 16;
+  return (allow_dbl && formq_double_buffered(P)) ? 1024 + 2 * tile + 3 * sq + 2 * 8 + 16
+                                                 : 1024 + tile + 4 * sq + 2 * 8 + 16;
 }
 
 // One level of the thin-Q broadcast (Sec. 4.1): node (level, idx) holds its block C of
@@ -166,14 +200,16 @@ __global__ void __launch_bounds__(kThreads, 1) formq_tree_kernel(const Plan P, c
 
 // Q rows of chain g, last leaf first.  chain step (V = [I; Y]): Q_rows = -Y M with M = T C,
 // then C -= M.  first leaf (V unit lower trapezoidal): Q_rows = [C; 0] - V (T (V_top^T C)).
-// With double buffering, the next leaf's tile (TMA) and T (register loads) are in flight while
-// the current leaf computes.
-template <class Ar>
+// With double buffering (kDbl, where two tiles fit), the next leaf's tile (TMA) and T (register
+// loads) are in flight while the current leaf computes.  It costs registers and shared memory,
+// so it pays where one block per SM is all that fits anyway (np = 64); narrower plans keep the
+// single-buffer kernel and two blocks per SM.
+template <class Ar, bool kDbl>
 __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Plan& P, const Store& st,
                                             typename Ar::Out* __restrict__ Q, int64_t ldq, int box_rows, int g,
                                             char* smem_raw) {
   using E = typename Ar::E;
-  FormQSmem<E> f = carve_formq<E>(smem_raw, P);
+  FormQSmem<E> f = carve_formq<E>(smem_raw, P, kDbl);
   const int tid = threadIdx.x;
   const int np = P.np, n = P.n, h = P.h, ld = f.ld;
   if (tid == 0) {
@@ -294,12 +330,12 @@ __device__ __forceinline__ void formq_chain(const CUtensorMap* mapV_p, const Pla
   }
 }
 
-template <class Ar>
+template <class Ar, bool kDbl>
 __global__ void __launch_bounds__(kThreads, 1)
     formq_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st,
                  typename Ar::Out* __restrict__ Q, int64_t ldq, int box_rows) {
   extern __shared__ char smem_raw[];
-  formq_chain<Ar>(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
+  formq_chain<Ar, kDbl>(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
 }
 
 // Batched thin Q: one tree step (item, node, level) per block, or one chain per block.
@@ -317,8 +353,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ char smem_raw[];
   const BatchWork w = work[blockIdx.x];
   const BatchItem& it = items[w.item];
-  formq_chain<Ar>(&it.mapV, it.plan, it.store, static_cast<typename Ar::Out*>(it.Q), it.ldq, it.box_rows, w.chain,
-                  smem_raw);
+  formq_chain<Ar, true>(&it.mapV, it.plan, it.store, static_cast<typename Ar::Out*>(it.Q), it.ldq, it.box_rows,
+                        w.chain, smem_raw);
 }
 
 template <class Ar>
@@ -675,13 +711,31 @@ template <class Ar>
 __device__ inline void wy_update(const Tile& S, bool plain, int h, int n, int np, typename Ar::E* B,
                                  typename Ar::E* C, const typename Ar::E* W2, int kb) {
   using E = typename Ar::E;
-  for (int o = threadIdx.x; o < h * kb; o += kThreads) {
-    const int r = o / kb, b = o % kb;
-    E acc = Ar::zero();
-    const int amax = plain ? (r < n ? r : n) : n;
-    for (int a = 0; a < amax; ++a) Ar::fma_acc(acc, tat<E>(S, r, a), W2[a * kb + b]);
-    if (plain && r < n) Ar::fma_acc(acc, Ar::from_int(1), W2[r * kb + b]);
-    B[o] = Ar::sub(B[o], Ar::fin(acc));
+  const int L = split_lanes(h * kb);
+  if (L == 1) {
+    for (int o = threadIdx.x; o < h * kb; o += kThreads) {
+      const int r = o / kb, b = o % kb;
+      E acc = Ar::zero();
+      const int amax = plain ? (r < n ? r : n) : n;
+      for (int a = 0; a < amax; ++a) Ar::fma_acc(acc, tat<E>(S, r, a), W2[a * kb + b]);
+      if (plain && r < n) Ar::fma_acc(acc, Ar::from_int(1), W2[r * kb + b]);
+      B[o] = Ar::sub(B[o], Ar::fin(acc));
+    }
+  } else {
+    // few outputs (narrow B): L adjacent lanes per row, each a strided part of the sum (one pass)
+    const int lL = __ffs(L) - 1;
+    const int o0 = threadIdx.x;
+    if (o0 < (h * kb) << lL) {
+      const int o = o0 >> lL, part = o0 & (L - 1);
+      const int r = o / kb, b = o % kb;
+      E acc = Ar::zero();
+      const int amax = plain ? (r < n ? r : n) : n;
+      for (int a = part; a < amax; a += L) Ar::fma_acc(acc, tat<E>(S, r, a), W2[a * kb + b]);
+      if (plain && r < n && part == 0) Ar::fma_acc(acc, Ar::from_int(1), W2[r * kb + b]);
+      acc = Ar::fin(acc);
+      for (int off = 1; off < L; off <<= 1) acc = Ar::add(acc, Ar::shfl_xor(acc, off));
+      if (part == 0) B[o] = Ar::sub(B[o], acc);
+    }
   }
   if (!plain)
     for (int o = threadIdx.x; o < np * kb; o += kThreads) C[o] = Ar::sub(C[o], W2[o]);
@@ -962,7 +1016,10 @@ static cudaError_t launch_form_q_t(const CUtensorMap& mapV, const Plan& P, const
                                    int box_rows, cudaStream_t stream) {
   typename Ar::Out* Q = static_cast<typename Ar::Out*>(Q_);
   const size_t smem = formq_smem_bytes(P);
-  cudaError_t e = cudaFuncSetAttribute(formq_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool dbl = (P.np == 64);  // the double-buffered chain kernel where it pays
+  const size_t smem_chain = formq_smem_bytes(P, dbl);
+  auto chain_kernel = dbl ? formq_kernel<Ar, true> : formq_kernel<Ar, false>;
+  cudaError_t e = cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_chain);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(formq_tree_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -971,7 +1028,7 @@ static cudaError_t launch_form_q_t(const CUtensorMap& mapV, const Plan& P, const
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  formq_kernel<Ar><<<P.chains, kThreads, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+  chain_kernel<<<P.chains, kThreads, smem_chain, stream>>>(mapV, P, st, Q, ldq, box_rows);
   return cudaGetLastError();
 }
 

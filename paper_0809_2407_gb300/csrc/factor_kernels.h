@@ -6,7 +6,8 @@
 namespace tsqr {
 
 size_t factor_smem_bytes(const Plan& P);
-size_t formq_smem_bytes(const Plan& P);
+// allow_dbl: the double-buffered chain kernel's layout where it fits (formq_double_buffered)
+size_t formq_smem_bytes(const Plan& P, bool allow_dbl = false);
 size_t apply_smem_bytes(const Plan& P, int kb);
 size_t formq_ozaki_smem_bytes(const Plan& P);
 bool ozaki_form_q_applies(const Plan& P);
