@@ -451,7 +451,9 @@ def test_full_size_properties(T, prec):
     """m = 2^22, n = 64, A = U Sigma V^T with kappa = 1 (the benchmark's workload and launch
     configuration).  At kappa = 1 the Cholesky factor of A^T A (a library routine on the Gram
     matrix) equals R to ~eps, which pins R elementwise; A = QR and Q^T Q = I are checked with
-    FP64 GEMMs on the device."""
+    FP64 GEMMs on the device.  Q^T b (the benchmark's k = 1) and Q^T B, Q B with 64 columns (on
+    the tensor cores in modes 2 and 3) are held to Q_thin^T B from an FP64 GEMM with the thin Q,
+    and to Q Q^T B = B."""
     import torch
 
     m, n = 1 << 22, 64
@@ -469,6 +471,20 @@ def test_full_size_properties(T, prec):
     be = (torch.linalg.norm(A - Q @ R) / torch.linalg.norm(A)).item()
     orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device="cuda") - Q.T @ Q).item()
     assert be <= TOL_BACK and orth <= TOL_ORTH
+    del A
+    for k in (1, 64):
+        B0 = torch.from_numpy(inputs.gaussian(m, k, inputs.seed_for(2, 100 + k))).cuda()
+        B = B0.clone()
+        f.apply_qt(B)
+        ref = Q.T @ B0
+        torch.cuda.synchronize()
+        assert f.status() == T.TSQR_OK
+        scale = torch.linalg.norm(B0, dim=0).max().item()
+        assert (B[:n] - ref).abs().max().item() <= 1e-12 * scale, (k, (B[:n] - ref).abs().max().item() / scale)
+        f.apply_q(B)
+        assert (B - B0).abs().max().item() <= 1e-12 * scale
+        del B0, B, ref
+    f.close()
 
 
 @pytest.mark.parametrize("precision", [0, 1])
