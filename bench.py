@@ -146,6 +146,50 @@ def cpu_oracle_sample(A_h, rows):
     return (f["factor"] + f["form_q"]) / dt / 1e9, dt
 
 
+def host_cpu():
+    """The host's CPU model and core count (context for the CPU lines)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:  # Arm hosts name the core in lscpu, not in /proc/cpuinfo
+        import subprocess
+
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if model is None:
+        import platform
+
+        model = platform.machine()
+    return {"model": model, "cpu_count": os.cpu_count()}
+
+
+def cpu_library_sample(torch, A_h, rows):
+    """torch.linalg.qr (LAPACK geqrf + orgqr) on the host cores, on the same rows as the oracle's
+    sample: a labelled library reference beside the oracle, not a target."""
+    X = torch.from_numpy(A_h[:rows].copy())
+    torch.linalg.qr(X)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        torch.linalg.qr(X)
+    dt = (time.perf_counter() - t0) / 3
+    f = flops(rows, A_h.shape[1])
+    return {"what": "torch.linalg.qr on the host (LAPACK), explicit Q and R", "threads": torch.get_num_threads(),
+            "value": (f["factor"] + f["form_q"]) / dt / 1e9, "unit": "GFLOP/s", "seconds": dt}
+
+
 def run_reference(args, rank, world):
     """The oracle on host cores, on bounded slices of the workload (rank 0 only)."""
     if rank != 0:
@@ -788,7 +832,8 @@ def main():
         rows = args.cpu_rows
         gf, dt = cpu_oracle_sample(A_h, rows)
         cpu = {"value": gf, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": "oracle QR + thin Q of the first %d rows of the same matrix (%.1f s)" % (rows, dt)}
+               "sample": "oracle QR + thin Q of the first %d rows of the same matrix (%.1f s)" % (rows, dt),
+               "host": host_cpu(), "library_cpu": cpu_library_sample(torch, A_h, rows)}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
