@@ -358,16 +358,16 @@ class Batch:
 _TUNE_CACHE = {}
 
 
-def tune_key(m, n, precision):
-    """Cache key: (log2 bucket of m, n rounded up to the padded width, precision)."""
+def tune_key(m, n, precision, dtype=TSQR_F64):
+    """Cache key: (log2 bucket of m, n rounded up to the padded width, precision, dtype code)."""
     mb = max(0, int(m).bit_length() - 1)
     np_ = 16
     while np_ < n:
         np_ *= 2
-    return (mb, np_, int(precision))
+    return (mb, np_, int(precision), int(dtype))
 
 
-def candidate_opts(m, n, precision=0):
+def candidate_opts(m, n, precision=0, dtype=TSQR_F64):
     """Plans the library accepts for an m x n problem: leaf height 64..1024, arity 2/4/8, flat
     chains (auto) or a pure tree (chain 1)."""
     out = []
@@ -376,22 +376,25 @@ def candidate_opts(m, n, precision=0):
             for chain in (0, 1):
                 o = Opts(leaf_h=h, chain=chain, arity=arity, precision=precision, inplace=0)
                 try:
-                    tsqr_workspace_size(TSQR_F64, m, n, o)
+                    tsqr_workspace_size(dtype, m, n, o)
                 except TsqrError:
                     continue
                 out.append(o)
     return out
 
 
-def autotune(m, n, precision=0, reps=2, proxy_rows=1 << 18, path=None):
+def autotune(m, n, precision=0, reps=2, proxy_rows=1 << 18, path=None, dtype=None):
     """Times factor + thin Q for each candidate plan on a seeded N(0,1) matrix of min(m, proxy_rows)
     rows and returns the fastest Opts, caching it by tune_key (and in the JSON file `path` if given).
+    dtype: torch.float64 (default) or torch.float32 (FP32 storage, precision 0).
     """
     import json
 
     import torch
 
-    key = tune_key(m, n, precision)
+    dtype = torch.float64 if dtype is None else dtype
+    code = TSQR_F32 if dtype == torch.float32 else TSQR_F64
+    key = tune_key(m, n, precision, code)
     if path and not _TUNE_CACHE and os.path.exists(path):
         with open(path) as fh:
             for k, v in json.load(fh).items():
@@ -400,9 +403,9 @@ def autotune(m, n, precision=0, reps=2, proxy_rows=1 << 18, path=None):
         return Opts(**_TUNE_CACHE[key])
     rows = int(min(m, proxy_rows))
     g = torch.Generator(device="cuda").manual_seed(20080809)
-    A = torch.randn((rows, n), dtype=torch.float64, device="cuda", generator=g)
+    A = torch.randn((rows, n), dtype=torch.float64, device="cuda", generator=g).to(dtype)
     best, best_ms = None, float("inf")
-    for o in candidate_opts(rows, n, precision):
+    for o in candidate_opts(rows, n, precision, code):
         times = []
         for _ in range(reps + 1):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

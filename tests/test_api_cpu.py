@@ -122,8 +122,10 @@ def test_autotune_candidates_and_key(lib):
     c = lib.candidate_opts(1 << 20, 64)
     assert len(c) >= 6
     assert all(o.leaf_h >= 64 for o in c)
-    assert lib.tune_key(1 << 20, 50, 0) == (20, 64, 0)
-    assert lib.tune_key(3 << 19, 9, 1) == (20, 16, 1)
+    assert lib.tune_key(1 << 20, 50, 0) == (20, 64, 0, lib.TSQR_F64)
+    assert lib.tune_key(3 << 19, 9, 1) == (20, 16, 1, lib.TSQR_F64)
+    assert lib.tune_key(3 << 19, 9, 0, lib.TSQR_F32) == (20, 16, 0, lib.TSQR_F32)
+    assert len(lib.candidate_opts(1 << 20, 64, 0, lib.TSQR_F32)) >= 6
 
 
 def test_panel_workspace(lib):

@@ -545,6 +545,14 @@ def test_autotune_returns_valid_plan(T):
     _, R, Q = run(T, A_h, leaf_h=o.leaf_h, chain=o.chain, arity=o.arity)
     check_against_oracle(A_h, R, Q)
     assert T.autotune(20000, 24) is not None  # cached
+    o32 = T.autotune(20000, 24, reps=1, proxy_rows=20000, dtype=torch.float32)  # FP32 storage, own key
+    A32 = torch.from_numpy(A_h).float().cuda()
+    f = T.Factorization(A32, leaf_h=o32.leaf_h, chain=o32.chain, arity=o32.arity)
+    Q = f.form_q().double()
+    torch.cuda.synchronize()
+    assert f.status() == T.TSQR_OK
+    assert torch.linalg.norm(torch.eye(24, dtype=torch.float64, device="cuda") - Q.T @ Q).item() <= 5e-5
+    f.close()
 
 
 # ---- FP32 storage (TSQR_F32): FP32-level bar, 5e-5 on backward error and orthogonality -------
