@@ -57,9 +57,11 @@ typedef enum {
 
 /* TSQR_F64: A, R, Q and B are binary64, arithmetic per tsqr_opts_t.precision.
  * TSQR_F32: A, R, Q and B are binary32 and every operation is binary32 (the FP32-level form of
- * the precision forms: backward error and loss of orthogonality of order n * 2^-24).  A is
- * widened into the workspace first (it is never overwritten: inplace is not supported), and
- * precision must be 0.  Every call takes both; tsqr_backward then works in the same type. */
+ * the precision forms: backward error and loss of orthogonality of order n * 2^-24); for n in
+ * 33..64 with leaf_h <= 128 the thin Q's Y M and, from 32 columns of B, Q^T B / Q B's Y^T B and
+ * Y M run on the tensor cores as bf16x3 term products with FP32 accumulation.  A is widened
+ * into the workspace first (it is never overwritten: inplace is not supported), and precision
+ * must be 0.  Every call takes both; tsqr_backward then works in the same type. */
 typedef enum { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype_t;
 /* TSQR_COL_MAJOR: n <= 64, not with inplace; tsqr_backward and batches take row-major only. */
 typedef enum { TSQR_ROW_MAJOR = 0, TSQR_COL_MAJOR = 1 } tsqr_layout_t;
@@ -77,12 +79,14 @@ typedef struct {
                             the FP32 pipe.  Magnitudes of A's and B's nonzero entries should lie
                             in about [2^-100, 2^100]; the stored factors (and A, with inplace)
                             then hold (hi, lo) FP32 pairs in each 8-byte slot.
-                        2 = Ozaki WY: native FP64 reflectors, T and tree; the thin Q's compact-WY
-                            products T C and Y M as Ozaki splits (8 slices of 7 bits in bf16,
-                            exact FP32 group sums) on the tensor cores (n in 33..64, leaf_h <= 128;
-                            other shapes run mode 0).
-                        3 = double-float factorization and Q^T B / Q B, thin Q as in mode 2
-                            (other shapes run mode 1).
+                        2 = Ozaki WY: native FP64 reflectors, T and tree; the compact-WY
+                            products of the thin Q (T C, Y M) and of Q^T B / Q B with at least 32
+                            columns of B (Y^T B, W^T T, Y M) as Ozaki splits (8 slices of 7 bits
+                            in bf16, exact FP32 group sums) on the tensor cores (n in 33..64,
+                            leaf_h <= 128; other shapes and narrower B run mode 0).
+                        3 = double-float factorization, and Q^T B / Q B with fewer than 32
+                            columns; the tensor-core products as in mode 2 (other shapes run
+                            mode 1).
                         Batches run mode 2 as 0 and mode 3 as 1. */
   int32_t inplace;   /* nonzero: the leaf reflectors overwrite A (Sec. 4.2 storage) and A's
                         upper triangles hold intermediate R factors; zero: A is read only */
