@@ -8,7 +8,10 @@
 // for Q^T, and the same with T in place of T^T for Q.
 //
 // Every kernel is a template on the arithmetic policy (arith.cuh); the factors in the
-// workspace are in that policy's element format, B and Q are FP64 at the boundary.
+// workspace are in that policy's element format, and B and Q are in the caller's type (FP64,
+// or FP32 with FP32 storage) and layout.  The tensor-core chain kernels of Q^T B / Q B live in
+// apply_ozaki.cu (precision modes 2 and 3) and apply_bf16x3.cu (FP32 storage); their tree
+// levels run here.
 #include "arith.cuh"
 #include "factor_kernels.h"
 #include "ozaki_pass.cuh"
