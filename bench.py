@@ -134,16 +134,28 @@ def make_input(m, n):
 
 
 def cpu_oracle_sample(A_h, rows):
-    """Times the oracle (QR + thin Q) on the first `rows` rows; returns (GFLOP/s, seconds)."""
+    """Times the oracle on the first `rows` rows, the step of the GPU line (QR, thin Q and Q^T b
+    through the stored reflectors); returns (GFLOP/s, seconds)."""
+    import numpy as np
+
     import oracle
 
     oracle._load()
     S = A_h[:rows].copy()
+    b = np.random.default_rng(5).standard_normal((rows, 1))
     t0 = time.perf_counter()
-    oracle.qr(S, want_q=True)
+    res = oracle.qr(S, want_q=True)
+    oracle.apply_qt(res["V"], res["tau"], b)
     dt = time.perf_counter() - t0
-    f = flops(rows, S.shape[1])
-    return (f["factor"] + f["form_q"]) / dt / 1e9, dt
+    return sum(flops(rows, S.shape[1]).values()) / dt / 1e9, dt
+
+
+def main_config(m, n, precision, world):
+    """The benchmark line's config (shared by the GPU and reference arms)."""
+    return {"workload": "tsqr factor + form_q + apply_qt(k=1), fp64, m=%d n=%d, A=U S V^T kappa=1" % (m, n),
+            "m": m, "n": n, "k": 1, "leaf_h": None, "chain": "auto", "arity": 2, "precision": precision,
+            "l2": "inputs larger than L2 (A is %.1f GB)" % (8.0 * m * n / 1e9),
+            "parallelism": "replicas" if world > 1 else "single-gpu"}
 
 
 def host_cpu():
@@ -205,17 +217,16 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         _, dt = cpu_oracle_sample(A_h, rows)
         times.append(dt)
-    f = flops(rows, n)
-    per = f["factor"] + f["form_q"]
+    per = sum(flops(rows, n).values())
     tot = sum(times)
     value = per * len(times) / tot / 1e9
     return {"metric": METRIC, "value": value, "unit": "GFLOP/s", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "tsqr fp64 usv kappa=1, n=%d; oracle on a %d-row slice per step" % (n, rows),
-                       "m": m, "n": n},
+            "config": main_config(m, n, 0, world),
             "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": "oracle QR + thin Q of the first %d rows x %d columns, per step" % (rows, n)},
+                             "sample": "oracle QR, thin Q and Q^T b of an A = U S V^T (kappa = 1) of %d rows x %d "
+                                       "columns from the workload's generator, per step" % (rows, n)},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -832,17 +843,14 @@ def main():
         rows = args.cpu_rows
         gf, dt = cpu_oracle_sample(A_h, rows)
         cpu = {"value": gf, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": "oracle QR + thin Q of the first %d rows of the same matrix (%.1f s)" % (rows, dt),
+               "sample": "oracle QR, thin Q and Q^T b of the first %d rows of the same matrix (%.1f s)" % (rows, dt),
                "host": host_cpu(), "library_cpu": cpu_library_sample(torch, A_h, rows)}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32" if args.fp32 else {0: "f64", 1: "f32x2", 2: "f64", 3: "f32x2"}[args.precision], "data": "synthetic",
-               "config": {"workload": "tsqr factor + form_q + apply_qt(k=1), fp64, m=%d n=%d, A=U S V^T kappa=1"
-                                      % (m, n), "m": m, "n": n, "k": 1, "leaf_h": None, "chain": "auto",
-                          "arity": 2, "precision": args.precision, "l2": "inputs larger than L2 (A is %.1f GB)" % (8.0 * m * n / 1e9),
-                          "parallelism": "replicas" if world > 1 else "single-gpu"},
+               "config": main_config(m, n, args.precision, world),
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
                "roofline": roofline, "precision_forms": forms, "apply_wide": apply_wide, "batched": batched,
