@@ -13,6 +13,17 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long-running CPU test")
 
 
+def pytest_collection_modifyitems(config, items):
+    """A GPU test that stops progressing ends its process after 10 minutes (the longest takes
+    seconds) instead of holding the run: pytest-timeout's thread method, which also works while
+    the main thread waits inside a CUDA call.  Without the plugin nothing changes."""
+    if not config.pluginmanager.hasplugin("timeout"):
+        return
+    for item in items:
+        if item.get_closest_marker("gpu") is not None and item.get_closest_marker("timeout") is None:
+            item.add_marker(pytest.mark.timeout(600, method="thread"))
+
+
 @pytest.fixture(scope="session")
 def oracle_mod():
     import oracle
