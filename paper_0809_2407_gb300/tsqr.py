@@ -7,8 +7,20 @@ CPU or PyTorch fallback.
 
 Low level (same names as the C-ABI): ``tsqr_workspace_size``, ``tsqr_factor``,
 ``tsqr_apply_qt``, ``tsqr_apply_q``, ``tsqr_form_q``, ``tsqr_status_poll``,
-``tsqr_handle_info``, ``tsqr_destroy``.  Convenience on torch tensors: ``Factorization`` and
-``qr``.
+``tsqr_handle_info``, ``tsqr_destroy``, the batch calls ``tsqr_batch_*`` and
+``tsqr_backward``.  Convenience on torch tensors: ``Factorization`` (one matrix), ``Batch``
+(many matrices in one launch, capturable in a CUDA graph), ``qr_autograd`` (differentiable QR)
+and ``autotune`` (plan search, cached per shape bucket).
+
+Example::
+
+    import torch
+    from paper_0809_2407_gb300 import tsqr
+    A = torch.randn(1 << 20, 64, dtype=torch.float64, device="cuda")
+    f = tsqr.Factorization(A)           # R in f.R, the implicit Q in the workspace
+    Q = f.form_q()                      # explicit thin Q
+    B = torch.randn(1 << 20, 64, dtype=torch.float64, device="cuda")
+    f.apply_qt(B)                       # B <- Q^T B in place (rows 0..63: Q_thin^T B)
 """
 import ctypes
 import os
