@@ -116,6 +116,9 @@ typedef struct {
   int32_t panels;         /* 64-column panels of the factorization (1 when n <= 64) */
   int32_t dtype;          /* tsqr_dtype_t of A, R, Q and B */
   int32_t layout;         /* tsqr_layout_t of A, R, Q and B */
+  const int32_t* status;  /* the device status word tsqr_status_poll reads (in the workspace;
+                             bit 0: a bounded device wait gave up), so that tests can drive that
+                             path from the host; the first panel's when panels > 1 */
 } tsqr_info_t;
 
 /* Bytes of device workspace tsqr_factor needs for an m x n factorization with `opts`

@@ -588,6 +588,7 @@ tsqr_status_t tsqr_handle_info(tsqr_handle_t h, tsqr_info_t* info) {
   info->node_y = h->st.node_y;
   info->node_tau = h->st.node_tau;
   info->node_t = h->st.node_t;
+  info->status = h->st.status;
   info->signs = h->st.signs;
   return TSQR_OK;
 }

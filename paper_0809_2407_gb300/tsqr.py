@@ -51,7 +51,8 @@ class Info(ctypes.Structure):
                 ("v", ctypes.c_void_p), ("ldv", ctypes.c_int64),
                 ("tau_leaf", ctypes.c_void_p), ("t_leaf", ctypes.c_void_p), ("node_y", ctypes.c_void_p),
                 ("node_tau", ctypes.c_void_p), ("node_t", ctypes.c_void_p), ("signs", ctypes.c_void_p),
-                ("panels", ctypes.c_int32), ("dtype", ctypes.c_int32), ("layout", ctypes.c_int32)]
+                ("panels", ctypes.c_int32), ("dtype", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("status", ctypes.c_void_p)]
 
 
 class TsqrError(RuntimeError):

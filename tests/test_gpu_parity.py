@@ -784,6 +784,26 @@ def test_extreme_scaling(T, scale_exp, prec):
     assert np.linalg.norm((R - ref["R"]) * s) / np.linalg.norm(ref["R"] * s) <= TOL_R
 
 
+def test_timeout_flag_reaches_the_host(T):
+    """Failure detection without a GPU fault: the status word that a bounded device wait sets
+    when it gives up is set here from the host; tsqr_status_poll then reports TSQR_ERR_TIMEOUT,
+    and clearing the word restores TSQR_OK.  The factorization itself ran normally."""
+    import torch
+
+    A = torch.from_numpy(inputs.gaussian(4096, 16, inputs.seed_for(24, 0))).cuda()
+    f = T.Factorization(A, leaf_h=256, chain=1)
+    torch.cuda.synchronize()
+    assert f.status() == T.TSQR_OK
+    off = f.info().status - f.work.data_ptr()
+    assert 0 <= off and off + 4 <= f.work.numel() and off % 4 == 0
+    word = f.work[off:off + 4].view(torch.int32)
+    word.fill_(1)
+    assert f.status() == T.TSQR_ERR_TIMEOUT
+    word.zero_()
+    assert f.status() == T.TSQR_OK
+    f.close()
+
+
 def test_nan_propagates_without_fault(T):
     """NaN in A propagates to R (no check, no trap); the device status word stays clear."""
     A_h = inputs.gaussian(2000, 16, 99)

@@ -353,3 +353,18 @@ def test_oracle_mutants(oracle_mod):
             assert src.count(old) == 1, name
             so = _build_mutant(src.replace(old, new), name, td)
             assert not _pins_pass(so), "pins missed planted mistake %s" % name
+
+
+def test_householder_stability_contrast_with_cholesky_qr(oracle_mod):
+    """Householder QR is unconditionally stable: its Q stays orthonormal to O(u) whatever
+    kappa(A) (Sec. 5), while CholeskyQR (R from the Cholesky factor of A^T A, Q = A R^-1; the
+    paper's comparison) loses orthogonality like kappa^2 u.  At kappa = 1e6 the two differ by
+    many orders of magnitude."""
+    from paper_0809_2407_gb300 import inputs
+
+    A = inputs.usv(4000, 20, 6.0, inputs.seed_for(30, 1))
+    ref = oracle_mod.qr(A)
+    assert oracle_mod.orthogonality(ref["Q"]) <= 1e-13
+    Rc = np.linalg.cholesky(A.T @ A).T
+    Qc = np.linalg.solve(Rc.T, A.T).T
+    assert oracle_mod.orthogonality(Qc) >= 1e-6
