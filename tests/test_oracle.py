@@ -368,3 +368,41 @@ def test_householder_stability_contrast_with_cholesky_qr(oracle_mod):
     Rc = np.linalg.cholesky(A.T @ A).T
     Qc = np.linalg.solve(Rc.T, A.T).T
     assert oracle_mod.orthogonality(Qc) >= 1e-6
+
+
+def test_paper_p4_binary_and_flat_trees(oracle_mod):
+    """The paper's P = 4 examples (Sec. 2): A in four row blocks, each factored locally; the
+    binary tree combines R_0 with R_1 and R_2 with R_3, then the two results (eq. par4:final), and
+    the flat tree folds the blocks one by one into a running R (eq. seq4:final).  Both reach the
+    QR of the whole matrix: the same R after sign normalisation, and Q from the tree factors
+    reproduces A."""
+    from paper_0809_2407_gb300 import inputs
+
+    m, n, P = 400, 6, 4
+    A = inputs.gaussian(m, n, inputs.seed_for(31, 0))
+    blocks = np.split(A, P)
+    whole = oracle_mod.qr(A)
+
+    def R_of(X):
+        return oracle_mod.qr(X, want_q=False)["R"]
+
+    # binary: level 1 pairs (0,1) and (2,3), level 2 the root
+    R01 = R_of(np.vstack([R_of(blocks[0]), R_of(blocks[1])]))
+    R23 = R_of(np.vstack([R_of(blocks[2]), R_of(blocks[3])]))
+    R_bin = R_of(np.vstack([R01, R23]))
+    # flat: R <- QR([R; A_k]) for k = 1, 2, 3
+    R_flat = R_of(blocks[0])
+    for k in range(1, P):
+        R_flat = R_of(np.vstack([R_flat, blocks[k]]))
+    tol = 1e-12 * np.abs(whole["R"]).max()
+    assert np.abs(R_bin - whole["R"]).max() <= tol
+    assert np.abs(R_flat - whole["R"]).max() <= tol
+    # Q of the binary tree: block-diagonal leaf factors times the node factors, applied to [I; 0]
+    leaf = [oracle_mod.qr(b) for b in blocks]
+    n1 = [oracle_mod.qr(np.vstack([leaf[0]["R"], leaf[1]["R"]])), oracle_mod.qr(np.vstack([leaf[2]["R"], leaf[3]["R"]]))]
+    root = oracle_mod.qr(np.vstack([n1[0]["R"], n1[1]["R"]]))
+    Qroot = root["Q"]                                    # 2n x n
+    Q1 = [n1[i]["Q"] @ Qroot[i * n:(i + 1) * n] for i in range(2)]           # 2n x n each
+    Q = np.vstack([leaf[2 * i + j]["Q"] @ Q1[i][j * n:(j + 1) * n] for i in range(2) for j in range(2)])
+    assert np.abs(Q @ root["R"] - A).max() <= 1e-12 * np.abs(A).max()
+    assert np.abs(Q - whole["Q"]).max() <= 1e-12
