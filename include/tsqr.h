@@ -214,9 +214,18 @@ tsqr_status_t tsqr_batch_destroy(tsqr_batch_t b);
  * (cudaGetSymbolAddress); make that first call before any stream capture starts.  Calls share
  * the array: each clears what must start at zero, and calls that overlap on the GPU (on
  * streams with no ordering between them) race and give wrong results.  The implicit Q is not
- * kept, so there is no handle. */
+ * kept, so there is no handle.  The array's address is kept for the life of the process: do not
+ * call this on a device after cudaDeviceReset.  If a device-side wait gives up (about one second
+ * on a TMA copy; no fault, no trap), R is filled with NaN and the array's status word is set;
+ * tsqr_noalloc_status_poll reports it. */
 tsqr_status_t tsqr_factor_r_noalloc(int64_t m, int64_t n, const void* dA, int64_t lda, void* dR, int64_t ldr,
                                     tsqr_stream_t stream);
+/* Outcome of the latest tsqr_factor_r_noalloc on the current device: waits for `stream` (the
+ * stream that call used), then reads the static array's status word.  TSQR_OK, or
+ * TSQR_ERR_TIMEOUT when a device-side wait gave up (R then holds NaN).  The next
+ * tsqr_factor_r_noalloc clears the word.  If status_word is not NULL it receives the word's
+ * device address (4 bytes; tests set it to check this path).  Allocates nothing. */
+tsqr_status_t tsqr_noalloc_status_poll(tsqr_stream_t stream, void** status_word);
 
 /* Frees the host handle (the workspace stays the caller's). NULL is a no-op. */
 tsqr_status_t tsqr_destroy(tsqr_handle_t h);

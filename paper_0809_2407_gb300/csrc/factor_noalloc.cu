@@ -10,10 +10,17 @@
 // not kept, so the leaf reflectors and T factors are never written.
 //
 // The array's address is taken once per device with cudaGetSymbolAddress, on the first call
-// made with that device current; make that first call before any stream capture begins.  All
-// calls on a device share the array and it keeps the previous call's contents: each call
-// clears the counters and status word it needs on its stream, and calls that overlap on the
-// GPU (different streams, no ordering between them) race on the array.
+// made with that device current; make that first call before any stream capture begins.  The
+// address is kept for the life of the process, so the entry point must not be used on a device
+// after cudaDeviceReset (the library's device array may then live elsewhere).  All calls on a
+// device share the array and it keeps the previous call's contents: each call clears the
+// counters and status word it needs on its stream, and calls that overlap on the GPU
+// (different streams, no ordering between them) race on the array.
+//
+// A device-side wait that gives up (about one second on a TMA copy) sets the status word in
+// the array and makes its block fill R with NaN before it returns: that block then never
+// reaches its parent in the tree, so no other block writes R and the NaN stays.
+// tsqr_noalloc_status_poll reads the word back.
 #include <mutex>
 
 #include "factor_kernels.h"
@@ -95,7 +102,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int64_t leaf = l0; leaf < l1; ++leaf) {
     const bool plain = (leaf == l0);
     const int dst = plain ? 0 : np;
-    if (!tile_load(S, &mapA, bar, phase, np, leaf * h, h, dst, box_rows, status, flag)) return;
+    if (!tile_load(S, &mapA, bar, phase, np, leaf * h, h, dst, box_rows, status, flag)) {
+      // no R can be produced: this block never arrives at its parent, so the root is never
+      // factored and nothing else writes R_out; mark R as invalid for the caller
+      const double qnan = __longlong_as_double(0x7FF8000000000000LL);
+      for (int i = tid; i < n * n; i += kThreads) R_out[(int64_t)(i / n) * ldr + (i % n)] = qnan;
+      return;
+    }
     stacked_qr<ArithF64>(S, plain ? PLAIN : CHAIN, dst + h, np, n, tau_s, nullptr, red, dvec, sc);
     if (plain) {
       for (int i = tid; i < np * np; i += kThreads) {
@@ -164,7 +177,9 @@ extern "C" tsqr_status_t tsqr_factor_r_noalloc(int64_t m, int64_t n, const void*
   tsqr_status_t s = internal_make_plan(m, n, nullptr, &P);
   if (s != TSQR_OK) return s;
   if (noalloc_layout(P).total > kStaticScratchBytes) {
-    // fewer, longer chains until the nodes' R factors fit the static scratch
+    // fewer, longer chains until the nodes' R factors fit the static scratch.  The default plan's
+    // tree is binary, so it has fewer than 2 x chains nodes in all (chains + chains/2 + ...):
+    // 2 x chains node R factors bound the scratch; the check below re-verifies the layout.
     const size_t per_node = (size_t)P.np * P.np * 8;
     const int64_t max_chains = (int64_t)((kStaticScratchBytes - 4096) / per_node / 2);
     if (max_chains < 1) return internal_fail(TSQR_ERR_UNSUPPORTED, "n too large for the 8 MiB static scratch");
@@ -194,5 +209,21 @@ extern "C" tsqr_status_t tsqr_factor_r_noalloc(int64_t m, int64_t n, const void*
                                                       box_rows);
   e = cudaGetLastError();
   if (e != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
+  return TSQR_OK;
+}
+
+extern "C" tsqr_status_t tsqr_noalloc_status_poll(tsqr_stream_t stream, void** status_word) {
+  using namespace tsqr;
+  void* scratch = nullptr;
+  tsqr_status_t s = scratch_address(&scratch);
+  if (s != TSQR_OK) return s;
+  int* word = static_cast<int*>(scratch);  // NoallocLayout::status is offset 0
+  if (status_word) *status_word = word;
+  int v = 0;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&v, word, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return internal_fail(TSQR_ERR_CUDA, cudaGetErrorString(e));
+  if (v & kStatusTimeout) return internal_fail(TSQR_ERR_TIMEOUT, "a device-side bounded wait timed out; R holds NaN");
   return TSQR_OK;
 }

@@ -34,8 +34,8 @@ TSQR_ROW_MAJOR, TSQR_COL_MAJOR = 0, 1
 
 EXPORTED = ("tsqr_workspace_size", "tsqr_factor", "tsqr_apply_qt", "tsqr_apply_q", "tsqr_form_q",
             "tsqr_status_poll", "tsqr_handle_info", "tsqr_destroy", "tsqr_status_string", "tsqr_last_error",
-            "tsqr_factor_r_noalloc", "tsqr_batch_workspace_size", "tsqr_batch_create", "tsqr_batch_factor",
-            "tsqr_batch_form_q", "tsqr_batch_status_poll", "tsqr_batch_destroy", "tsqr_backward")
+            "tsqr_factor_r_noalloc", "tsqr_noalloc_status_poll", "tsqr_batch_workspace_size", "tsqr_batch_create",
+            "tsqr_batch_factor", "tsqr_batch_form_q", "tsqr_batch_status_poll", "tsqr_batch_destroy", "tsqr_backward")
 
 
 class Opts(ctypes.Structure):
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
     lib.tsqr_handle_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.tsqr_destroy.argtypes = [vp]
     lib.tsqr_factor_r_noalloc.argtypes = [i64, i64, vp, i64, vp, i64, vp]
+    lib.tsqr_noalloc_status_poll.argtypes = [vp, ctypes.POINTER(vp)]
     i32, pi64, pvp = ctypes.c_int32, ctypes.POINTER(i64), ctypes.POINTER(vp)
     lib.tsqr_batch_workspace_size.argtypes = [ctypes.c_int, i32, pi64, pi64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
     lib.tsqr_batch_create.argtypes = [ctypes.c_int, i32, pi64, pi64, pvp, pi64, pvp, pi64, pvp, pi64, vp, sz,
@@ -167,6 +168,14 @@ def tsqr_destroy(h):
 def tsqr_factor_r_noalloc(m, n, dA, lda, dR, ldr, stream):
     """R only, using the library's static device scratch: for callers that cannot allocate."""
     _check(load().tsqr_factor_r_noalloc(m, n, dA, lda, dR, ldr, stream))
+
+
+def tsqr_noalloc_status_poll(stream):
+    """Status of the latest tsqr_factor_r_noalloc on the current device (waits for `stream`):
+    returns (status code, device address of the static scratch's status word)."""
+    word = ctypes.c_void_p()
+    st = load().tsqr_noalloc_status_poll(stream, ctypes.byref(word))
+    return st, word.value
 
 
 def tsqr_backward(h, dQbar, ldqb, dRbar, ldrb, dR, ldr, dAbar, ldab, stream):

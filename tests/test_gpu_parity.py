@@ -69,6 +69,7 @@ def check_against_oracle(A_h, R, Q, unique=True, precision=0):
     if unique:
         ref = oracle.qr(A_h)
         assert np.linalg.norm(R - ref["R"]) / np.linalg.norm(ref["R"]) <= TOL_R
+        assert np.abs(R - ref["R"]).max() <= TOL_R * np.abs(ref["R"]).max()  # and per element
         kappa = np.linalg.cond(ref["R"])
         n = A_h.shape[1]
         assert np.abs(Q - ref["Q"]).max() <= max(1e-13, 50 * kappa * n * UNIT[precision])
@@ -445,6 +446,43 @@ def test_virtual_ranks(T):
         Rs.append(Rp)
     _, R_two, _ = run(T, np.vstack(Rs), leaf_h=16, chain=1)
     assert np.abs(R_two - R_one).max() <= 1e-12 * np.abs(R_one).max()
+
+
+@pytest.fixture(scope="module")
+def full_size_oracle():
+    """The oracle on the benchmark's own matrix (m = 2^22, n = 64, A = U Sigma V^T with kappa = 1,
+    the benchmark's seed) and on b: R and the top n rows of Q^T b, sign-normalised.  Computed
+    once per module: about a minute of single-threaded FP64 work on the host."""
+    m, n = 1 << 22, 64
+    A_h = inputs.usv(m, n, 0.0, inputs.seed_for(2, 0))
+    b = inputs.gaussian(m, 1, inputs.seed_for(2, 101))[:, 0]
+    ref = oracle.qr(A_h, want_q=False)
+    qtb = ref["D"] * oracle.apply_qt(ref["V"], ref["tau"], b)[:n]
+    return A_h, b, ref["R"], qtb
+
+
+@pytest.mark.timeout(1500, method="thread")
+def test_full_size_against_oracle(T, full_size_oracle, prec):
+    """Parity at the benchmark's configuration: every FP64-storage precision form's R equals the
+    oracle's per element within 1e-10 of max |R|, and its Q^T b (top n rows) the oracle's within
+    1e-12 of ||b||, on the benchmark's matrix and launch configuration."""
+    import torch
+
+    A_h, b_h, R_ref, qtb_ref = full_size_oracle
+    n = A_h.shape[1]
+    A = torch.from_numpy(A_h).cuda()
+    f = T.Factorization(A, precision=prec)
+    b = torch.from_numpy(b_h.copy()).cuda().reshape(-1, 1)
+    f.apply_qt(b)
+    torch.cuda.synchronize()
+    assert f.status() == T.TSQR_OK
+    R = f.R.cpu().numpy()
+    qtb = b[:n, 0].cpu().numpy()
+    f.close()
+    del A, b
+    assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) >= 0.0)
+    assert np.abs(R - R_ref).max() <= TOL_R * np.abs(R_ref).max()
+    assert np.abs(qtb - qtb_ref).max() <= 1e-12 * np.linalg.norm(b_h)
 
 
 def test_full_size_properties(T, prec):
