@@ -70,8 +70,71 @@ def load_peaks():
 # written once, so traffic grows in proportion to m.  Only valid for the kernel as captured.
 FACTOR_F64_TRAFFIC = {(4194304, 64): 8 * 700.40e6}
 
-# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s).
+# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s);
+# the fallback when the live probe below cannot run.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# Thin-Q tensor-core products per useful FP64 multiply-add: the Ozaki split runs 36 bf16 slice
+# products, bf16x3 six term products (on the chains' Y M; the FP32 form's T C stays on the FP32 pipe).
+OZAKI_PRODUCTS, BF16X3_PRODUCTS = 36, 6
+
+
+def measure_pipe_peaks():
+    """FP64 and FP32 FMA rates of this GPU in TFLOP/s, measured now by the probe library
+    (independent FMA chains on every SM); None where the probe cannot run."""
+    import ctypes
+
+    from paper_0809_2407_gb300 import build
+
+    try:
+        lib = ctypes.CDLL(build.PROBE_LIB)
+    except OSError:
+        return {"fp64_tflops": None, "fp32_tflops": None}
+    lib.tsqr_probe_fma_tflops.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for name, fp32, iters in (("fp64_tflops", 0, 20000), ("fp32_tflops", 1, 1000000)):
+        v = ctypes.c_double(0.0)
+        out[name] = v.value if lib.tsqr_probe_fma_tflops(fp32, iters, ctypes.byref(v)) == 0 else None
+    out["how"] = ("8 independent FMA chains per thread, 8 blocks x 256 threads per SM, CUDA events over the "
+                  "second of two launches (about 0.1 s each)")
+    return out
+
+
+def form_roofline(kind, fl, kernel_ms, ab, peaks, pipes):
+    """Roofline of one precision form's step: the dominant kernel against the unit that binds it
+    (FP64 pipe for native FP64, FP32 pipe for FP32 storage and double-float arithmetic), with its
+    HBM view; for forms whose thin Q runs on the tensor cores, that kernel's tensor view: the bf16
+    slice or term products it executes (useful flops x products per multiply-add) against the
+    measured bf16 peak."""
+    dom = max(("factor", "form_q"), key=lambda k: kernel_ms[k])
+    t = kernel_ms[dom] / 1e3
+    achieved = fl[dom] / t / 1e12
+    if kind in ("fp64", "ozaki_wy", "ozaki_wy_blocked"):
+        measured = pipes.get("fp64_tflops")
+        peak, src = measured or FP64_PEAK_TFLOPS, "FP64 pipe"
+    else:
+        measured = pipes.get("fp32_tflops")
+        peak, src = measured, "FP32 pipe"
+        if kind in ("double_float", "df_ozaki_wy"):
+            src += ", useful FP64-equivalent flops (a double-float multiply-add takes about 10 FP32 instructions)"
+    src += ": measured in this run" if measured else ": nominal"
+    hbm = peaks.get("hbm_gbs")
+    r = {"bound": "alu", "kernel": dom + "_kernel", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+         "frac": (achieved / peak) if peak else None, "peak_source": src,
+         "hbm_view": {"achieved_gbs": ab[dom] / t / 1e9, "peak_gbs": hbm,
+                      "frac_of_measured": (ab[dom] / t / 1e9 / hbm) if hbm else None}}
+    prod = {"ozaki_wy": OZAKI_PRODUCTS, "df_ozaki_wy": OZAKI_PRODUCTS, "ozaki_wy_blocked": OZAKI_PRODUCTS,
+            "fp32": BF16X3_PRODUCTS, "fp32_blocked": BF16X3_PRODUCTS}.get(kind)
+    bf16 = peaks.get("bf16_tflops")
+    if prod:
+        tq = kernel_ms["form_q"] / 1e3
+        # fp32: the tensor cores take Y M, half of the thin Q's multiply-adds
+        share = 0.5 if kind.startswith("fp32") else 1.0
+        tc = fl["form_q"] * share * prod / tq / 1e12
+        r["tensor_view"] = {"kernel": "form_q (chains)", "products_per_fma": prod, "share_on_tensor_cores": share,
+                            "achieved_bf16_tflops": tc, "peak_bf16_tflops": bf16,
+                            "frac_of_measured": (tc / bf16) if bf16 else None}
+    return r
 
 
 class ClockSampler:
@@ -133,21 +196,30 @@ def make_input(m, n):
     return inputs.usv(m, n, 0.0, inputs.seed_for(2, 0))
 
 
-def cpu_oracle_sample(A_h, rows):
+def cpu_oracle_sample(A_h, rows, openmp=False):
     """Times the oracle on the first `rows` rows, the step of the GPU line (QR, thin Q and Q^T b
-    through the stored reflectors); returns (GFLOP/s, seconds)."""
+    through the stored reflectors); returns (GFLOP/s, seconds, threads).  openmp: the oracle's
+    -fopenmp build (bitwise the serial results) on all host cores."""
     import numpy as np
 
     import oracle
 
-    oracle._load()
-    S = A_h[:rows].copy()
-    b = np.random.default_rng(5).standard_normal((rows, 1))
-    t0 = time.perf_counter()
-    res = oracle.qr(S, want_q=True)
-    oracle.apply_qt(res["V"], res["tau"], b)
-    dt = time.perf_counter() - t0
-    return sum(flops(rows, S.shape[1]).values()) / dt / 1e9, dt
+    threads = 1
+    if openmp:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        threads = int(os.environ["OMP_NUM_THREADS"])
+        oracle.set_variant("openmp")
+    try:
+        oracle._load()
+        S = A_h[:rows].copy()
+        b = np.random.default_rng(5).standard_normal((rows, 1))
+        t0 = time.perf_counter()
+        res = oracle.qr(S, want_q=True)
+        oracle.apply_qt(res["V"], res["tau"], b)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_variant("serial")
+    return sum(flops(rows, S.shape[1]).values()) / dt / 1e9, dt, threads
 
 
 def main_config(m, n, precision, world):
@@ -215,7 +287,7 @@ def run_reference(args, rank, world):
         cpu_oracle_sample(A_h, rows)
     times = []
     for _ in range(args.steps):
-        _, dt = cpu_oracle_sample(A_h, rows)
+        _, dt, _ = cpu_oracle_sample(A_h, rows)
         times.append(dt)
     per = sum(flops(rows, n).values())
     tot = sum(times)
@@ -411,63 +483,104 @@ SHAPE_FORMS = {32: (("double_float", 1, False), ("fp32", 0, True)),
                      ("fp32", 0, True))}
 
 
+def time_form(tsqr, torch, dev, stream, sptr, A, m, n, precision, f32, steps=3, warmup=2, leaf_h=0):
+    """One step (factor, thin Q, Q^T b) of one precision form on the device matrix A, timed per
+    kernel with CUDA events; GFLOP/s with the LAPACK counts, backward error and orthogonality."""
+    import numpy as np
+
+    code = tsqr.TSQR_F32 if f32 else tsqr.TSQR_F64
+    A_ = A.float() if f32 else A
+    b = torch.from_numpy(np.random.default_rng(6).standard_normal((m, 1))).to(dev).to(A_.dtype)
+    Q = torch.empty((m, n), dtype=A_.dtype, device=dev)
+    R = torch.empty((n, n), dtype=A_.dtype, device=dev)
+    opts = tsqr.Opts(precision=precision, leaf_h=leaf_h)
+    nbytes = tsqr.tsqr_workspace_size(code, m, n, opts)
+    work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    ev = {"factor": [], "form_q": [], "apply_qt": []}
+    for it in range(warmup + steps):
+        mk = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        mk[0].record(stream)
+        h = tsqr.tsqr_factor(code, tsqr.TSQR_ROW_MAJOR, m, n, A_.data_ptr(), n, R.data_ptr(), n,
+                             work.data_ptr(), nbytes, opts, sptr)
+        mk[1].record(stream)
+        tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
+        mk[2].record(stream)
+        tsqr.tsqr_apply_qt(h, 1, b.data_ptr(), 1, sptr)
+        mk[3].record(stream)
+        info = tsqr.tsqr_handle_info(h)
+        tsqr.tsqr_destroy(h)
+        torch.cuda.synchronize()
+        if it >= warmup:
+            for i, k in enumerate(("factor", "form_q", "apply_qt")):
+                ev[k].append(mk[i].elapsed_time(mk[i + 1]))
+    fl = flops(m, n)
+    ms = sum(statistics.mean(v) for v in ev.values())
+    Ad, Qd, Rd = A_.double(), Q.double(), R.double()
+    res = {"m": m, "n": n, "panels": info.panels, "leaf_h": info.leaf_h, "chains": info.chains,
+           "value": sum(fl.values()) / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
+           "kernel_ms": {k: statistics.mean(v) for k, v in ev.items()},
+           "backward_error": (torch.linalg.norm(Ad - Qd @ Rd) / torch.linalg.norm(Ad)).item(),
+           "orthogonality": torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Qd.T @ Qd).item()}
+    del Ad, Qd, Rd, A_, b, Q, R, work
+    torch.cuda.empty_cache()
+    return res
+
+
+
 def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, warmup=2, forms=SHAPE_FORMS):
     """Plain FP64 TSQR (factor + thin Q + Q^T b) on the other column counts of the workload
     family, A = U Sigma V^T with kappa = 1: n = 16 and 32 are single TSQRs with taller leaves,
     n = 128 is the blocked QR over two 64-column TSQR panels.  The precision forms run beside
     FP64 at n = 32 and 128 (the Ozaki forms only differ from FP64 where np = 64: at n = 128 the
     panels' thin Q and their trailing updates Q^T [A_2] and Q [0; Q_2] run on the tensor cores)."""
-    import numpy as np
-
-    def time_form(A, n, precision, f32):
-        code = tsqr.TSQR_F32 if f32 else tsqr.TSQR_F64
-        A_ = A.float() if f32 else A
-        b = torch.from_numpy(np.random.default_rng(6).standard_normal((m, 1))).to(dev).to(A_.dtype)
-        Q = torch.empty((m, n), dtype=A_.dtype, device=dev)
-        R = torch.empty((n, n), dtype=A_.dtype, device=dev)
-        opts = tsqr.Opts(precision=precision)
-        nbytes = tsqr.tsqr_workspace_size(code, m, n, opts)
-        work = torch.empty(nbytes, dtype=torch.uint8, device=dev)
-        ev = {"factor": [], "form_q": [], "apply_qt": []}
-        for it in range(warmup + steps):
-            mk = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            mk[0].record(stream)
-            h = tsqr.tsqr_factor(code, tsqr.TSQR_ROW_MAJOR, m, n, A_.data_ptr(), n, R.data_ptr(), n,
-                                 work.data_ptr(), nbytes, opts, sptr)
-            mk[1].record(stream)
-            tsqr.tsqr_form_q(h, Q.data_ptr(), n, sptr)
-            mk[2].record(stream)
-            tsqr.tsqr_apply_qt(h, 1, b.data_ptr(), 1, sptr)
-            mk[3].record(stream)
-            info = tsqr.tsqr_handle_info(h)
-            tsqr.tsqr_destroy(h)
-            torch.cuda.synchronize()
-            if it >= warmup:
-                for i, k in enumerate(("factor", "form_q", "apply_qt")):
-                    ev[k].append(mk[i].elapsed_time(mk[i + 1]))
-        fl = flops(m, n)
-        ms = sum(statistics.mean(v) for v in ev.values())
-        Ad, Qd, Rd = A_.double(), Q.double(), R.double()
-        res = {"m": m, "n": n, "panels": info.panels, "leaf_h": info.leaf_h, "chains": info.chains,
-               "value": sum(fl.values()) / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms,
-               "kernel_ms": {k: statistics.mean(v) for k, v in ev.items()},
-               "backward_error": (torch.linalg.norm(Ad - Qd @ Rd) / torch.linalg.norm(Ad)).item(),
-               "orthogonality": torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Qd.T @ Qd).item()}
-        del Ad, Qd, Rd, A_, b, Q, R, work
-        torch.cuda.empty_cache()
-        return res
-
     out = {}
     for n in ns:
         A = torch.from_numpy(make_input(m, n)).to(dev)
-        out["n%d" % n] = time_form(A, n, 0, False)
+        out["n%d" % n] = time_form(tsqr, torch, dev, stream, sptr, A, m, n, 0, False, steps, warmup)
         if forms and n in forms:
             f64_ms = out["n%d" % n]["ms_per_step"]
             out["n%d" % n]["forms"] = {}
             for name, precision, f32 in forms[n]:
-                r = time_form(A, n, precision, f32)
+                r = time_form(tsqr, torch, dev, stream, sptr, A, m, n, precision, f32, steps, warmup)
                 r["speedup_vs_f64"] = f64_ms / r["ms_per_step"]
                 out["n%d" % n]["forms"][name] = r
+        del A
+        torch.cuda.empty_cache()
+    return out
+
+
+COND_FORMS = (("fp64", 0, False), ("double_float", 1, False), ("ozaki_wy", 2, False), ("df_ozaki_wy", 3, False),
+              ("fp32", 0, True))
+
+
+def run_conditioning(tsqr, torch, dev, stream, sptr, m, n, steps=2, warmup=1):
+    """Every precision form on the conditioning inputs of the workload family at the benchmark's
+    size: A = U Sigma V^T with kappa = 1e4, 1e6, 1e8 and 1e12 (U, V as the main line's) and the
+    s-step monomial Krylov basis of a random sparse symmetric matrix.  The Krylov basis is
+    numerically rank deficient, and at kappa = 1e12 R is not unique to the working precision, so
+    there only the backward error and orthogonality, which Householder QR bounds whatever the
+    conditioning, are meaningful."""
+    from paper_0809_2407_gb300 import inputs
+
+    ks = (4.0, 6.0, 8.0, 12.0)
+
+    def mats():
+        for k, Ah in zip(ks, inputs.usv_family(m, n, ks, inputs.seed_for(2, 0))):
+            yield "usv_kappa_1e%d" % int(k), Ah
+        yield "krylov", inputs.krylov(m, n, inputs.seed_for(2, 50))
+
+    out = {"m": m, "n": n, "steps": steps, "inputs": "A = U Sigma V^T, singular values log-spaced from 1 to 1/kappa; "
+           "krylov: [x, Sx, ...] with unit columns, S sparse symmetric (about 8 nonzeros per row) scaled "
+           "to spectral radius 1"}
+    for name, Ah in mats():
+        A = torch.from_numpy(Ah).to(dev)
+        del Ah
+        row = {}
+        for fname, precision, f32 in COND_FORMS:
+            r = time_form(tsqr, torch, dev, stream, sptr, A, m, n, precision, f32, steps, warmup)
+            row[fname] = {k: r[k] for k in ("value", "unit", "ms_per_step", "kernel_ms", "backward_error",
+                                            "orthogonality")}
+        out[name] = row
         del A
         torch.cuda.empty_cache()
     return out
@@ -579,6 +692,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-matrix batched workload")
     ap.add_argument("--no-autograd", action="store_true", help="skip the differentiable-QR workload")
     ap.add_argument("--no-shapes", action="store_true", help="skip the n = 16, 32, 128 shapes")
+    ap.add_argument("--no-conditioning", action="store_true",
+                    help="skip the kappa = 1e4..1e12 and Krylov inputs (every precision form)")
     ap.add_argument("--apply-wide", action="store_true",
                     help="time Q^T B / Q B with 64 columns even with --no-forms (for profiling)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 3],
@@ -625,10 +740,11 @@ def main():
     sptr = tsqr.ctypes.c_void_p(stream.cuda_stream)
     work_holder = {}
 
-    def run_mode(precision, steps, warmup, sample_clocks, f32=False):
+    def run_mode(precision, steps, warmup, sample_clocks, f32=False, leaf_h=0):
         """Times `steps` full steps in one arithmetic mode (f32: FP32 storage, the float32
-        rounding of the same A); returns timings and accuracy."""
-        opts = tsqr.Opts(precision=precision)
+        rounding of the same A; leaf_h: 64 selects the blocked tensor-core factor step of mode 2
+        and FP32 storage); returns timings and accuracy."""
+        opts = tsqr.Opts(precision=precision, leaf_h=leaf_h)
         code = tsqr.TSQR_F32 if f32 else tsqr.TSQR_F64
         if f32:
             A_, Q_, R_, b_ = A.float(), Q.float(), R.float(), b.float()
@@ -697,6 +813,7 @@ def main():
         return {"ms": ms, "ev": ev, "be": be, "orth": orth, "clocks": clocks, "opts": opts, "nbytes": nbytes,
                 "launches": launches}
 
+    pipes = measure_pipe_peaks()
     main_mode = run_mode(args.precision, args.steps, args.warmup, True, f32=args.fp32)
     # end to end right after the main line, before the other sections fill host and device memory
     e2e = None
@@ -726,11 +843,15 @@ def main():
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs")
     ab = algorithmic_bytes(m, n)
-    roofline = {"bound": "alu", "kernel": dom + "_kernel", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+    fp64_peak = pipes.get("fp64_tflops") or FP64_PEAK_TFLOPS
+    roofline = {"bound": "alu", "kernel": dom + "_kernel", "achieved": achieved_tf, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
                 "traffic": FACTOR_F64_TRAFFIC.get((m, n)) if (dom == "factor" and args.precision == 0) else None,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                "peak_source": "FP64 pipe, 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "peak_source": ("FP64 pipe, measured in this run by the FMA-chain probe (%s); nominal 152 SMs x 2 "
+                                "DFMA/clk x 2.07 GHz = %.3f TFLOP/s" % (pipes.get("how"), FP64_PEAK_TFLOPS))
+                if pipes.get("fp64_tflops") else "FP64 pipe, 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "measured_pipes": pipes,
                 "hbm_view": {"achieved_gbs": ab[dom] / (dom_ms / 1e3) / 1e9, "peak_gbs": hbm,
                              "frac_of_measured": (ab[dom] / (dom_ms / 1e3) / 1e9 / hbm) if hbm else None}}
 
@@ -769,6 +890,23 @@ def main():
             "backward_error": f3["be"], "orthogonality": f3["orth"],
             "note": "FP32 storage (A rounded to float32, R, Q, b float32) and FP32 arithmetic; "
                     "measures against the float32 A, bar 5e-5"}
+        # the blocked factor step whose WY products and Gram entries run on the tensor cores
+        # (64-row leaves): Ozaki splits with FP64 reflectors, bf16x3 terms with FP32 storage
+        for nm, prec, f32, note in (
+                ("ozaki_wy_blocked", 2, False, "mode 2 with 64-row leaves: blocked factor step, FP64 panel "
+                 "reflectors, panel WY products and Gram entries as Ozaki splits on tcgen05; thin Q as ozaki_wy"),
+                ("fp32_blocked", 0, True, "FP32 storage with 64-row leaves: blocked factor step, FP32 panel "
+                 "reflectors, panel WY products and Gram entries as bf16x3 terms on tcgen05; thin Q as fp32")):
+            r = run_mode(prec, args.steps, min(args.warmup, 3), False, f32=f32, leaf_h=64)
+            r_ms = r["ms"] / args.steps
+            forms[nm] = {"precision": prec, "leaf_h": 64, "dtype": "f32" if f32 else "f64+bf16x8-split",
+                         "value": per_step * world / (r_ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": r_ms,
+                         "speedup_vs_f64": ms_step / r_ms,
+                         "kernel_ms": {k: statistics.mean(v) for k, v in r["ev"].items()},
+                         "backward_error": r["be"], "orthogonality": r["orth"], "note": note}
+        ab_ = algorithmic_bytes(m, n)
+        for nm, fm in forms.items():
+            fm["roofline"] = form_roofline(nm, fl, fm["kernel_ms"], ab_, peaks, pipes)
         opts = tsqr.Opts(precision=0)
 
     # batched TSQR: 512 uneven matrices in one persistent launch (CUDA graph) vs a per-matrix loop
@@ -834,6 +972,10 @@ def main():
     if not args.no_shapes and world == 1:
         shapes = run_shapes(tsqr, torch, dev, stream, sptr, m)
 
+    conditioning = None
+    if not args.no_conditioning and world == 1:
+        conditioning = run_conditioning(tsqr, torch, dev, stream, sptr, m, n)
+
     autograd = None
     if not args.no_autograd and world == 1:
         autograd = run_autograd(tsqr, torch, dev, args)
@@ -841,9 +983,13 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = args.cpu_rows
-        gf, dt = cpu_oracle_sample(A_h, rows)
+        gf, dt, _ = cpu_oracle_sample(A_h, rows)
+        gfo, dto, thr = cpu_oracle_sample(A_h, rows, openmp=True)
         cpu = {"value": gf, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": "oracle QR, thin Q and Q^T b of the first %d rows of the same matrix (%.1f s)" % (rows, dt),
+               "openmp": {"value": gfo, "unit": "GFLOP/s", "cores": thr, "seconds": dto,
+                          "what": "the same oracle source built with -fopenmp (its reflector applications run "
+                                  "column-parallel; results bitwise the serial build's), same sample"},
                "host": host_cpu(), "library_cpu": cpu_library_sample(torch, A_h, rows)}
 
     if rank == 0:
@@ -854,7 +1000,7 @@ def main():
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
                "roofline": roofline, "precision_forms": forms, "apply_wide": apply_wide, "batched": batched,
-               "shapes": shapes,
+               "shapes": shapes, "conditioning": conditioning,
                "autograd": autograd, "r_alone": r_alone, "library_context": library, "cpu_baseline": cpu,
                "e2e": e2e,
                "gpu_launches": main_mode["launches"] * args.steps, "clocks": clocks}

@@ -180,9 +180,10 @@ tsqr_status_t tsqr_backward(tsqr_handle_t h, const void* dQbar, int64_t ldqb, co
 
 /* ---- Batches: many independent tall-skinny factorizations in one launch --------------------
  * The s-step and block Krylov uses of TSQR (Sec. 1) produce many small tall-skinny blocks; a
- * batch factors all of them with one persistent launch of the factorization kernel (every
- * chain of every matrix is one block) and forms their thin Q factors with one launch per tree
- * depth plus one chain launch.  All arrays below are host arrays of `count` entries; matrices
+ * batch factors all of them with one persistent launch of the factorization kernel (as many
+ * blocks as fit on the GPU, each taking the next chain of any matrix from a work list ordered
+ * longest chain first, until the list is used up) and forms their thin Q factors with one
+ * launch per tree depth plus one chain launch.  All arrays below are host arrays of `count` entries; matrices
  * follow the conventions of tsqr_factor (A is read only; inplace is not supported).
  * tsqr_batch_factor and tsqr_batch_form_q only enqueue kernels and memsets on `stream`, so a
  * CUDA graph can capture them once and replay them; tsqr_batch_create plans the batch, uploads
@@ -195,6 +196,16 @@ tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t
                                 void* const* dQ, const int64_t* ldq, void* dWork, size_t work_bytes,
                                 const tsqr_opts_t* opts, tsqr_stream_t stream, tsqr_batch_t* out);
 /* R of every matrix (Algorithms 1 and 2 per matrix). */
+/* The same with a plan per matrix: item_opts holds `count` entries (leaf height, arity and chain
+ * length of each matrix, e.g. an autotuner's choice for its shape; chain = 0 takes the batch's
+ * shared chain length).  Every entry takes the same precision; TSQR_ERR_UNSUPPORTED otherwise.
+ * The plans tune the tree to each shape (Sec. 7: the tuning space composes across levels). */
+tsqr_status_t tsqr_batch_workspace_size_plans(tsqr_dtype_t dtype, int32_t count, const int64_t* m,
+                                              const int64_t* n, const tsqr_opts_t* item_opts, size_t* bytes);
+tsqr_status_t tsqr_batch_create_plans(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
+                                      void* const* dA, const int64_t* lda, void* const* dR, const int64_t* ldr,
+                                      void* const* dQ, const int64_t* ldq, void* dWork, size_t work_bytes,
+                                      const tsqr_opts_t* item_opts, tsqr_stream_t stream, tsqr_batch_t* out);
 tsqr_status_t tsqr_batch_factor(tsqr_batch_t b, tsqr_stream_t stream);
 /* Thin Q of every matrix (after tsqr_batch_factor). */
 tsqr_status_t tsqr_batch_form_q(tsqr_batch_t b, tsqr_stream_t stream);

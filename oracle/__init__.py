@@ -15,15 +15,25 @@ import numpy as np
 
 from .build import build as _build
 
-_lib = None
+_libs = {}
+_variant = "serial"
 _dp = ctypes.POINTER(ctypes.c_double)
 _i64 = ctypes.c_int64
 
 
+def set_variant(name):
+    """Selects the build the functions below call: "serial" (the default) or "openmp" (the same
+    source compiled with -fopenmp, bitwise the same results; used only to time the oracle on all
+    host cores, with OMP_NUM_THREADS threads)."""
+    global _variant
+    assert name in ("serial", "openmp")
+    _variant = name
+
+
 def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(_build())
+    lib = _libs.get(_variant)
+    if lib is None:
+        lib = ctypes.CDLL(_build(openmp=(_variant == "openmp")))
         lib.oracle_geqr2.argtypes = [_i64, _i64, _dp, _i64, _dp]
         lib.oracle_org2r.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp, _i64]
         lib.oracle_apply_qt.argtypes = [_i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
@@ -34,8 +44,8 @@ def _load():
         lib.oracle_backward_error.restype = ctypes.c_double
         lib.oracle_orthogonality.argtypes = [_i64, _i64, _dp, _i64]
         lib.oracle_orthogonality.restype = ctypes.c_double
-        _lib = lib
-    return _lib
+        _libs[_variant] = lib
+    return lib
 
 
 def _p(a):

@@ -24,7 +24,11 @@
  * Norms use two-pass max scaling so that they neither overflow nor underflow.
  *
  * Storage is row-major: element (i, j) of an m x n matrix M with leading dimension ldm is
- * M[i*ldm + j].  Only tests/, the smoke check and the CPU-baseline leg of the benchmark may
+ * M[i*ldm + j].
+ *
+ * The loops over the columns a reflector is applied to carry an OpenMP pragma.  The default build
+ * ignores it.  A second build with -fopenmp exists only to time the oracle on all host cores.
+ * Each column's sums run in the same order either way, so both builds give the same bits.  Only tests/, the smoke check and the CPU-baseline leg of the benchmark may
  * load this library.  It shares no code, header or constant with the CUDA path.
  */
 #include <math.h>
@@ -70,6 +74,7 @@ static double make_reflector(int64_t len, double* x, int64_t inc, double* tau) {
 static void apply_reflector(int64_t m, int64_t top, const double* V, int64_t ldv, int64_t col,
                             double tau, int64_t k, double* B, int64_t ldb) {
   if (tau == 0.0) return;
+#pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < k; ++c) {
     double w = B[top * ldb + c];
     for (int64_t i = top + 1; i < m; ++i) w += V[i * ldv + col] * B[i * ldb + c];
@@ -85,6 +90,7 @@ void oracle_geqr2(int64_t m, int64_t n, double* A, int64_t lda, double* tau) {
     double beta = make_reflector(m - j, &A[j * lda + j], lda, &tau[j]);
     A[j * lda + j] = beta;
     if (tau[j] == 0.0) continue;
+#pragma omp parallel for schedule(static)
     for (int64_t c = j + 1; c < n; ++c) {
       double w = A[j * lda + c];
       for (int64_t i = j + 1; i < m; ++i) w += A[i * lda + j] * A[i * lda + c];

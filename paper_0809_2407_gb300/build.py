@@ -13,6 +13,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtsqr.so")
+# measurement tooling for the benchmark (FMA-pipe peaks), kept out of the TSQR library
+PROBE_SRC = os.path.join(CSRC, "probe", "fma_probe.cu")
+PROBE_LIB = os.path.join(OUT_DIR, "libtsqr_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -28,10 +31,10 @@ def _deps():
 
 
 def _stale():
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(p) > t for p in _deps())
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
+    return any(os.path.getmtime(p) > t for p in _deps() + [PROBE_SRC])
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -51,8 +54,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stdout + r.stderr)
         return obj
 
+    def compile_probe():
+        tmp = PROBE_LIB + ".tmp.%d" % os.getpid()
+        r = subprocess.run([NVCC] + FLAGS + ["-shared", "-o", tmp, PROBE_SRC], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed on %s:\n%s%s" % (PROBE_SRC, r.stdout, r.stderr))
+        os.replace(tmp, PROBE_LIB)
+
     with concurrent.futures.ThreadPoolExecutor(max_workers=8) as ex:
+        probe = ex.submit(compile_probe)
         objs = list(ex.map(compile_one, _sources()))
+        probe.result()
     tmp = LIB + ".tmp.%d" % os.getpid()
     r = subprocess.run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
     if r.returncode != 0:

@@ -19,6 +19,7 @@ using tsqr::Store;
 struct tsqr_batch_s {
   int count = 0, precision = 0;
   int total_chains = 0, max_depth = 0;
+  int factor_blocks = 1;  // resident blocks of the persistent factor launch
   size_t smem_factor = 0, smem_formq = 0;
   tsqr::BatchItem* d_items = nullptr;
   tsqr::BatchWork* d_chain_work = nullptr;
@@ -88,7 +89,8 @@ int default_leaf_h(int np) {
   switch (np) {
     case 16: return 512;
     case 32: return 256;
-    default: return 96;  // np = 64: tile + packed T fit twice in one SM's shared memory
+    default:
+      return 96;  // np = 64: tile + packed T fit twice in one SM's shared memory
   }
 }
 
@@ -614,43 +616,55 @@ struct BatchPlan {
   size_t counters_bytes = 0;
 };
 
+// Plans of a batch.  item_opts (count entries, or NULL for opts everywhere) lets every matrix
+// take its own leaf height, arity and chain length (an autotuner's choice per shape); the
+// precision must be the same for all.  An entry with chain = 0 takes the batch's shared chain
+// length.
 tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n, const tsqr_opts_t* opts,
-                              BatchPlan* bp, bool f32 = false) {
+                              const tsqr_opts_t* item_opts, BatchPlan* bp, bool f32 = false) {
   if (count < 1) return fail(TSQR_ERR_INVALID_ARG, "count must be >= 1");
   if (!m || !n) return fail(TSQR_ERR_INVALID_ARG, "m and n arrays must be non-NULL");
-  tsqr_opts_t base{};
-  if (opts) base = *opts;
-  if (base.inplace) return fail(TSQR_ERR_UNSUPPORTED, "batches keep A read-only (inplace is not supported)");
-  if (base.r_only) return fail(TSQR_ERR_UNSUPPORTED, "batches keep Q (r_only is not supported)");
-  // the batched thin Q runs on the FP64-pipe or FP32-pipe kernels: the Ozaki forms run as their
-  // factorization's arithmetic
-  if (base.precision == tsqr::kPrecOzaki) base.precision = tsqr::kPrecF64;
-  if (base.precision == tsqr::kPrecDFOzaki) base.precision = tsqr::kPrecDF;
-  if (f32 && base.precision != 0)
-    return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 runs FP32 arithmetic: precision must be 0");
+  std::vector<tsqr_opts_t> io(count);
+  for (int i = 0; i < count; ++i) {
+    tsqr_opts_t o{};
+    if (item_opts) o = item_opts[i];
+    else if (opts) o = *opts;
+    if (o.inplace) return fail(TSQR_ERR_UNSUPPORTED, "batches keep A read-only (inplace is not supported)");
+    if (o.r_only) return fail(TSQR_ERR_UNSUPPORTED, "batches keep Q (r_only is not supported)");
+    // the batched thin Q runs on the FP64-pipe or FP32-pipe kernels: the Ozaki forms run as their
+    // factorization's arithmetic
+    if (o.precision == tsqr::kPrecOzaki) o.precision = tsqr::kPrecF64;
+    if (o.precision == tsqr::kPrecDFOzaki) o.precision = tsqr::kPrecDF;
+    if (f32 && o.precision != 0)
+      return fail(TSQR_ERR_UNSUPPORTED, "TSQR_F32 runs FP32 arithmetic: precision must be 0");
+    if (i > 0 && o.precision != io[0].precision)
+      return fail(TSQR_ERR_UNSUPPORTED, "every matrix of a batch takes the same precision");
+    io[i] = o;
+  }
   // shared chain length: about 16 waves of two blocks per SM over the whole batch; double-float
   // keeps chains of at most 18 leaves (its orthogonality grows with chain length)
-  tsqr_opts_t probe = base;
-  probe.chain = 1;
   int64_t total_leaves = 0;
   for (int i = 0; i < count; ++i) {
+    tsqr_opts_t probe = io[i];
+    probe.chain = 1;
     Plan P;
     tsqr_status_t s = make_plan(m[i], n[i], &probe, &P, f32);
     if (s != TSQR_OK) return fail(s, "batch item " + std::to_string(i) + ": " + g_last_error);
     total_leaves += P.leaves;
   }
-  if (base.chain == 0) {
+  {
     const int64_t blocks = 16LL * 2 * device_sms();
     int64_t c = (total_leaves + blocks - 1) / blocks;
     if (c < 1) c = 1;
-    if (tsqr::prec_df(base.precision) && c > 18) c = 18;
-    base.chain = (int32_t)c;
+    if (tsqr::prec_df(io[0].precision) && c > 18) c = 18;
+    for (int i = 0; i < count; ++i)
+      if (io[i].chain == 0) io[i].chain = (int32_t)c;
   }
   bp->plans.resize(count);
   bp->layouts.resize(count);
   bp->item_off.resize(count);
   for (int i = 0; i < count; ++i) {
-    tsqr_status_t s = make_plan(m[i], n[i], &base, &bp->plans[i], f32);
+    tsqr_status_t s = make_plan(m[i], n[i], &io[i], &bp->plans[i], f32);
     if (s != TSQR_OK) return fail(s, "batch item " + std::to_string(i) + ": " + g_last_error);
     bp->layouts[i] = make_layout(bp->plans[i], false);
     bp->total_chains += bp->plans[i].chains;
@@ -664,7 +678,7 @@ tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n,
     off = align256(off + bytes);
     return at;
   };
-  bp->status_off = take(256);
+  bp->status_off = take(256);  // status word, then the persistent factor launch's work counter
   bp->items_off = take(sizeof(tsqr::BatchItem) * (size_t)count);
   bp->chain_work_off = take(sizeof(tsqr::BatchWork) * (size_t)bp->total_chains);
   bp->level_work_off = take(sizeof(tsqr::BatchWork) * (size_t)(bp->level_items > 0 ? bp->level_items : 1));
@@ -678,21 +692,34 @@ tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n,
 
 extern "C" {
 
-tsqr_status_t tsqr_batch_workspace_size(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
-                                        const tsqr_opts_t* opts, size_t* bytes) {
+tsqr_status_t tsqr_batch_workspace_size_plans(tsqr_dtype_t dtype, int32_t count, const int64_t* m,
+                                              const int64_t* n, const tsqr_opts_t* item_opts, size_t* bytes) {
   if (!bytes) return fail(TSQR_ERR_INVALID_ARG, "bytes is NULL");
+  if (!item_opts) return fail(TSQR_ERR_INVALID_ARG, "item_opts is NULL");
   if (dtype != TSQR_F64 && dtype != TSQR_F32) return fail(TSQR_ERR_INVALID_ARG, "unknown dtype");
   BatchPlan bp;
-  tsqr_status_t s = make_batch_plan(count, m, n, opts, &bp, dtype == TSQR_F32);
+  tsqr_status_t s = make_batch_plan(count, m, n, nullptr, item_opts, &bp, dtype == TSQR_F32);
   if (s != TSQR_OK) return s;
   *bytes = bp.total;
   return TSQR_OK;
 }
 
-tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
-                                void* const* dA, const int64_t* lda, void* const* dR, const int64_t* ldr,
-                                void* const* dQ, const int64_t* ldq, void* dWork, size_t work_bytes,
-                                const tsqr_opts_t* opts, tsqr_stream_t stream, tsqr_batch_t* out) {
+tsqr_status_t tsqr_batch_workspace_size(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
+                                        const tsqr_opts_t* opts, size_t* bytes) {
+  if (!bytes) return fail(TSQR_ERR_INVALID_ARG, "bytes is NULL");
+  if (dtype != TSQR_F64 && dtype != TSQR_F32) return fail(TSQR_ERR_INVALID_ARG, "unknown dtype");
+  BatchPlan bp;
+  tsqr_status_t s = make_batch_plan(count, m, n, opts, nullptr, &bp, dtype == TSQR_F32);
+  if (s != TSQR_OK) return s;
+  *bytes = bp.total;
+  return TSQR_OK;
+}
+
+static tsqr_status_t batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
+                                  void* const* dA, const int64_t* lda, void* const* dR, const int64_t* ldr,
+                                  void* const* dQ, const int64_t* ldq, void* dWork, size_t work_bytes,
+                                  const tsqr_opts_t* opts, const tsqr_opts_t* item_opts, tsqr_stream_t stream,
+                                  tsqr_batch_t* out) {
   if (!out) return fail(TSQR_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (dtype != TSQR_F64 && dtype != TSQR_F32) return fail(TSQR_ERR_INVALID_ARG, "unknown dtype");
@@ -700,7 +727,7 @@ tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t
   if (!dA || !lda || !dR || !ldr) return fail(TSQR_ERR_INVALID_ARG, "A, lda, R and ldr arrays must be non-NULL");
   if (dQ && !ldq) return fail(TSQR_ERR_INVALID_ARG, "ldq array must be given with Q");
   BatchPlan bp;
-  tsqr_status_t s = make_batch_plan(count, m, n, opts, &bp, f32);
+  tsqr_status_t s = make_batch_plan(count, m, n, opts, item_opts, &bp, f32);
   if (s != TSQR_OK) return s;
   if (!dWork || work_bytes < bp.total)
     return fail(TSQR_ERR_WORKSPACE, "batch workspace needs " + std::to_string(bp.total) + " bytes");
@@ -778,6 +805,15 @@ tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t
     b->smem_formq = std::max(b->smem_formq, tsqr::formq_smem_bytes(P, true));  // the chain kernel double-buffers
     for (int g = 0; g < P.chains; ++g) chain_work.push_back({i, g, 0});
   }
+  // longest chains first: the persistent factor launch takes work in this order, so the last
+  // items to start are the shortest (longest-processing-time-first balancing)
+  auto chain_cost = [&](const tsqr::BatchWork& w) {
+    const Plan& P = bp.plans[w.item];
+    const int64_t leaves = tsqr::chain_end_leaf(P, w.chain) - tsqr::chain_first_leaf(P, w.chain);
+    return (double)leaves * P.h * P.n * P.n;
+  };
+  std::stable_sort(chain_work.begin(), chain_work.end(),
+                   [&](const tsqr::BatchWork& a, const tsqr::BatchWork& c) { return chain_cost(a) > chain_cost(c); });
   // tree steps of the batched thin Q, by distance d from each item's root
   std::vector<std::vector<tsqr::BatchWork>> levels(bp.max_depth);
   for (int i = 0; i < count; ++i) {
@@ -806,6 +842,7 @@ tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t
                         cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);  // the host arrays above are about to go away
   if (e == cudaSuccess) e = tsqr::prepare_factor_batched(b->precision, b->smem_factor);
+  if (e == cudaSuccess) e = tsqr::factor_batched_blocks(b->precision, b->total_chains, b->smem_factor, &b->factor_blocks);
   if (e == cudaSuccess) e = tsqr::prepare_form_q_batched(b->precision, b->smem_formq);
   if (e != cudaSuccess) {
     delete b;
@@ -815,10 +852,27 @@ tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t
   return TSQR_OK;
 }
 
+tsqr_status_t tsqr_batch_create(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
+                                void* const* dA, const int64_t* lda, void* const* dR, const int64_t* ldr,
+                                void* const* dQ, const int64_t* ldq, void* dWork, size_t work_bytes,
+                                const tsqr_opts_t* opts, tsqr_stream_t stream, tsqr_batch_t* out) {
+  return batch_create(dtype, count, m, n, dA, lda, dR, ldr, dQ, ldq, dWork, work_bytes, opts, nullptr, stream, out);
+}
+
+tsqr_status_t tsqr_batch_create_plans(tsqr_dtype_t dtype, int32_t count, const int64_t* m, const int64_t* n,
+                                      void* const* dA, const int64_t* lda, void* const* dR, const int64_t* ldr,
+                                      void* const* dQ, const int64_t* ldq, void* dWork, size_t work_bytes,
+                                      const tsqr_opts_t* item_opts, tsqr_stream_t stream, tsqr_batch_t* out) {
+  if (!item_opts) return fail(TSQR_ERR_INVALID_ARG, "item_opts is NULL");
+  return batch_create(dtype, count, m, n, dA, lda, dR, ldr, dQ, ldq, dWork, work_bytes, nullptr, item_opts, stream,
+                      out);
+}
+
 tsqr_status_t tsqr_batch_factor(tsqr_batch_t b, tsqr_stream_t stream) {
   if (!b) return fail(TSQR_ERR_INVALID_ARG, "batch is NULL");
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(b->d_status, 0, sizeof(int), cs);
+  // the status word and the persistent launch's work counter (the next int) start at zero
+  cudaError_t e = cudaMemsetAsync(b->d_status, 0, 2 * sizeof(int), cs);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, b->counters_bytes, cs);
   for (size_t k = 0; e == cudaSuccess && k < b->stages.size(); ++k) {
     const auto& sg = b->stages[k];
@@ -826,7 +880,8 @@ tsqr_status_t tsqr_batch_factor(tsqr_batch_t b, tsqr_stream_t stream) {
   }
   if (e == cudaSuccess && b->widen) e = tsqr::launch_stage_widen_batched(b->d_items, b->count, cs);
   if (e == cudaSuccess)
-    e = tsqr::launch_factor_batched(b->d_items, b->d_chain_work, b->total_chains, b->precision, b->smem_factor, cs);
+    e = tsqr::launch_factor_batched(b->d_items, b->d_chain_work, b->total_chains, b->d_status + 1, b->factor_blocks,
+                                    b->precision, b->smem_factor, cs);
   if (e != cudaSuccess) return cuda_fail(e, "batched factor launch");
   return TSQR_OK;
 }

@@ -61,7 +61,15 @@ struct ChainScratch {
 // Leaves R in rows 0..n-1, the scaled reflectors in rows NP.., tau in tau_s and, with want_t,
 // T packed by rows in T_s (tri_off); without it the Gram entries and the merge are skipped (R
 // alone).  All threads call.
-template <class Ar, int NP, int H = ChainShape<NP>::H>
+//
+// kTri: the bottom block is the upper triangle R_1 of a binary tree node (rows past NP zero), so
+// the structure of eq. fact_2rs holds: column j's reflector and every column it updates are
+// nonzero in bottom rows 0..j only (reflectors 0..j-1 touched rows below j of no column), and
+// the dot products, Gram entries and updates visit only the 8-row blocks 0..j/8.  The skipped
+// terms are products with exact zeros (in FP64 the results equal the dense step's bit for bit on
+// finite data), and the structural zeros stay exactly zero even when a reflector carries Inf or
+// NaN.  Every loop bound depends on j alone, never on data, and no barrier is skipped.
+template <class Ar, int NP, int H = ChainShape<NP>::H, bool kTri = false>
 __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename Ar::E* T_s,
                          const ChainScratch<Ar, NP>& w, bool want_t = true) {
   using E = typename Ar::E;
@@ -76,11 +84,14 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
   char* const bottom = S.base + (size_t)NP * 128;  // row NP starts block 0
   E* sc = w.sc;
 
+  // bottom rows that can be nonzero in column c (all of them unless kTri)
+  auto rows_of = [](int c) { return kTri ? (c + 1 < H ? c + 1 : H) : H; };
   // warp 0: v_c = x_c inv_c over the bottom rows, once reflector c is built
   auto scale_column = [&](int c) {
     __syncwarp();
     const E s = w.invs[c];
-    for (int r = NP + lane; r < NP + H; r += 32) {
+    const int rc_end = NP + rows_of(c);
+    for (int r = NP + lane; r < rc_end; r += 32) {
       E& x = at<E>(S, r, c);
       x = Ar::mul(x, s);
     }
@@ -115,6 +126,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
         E acc[4] = {Ar::zero(), Ar::zero(), Ar::zero(), Ar::zero()};
 #pragma unroll
         for (int bb = 0; bb < NBG; ++bb) {
+          if (kTri && gown + bb * G > (j >> 3)) continue;  // rows past j: exact zeros in v_j
           const char* pb = bottom + (size_t)(gown + bb * G) * 1024;
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
@@ -153,7 +165,8 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
         if (j + 1 < n) {
           const int c = j + 1;
           const E wc = w.wvec[c];
-          for (int r = NP + lane; r < NP + H; r += 32) {
+          const int r_end = NP + rows_of(j);  // v_j is zero below
+          for (int r = NP + lane; r < r_end; r += 32) {
             E& a = at<E>(S, r, c);
             a = Ar::axpy(a, wc, at<E>(S, r, j));
           }
@@ -172,7 +185,8 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
             const E wc = w.wvec[c];
             uint32_t oa[8];
             block_offsets(rc, c, oa);
-            for (int b = gu; b < NB; b += Gu) {
+            const int nb_end = kTri ? ((j >> 3) + 1 < NB ? (j >> 3) + 1 : NB) : NB;
+            for (int b = gu; b < nb_end; b += Gu) {
               char* pb = bottom + (size_t)b * 1024;
 #pragma unroll
               for (int t = 0; t < 8; ++t) {

@@ -1,240 +1,15 @@
-// TSQR factorization kernel: leaves, flat chains and the tree over thread blocks, in one launch.
-//
-// Block g owns chain g: leaves [g*chain, ...).  It factors its first leaf with a plain
-// Householder QR (Algorithm 1, first step) and each following leaf A_k with the flat-tree step
-// QR([R; A_k]) (Algorithm 2), keeping R in shared memory so that only one R per block leaves
-// the chip (Sec. 2: the flat tree minimises slow-memory traffic).  Every leaf's reflectors,
-// tau and T go to HBM (the reified tree, Sec. 4.1).
-//
-// The chains' R factors are then reduced up an arity-q tree (Algorithm 1, tree steps) without
-// any block waiting for another: each block publishes its R and bumps its parent's counter;
-// the block that arrives last stacks the q children's R factors in child order (Algorithm 1:
-// "by order of processor ids"), takes their structured QR (eq. fact_2rs) and climbs on.  The
-// block that finishes the root writes R with diag(R) >= 0 and the sign vector.
+// TSQR factorization kernels: leaves, flat chains and the tree over thread blocks, in one launch
+// (the schedule is in factor_chain.cuh), with the flat-tree step on the FP64 (or FP32) pipe.
+#include <algorithm>
+
 #include "factor_kernels.h"
-#include "chain_qr.cuh"
+#include "factor_chain.cuh"
 
 namespace tsqr {
-
-template <class E>
-struct FactorSmem {
-  Tile S;
-  E *T_s, *red, *dvec, *sc, *tau_s, *wvec, *invs, *X;
-  uint64_t* bar;
-  int* flag;
-};
-
-template <class E>
-__device__ inline FactorSmem<E> carve_factor(char* raw, const Plan& P) {
-  FactorSmem<E> f;
-  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
-  f.S = Tile{base, P.rows_cap};
-  f.T_s = reinterpret_cast<E*>(base + (size_t)P.rows_cap * P.np * 8);
-  f.red = f.T_s + tri_size(P.np);
-  f.dvec = f.red + kThreads;
-  f.sc = f.dvec + P.np;
-  f.tau_s = f.sc + 8;
-  f.wvec = f.tau_s + P.np;
-  f.invs = f.wvec + P.np;
-  f.X = f.invs + P.np;
-  f.bar = reinterpret_cast<uint64_t*>(f.X + P.np * P.np / 4);
-  f.flag = reinterpret_cast<int*>(f.bar + 1);
-  return f;
-}
 
 size_t factor_smem_bytes(const Plan& P) {
   return 1024 + (size_t)P.rows_cap * P.np * 8 + (size_t)tri_size(P.np) * 8 + kThreads * 8 + P.np * 8 + 8 * 8 +
          P.np * 8 + 2 * P.np * 8 + (size_t)P.np * P.np / 4 * 8 + 8 + 16;
-}
-
-// The flat-tree step on the tile: the scheduled chain_qr for the default shapes, the generic
-// stacked_qr otherwise.
-template <class Ar>
-__device__ inline void chain_step(const FactorSmem<typename Ar::E>& f, const Plan& P) {
-  const int np = P.np, n = P.n, h = P.h;
-  const bool want_t = !P.r_only;
-  if (np == 64 && h == ChainShape<64>::H) {
-    chain_qr<Ar, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 64>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X}, want_t);
-  } else if (np == 32 && h == ChainShape<32>::H) {
-    chain_qr<Ar, 32>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 32>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X}, want_t);
-  } else if (np == 16 && h == ChainShape<16>::H) {
-    chain_qr<Ar, 16>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 16>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X}, want_t);
-  } else {
-    stacked_qr<Ar>(f.S, CHAIN, np + h, np, n, f.tau_s, want_t ? f.T_s : nullptr, f.red, f.dvec, f.sc);
-  }
-}
-
-// A binary tree node (q <= 2 children) by the scheduled chain step: the second child's triangle
-// (zeros for a lone child) is the block under the first child's R, padded with zero rows to a
-// height the step's schedule takes (64 rows for np = 64 and 32, 128 for np = 16).  Rows that are
-// zero stay exactly zero under the reflectors, so the node's reflectors keep the structure of
-// eq. fact_2rs and the result equals the structured QR's.  False (nothing done) when the node
-// does not fit that form.
-template <class Ar>
-__device__ inline bool node_step(const FactorSmem<typename Ar::E>& f, const Plan& P, int q) {
-  using E = typename Ar::E;
-  const int np = P.np, n = P.n;
-  const int H = (np == 16) ? 128 : 64;
-  if (q > 2 || np < 16 || P.rows_cap < np + H) return false;
-  const int lnp = __ffs(np) - 1;
-  for (int i = threadIdx.x; i < (np + H - q * np) * np; i += kThreads)
-    at<E>(f.S, q * np + (i >> lnp), i & (np - 1)) = Ar::zero();
-  __syncthreads();
-  const bool want_t = !P.r_only;
-  if (np == 64)
-    chain_qr<Ar, 64, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 64>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X},
-                         want_t);
-  else if (np == 32)
-    chain_qr<Ar, 32, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 32>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X},
-                         want_t);
-  else
-    chain_qr<Ar, 16, 128>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 16>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X},
-                          want_t);
-  __syncthreads();
-  return true;
-}
-
-// Rows [r0, r0 + rows) of the tile arrive from TMA as FP64; in double-float mode they are split
-// into (hi, lo) pairs in place.
-template <class Ar>
-__device__ inline void convert_rows_in(const Tile& S, int r0, int rows, int np) {
-  if constexpr (Ar::kPrecision != 0) {
-    const int lnp = __ffs(np) - 1;  // np is a power of two
-    for (int i = threadIdx.x; i < rows * np; i += kThreads) {
-      double* p = S.ptr(r0 + (i >> lnp), i & (np - 1));
-      *reinterpret_cast<typename Ar::E*>(p) = Ar::from_f64(*p);
-    }
-    __syncthreads();
-  }
-}
-
-// Chain g of one factorization, then the tree above it while this block arrives last.
-template <class Ar>
-__device__ __forceinline__ void factor_chain(const CUtensorMap* mapA_p, const CUtensorMap* mapV_p, const Plan& P,
-                                             const Store& st, typename Ar::Out* __restrict__ R_out, int64_t ldr,
-                                             int box_rows,
-                                             int g, char* smem_raw) {
-  using E = typename Ar::E;
-  FactorSmem<E> f = carve_factor<E>(smem_raw, P);
-  const Tile& S = f.S;
-  const int tid = threadIdx.x;
-  const int np = P.np, n = P.n, h = P.h;
-  const int lnp = __ffs(np) - 1;  // np is a power of two
-  E* tau_leaf = reinterpret_cast<E*>(st.tau_leaf);
-  E* t_leaf = reinterpret_cast<E*>(st.t_leaf);
-  E* node_r = reinterpret_cast<E*>(st.node_r);
-  if (tid == 0) {
-    mbar_init(f.bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  uint32_t phase = 0;
-
-  // ---- the chain: plain QR of the first leaf, then QR([R; A_k]) for each following leaf
-  const int64_t l0 = chain_first_leaf(P, g), l1 = chain_end_leaf(P, g);
-  for (int64_t leaf = l0; leaf < l1; ++leaf) {
-    const bool plain = (leaf == l0);
-    const int dst = plain ? 0 : np;
-    const int64_t row0 = leaf * h;
-    if (!tile_load(S, mapA_p, f.bar, phase, np, row0, h, dst, box_rows, st.status, f.flag)) {
-      if (tid == 0) tma_store_wait_all();
-      return;
-    }
-    convert_rows_in<Ar>(S, dst, h, np);
-    if (plain)
-      stacked_qr<Ar>(S, PLAIN, h, np, n, f.tau_s, P.r_only ? nullptr : f.T_s, f.red, f.dvec, f.sc);
-    else
-      chain_step<Ar>(f, P);
-    if (!P.r_only) {  // the leaf's reflectors, tau and T: the reified tree (Sec. 4.1)
-      tile_store(S, mapV_p, np, row0, h, dst, box_rows);
-      E* tau_g = tau_leaf + leaf * np;
-      E* T_g = t_leaf + leaf * np * np;
-      for (int i = tid; i < np; i += kThreads) tau_g[i] = f.tau_s[i];
-      for (int i = tid; i < np * np; i += kThreads) {
-        const int a = (i >> lnp), b = (i & (np - 1));
-        T_g[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
-      }
-      tile_store_drain();
-    } else {
-      __syncthreads();
-    }
-    if (plain) {  // rows 0..np-1 now carry R above the diagonal; clear the reflector part below
-      for (int i = tid; i < np * np; i += kThreads) {
-        const int r = (i >> lnp), c = (i & (np - 1));
-        if (c < r) at<E>(S, r, c) = Ar::zero();
-      }
-      __syncthreads();
-    }
-  }
-
-  // ---- publish the chain's R (level-0 node g); the reflector stores are complete first
-  if (tid == 0) tma_store_wait_all();
-  {
-    E* Rg = node_r + (size_t)g * np * np;
-    for (int i = tid; i < np * np; i += kThreads) {
-      const int r = (i >> lnp), c = (i & (np - 1));
-      Rg[i] = (c >= r) ? at<E>(S, r, c) : Ar::zero();
-    }
-  }
-
-  // ---- climb the tree while this block is the last child to arrive
-  int idx = g;
-  for (int level = 0; level < P.depth; ++level) {
-    const int parent = idx / P.arity;
-    const int first = parent * P.arity;
-    const int q = min(P.arity, P.level_count[level] - first);
-    const int pid = P.level_offset[level + 1] + parent;
-    const int tn = pid - P.chains;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-      const int prev = atomicAdd(&st.counters[tn], 1);
-      __threadfence();
-      *f.flag = (prev == q - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (*f.flag == 0) return;
-    // stack the children's R factors in child order: child s at rows s*np..s*np+np-1
-    for (int s = 0; s < q; ++s) {
-      const double* Rc = st.node_r + (size_t)(P.level_offset[level] + first + s) * np * np;
-      for (int i = tid; i < np * np; i += kThreads) *S.ptr(s * np + (i >> lnp), (i & (np - 1))) = __ldcg(Rc + i);
-    }
-    __syncthreads();
-    if (!node_step<Ar>(f, P, q))
-      stacked_qr<Ar>(S, NODE, q * np, np, n, f.tau_s, P.r_only ? nullptr : f.T_s, f.red, f.dvec, f.sc);
-    if (!P.r_only) {  // the node's reflectors (eq. fact_2rs), tau and T
-      E* Y = reinterpret_cast<E*>(st.node_y) + (size_t)tn * (P.arity - 1) * np * np;
-      for (int s = 1; s < P.arity; ++s) {
-        E* Ys = Y + (size_t)(s - 1) * np * np;
-        for (int i = tid; i < np * np; i += kThreads) {
-          const int r = (i >> lnp), c = (i & (np - 1));
-          Ys[i] = (s < q && c >= r) ? at<E>(S, s * np + r, c) : Ar::zero();
-        }
-      }
-      for (int i = tid; i < np; i += kThreads) reinterpret_cast<E*>(st.node_tau)[(size_t)tn * np + i] = f.tau_s[i];
-      E* Tn = reinterpret_cast<E*>(st.node_t) + (size_t)tn * np * np;
-      for (int i = tid; i < np * np; i += kThreads) {
-        const int a = (i >> lnp), b = (i & (np - 1));
-        Tn[i] = (b >= a && b < n) ? f.T_s[tri_off(a, np) + (b - a)] : Ar::zero();
-      }
-    }
-    E* Rp = node_r + (size_t)pid * np * np;
-    for (int i = tid; i < np * np; i += kThreads) {
-      const int r = (i >> lnp), c = (i & (np - 1));
-      Rp[i] = (c >= r) ? at<E>(S, r, c) : Ar::zero();
-    }
-    idx = parent;
-  }
-
-  // ---- root: R <- D R with D = diag(sign(R_jj)), sign(0) = +1
-  __syncthreads();
-  for (int j = tid; j < np; j += kThreads) st.signs[j] = (j < n && Ar::is_neg(at<E>(S, j, j))) ? -1.0 : 1.0;
-  using Out = typename Ar::Out;
-  for (int i = tid; i < n * n; i += kThreads) {
-    const int r = i / n, c = i % n;
-    const Out d = Ar::is_neg(at<E>(S, r, r)) ? Out(-1) : Out(1);
-    R_out[gidx(P, r, c, ldr)] = (c >= r) ? d * Ar::to_out(at<E>(S, r, c)) : Out(0);
-  }
 }
 
 template <class Ar>
@@ -242,18 +17,47 @@ __global__ void __launch_bounds__(kThreads, 2)
     factor_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, const Plan P,
                   const Store st, typename Ar::Out* __restrict__ R_out, int64_t ldr, int box_rows) {
   extern __shared__ char smem_raw[];
-  factor_chain<Ar>(&mapA, &mapV, P, st, R_out, ldr, box_rows, blockIdx.x, smem_raw);
+  factor_chain<Ar>(&mapA, &mapV, P, st, R_out, ldr, box_rows, blockIdx.x, carve_factor<typename Ar::E>(smem_raw, P),
+                   [](const FactorSmem<typename Ar::E>& f, const Plan& p) {
+                     chain_step<Ar>(f, p);
+                     return true;
+                   });
 }
 
-// Many factorizations in one launch: block b runs chain work[b].chain of item work[b].item.
+// Many factorizations in one persistent launch: every block takes the next chain from the work
+// list (work[k]: chain work[k].chain of item work[k].item, longest chains first) through the
+// counter *next until the list is used up.  No block waits for another (the tree above each
+// item's chains is climbed by the last arrival), so any number of resident blocks is safe.
 template <class Ar>
 __global__ void __launch_bounds__(kThreads, 2)
-    factor_batched_kernel(const BatchItem* __restrict__ items, const BatchWork* __restrict__ work) {
+    factor_batched_kernel(const BatchItem* __restrict__ items, const BatchWork* __restrict__ work, int total,
+                          int* __restrict__ next) {
   extern __shared__ char smem_raw[];
-  const BatchWork w = work[blockIdx.x];
-  const BatchItem& it = items[w.item];
-  factor_chain<Ar>(&it.mapA, &it.mapV, it.plan, it.store, static_cast<typename Ar::Out*>(it.R), it.ldr, it.box_rows,
-                   w.chain, smem_raw);
+  __shared__ int k_s;
+  for (;;) {
+    if (threadIdx.x == 0) k_s = atomicAdd(next, 1);
+    __syncthreads();
+    const int k = k_s;
+    __syncthreads();  // every thread has read k_s before thread 0 takes the next one
+    if (k >= total) return;
+    const BatchWork w = work[k];
+    const BatchItem& it = items[w.item];
+    const FactorSmem<typename Ar::E> f = carve_factor<typename Ar::E>(smem_raw, it.plan);
+    factor_chain<Ar>(&it.mapA, &it.mapV, it.plan, it.store, static_cast<typename Ar::Out*>(it.R), it.ldr,
+                     it.box_rows, w.chain, f, [](const FactorSmem<typename Ar::E>& ff, const Plan& p) {
+                       chain_step<Ar>(ff, p);
+                       return true;
+                     });
+    // a bounded wait that gave up may leave a copy in flight: take no further work
+    __syncthreads();
+    if (threadIdx.x == 0) k_s = *reinterpret_cast<volatile int*>(it.store.status) & kStatusTimeout;
+    __syncthreads();
+    const int failed = k_s;
+    __syncthreads();  // every thread has read k_s before thread 0 reuses it
+    if (failed) return;
+    // the next item carves shared memory by its own plan: retire this item's TMA barrier first
+    if (threadIdx.x == 0) mbar_inval(f.bar);
+  }
 }
 
 cudaError_t prepare_factor_batched(int precision, size_t smem) {
@@ -264,14 +68,32 @@ cudaError_t prepare_factor_batched(int precision, size_t smem) {
   return cudaFuncSetAttribute(factor_batched_kernel<ArithF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work, int blocks, int precision,
-                                  size_t smem, cudaStream_t stream) {
+template <class Ar>
+static cudaError_t factor_batched_blocks_t(int total, size_t smem, int* blocks) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_batched_kernel<Ar>, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  *blocks = std::max(1, std::min(total, std::max(1, per_sm) * sms));
+  return cudaSuccess;
+}
+
+cudaError_t factor_batched_blocks(int precision, int total, size_t smem, int* blocks) {
+  if (prec_df(precision)) return factor_batched_blocks_t<ArithDF>(total, smem, blocks);
+  if (precision == kPrecF32) return factor_batched_blocks_t<ArithF32>(total, smem, blocks);
+  return factor_batched_blocks_t<ArithF64>(total, smem, blocks);
+}
+
+cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work, int total, int* next, int blocks,
+                                  int precision, size_t smem, cudaStream_t stream) {
   if (prec_df(precision))
-    factor_batched_kernel<ArithDF><<<blocks, kThreads, smem, stream>>>(items, work);
+    factor_batched_kernel<ArithDF><<<blocks, kThreads, smem, stream>>>(items, work, total, next);
   else if (precision == kPrecF32)
-    factor_batched_kernel<ArithF32><<<blocks, kThreads, smem, stream>>>(items, work);
+    factor_batched_kernel<ArithF32><<<blocks, kThreads, smem, stream>>>(items, work, total, next);
   else
-    factor_batched_kernel<ArithF64><<<blocks, kThreads, smem, stream>>>(items, work);
+    factor_batched_kernel<ArithF64><<<blocks, kThreads, smem, stream>>>(items, work, total, next);
   return cudaGetLastError();
 }
 
@@ -382,6 +204,7 @@ cudaError_t launch_stage_transpose(const void* A, bool f32, int64_t lda, double*
 
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                           void* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
+  if (blocked_factor_applies(P)) return launch_factor_blocked(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
   if (prec_df(P.precision)) return launch_factor_t<ArithDF>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
   if (P.precision == kPrecF32) return launch_factor_t<ArithF32>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
   return launch_factor_t<ArithF64>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);

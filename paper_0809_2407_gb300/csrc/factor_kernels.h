@@ -34,14 +34,24 @@ cudaError_t launch_stage_widen(const float* A, int64_t lda, double* V, int64_t l
                                cudaStream_t stream);
 cudaError_t launch_stage_transpose(const void* A, bool f32, int64_t lda, double* V, int64_t ldv, int64_t m, int n,
                                    cudaStream_t stream);
+// Precision mode 2 (Ozaki products) or FP32 storage (bf16x3 products) at np = 64, h = 64, binary
+// tree: the blocked flat-tree step whose WY products run on the tensor cores (factor_blocked.cu)
+// in place of the FP64- or FP32-pipe step.  R_out is double*, or float* for FP32 storage.
+bool blocked_factor_applies(const Plan& P);
+cudaError_t launch_factor_blocked(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
+                                  void* R_out, int64_t ldr, int box_rows, cudaStream_t stream);
 // R_out, Q and B are double*, or float* when P.precision == 3 (FP32 storage)
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                           void* R_out, int64_t ldr, int box_rows, cudaStream_t stream);
 cudaError_t prepare_factor_batched(int precision, size_t smem);
 cudaError_t launch_stage_widen_batched(const BatchItem* items, int count, cudaStream_t stream);
 cudaError_t prepare_form_q_batched(int precision, size_t smem);
-cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work, int blocks, int precision,
-                                  size_t smem, cudaStream_t stream);
+// the persistent batched factorization: `blocks` resident blocks (factor_batched_blocks: as many
+// as fit on the device at `smem`, at most `total`) take the `total` chains in `work` through the
+// counter *next (zero before the launch)
+cudaError_t factor_batched_blocks(int precision, int total, size_t smem, int* blocks);
+cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work, int total, int* next, int blocks,
+                                  int precision, size_t smem, cudaStream_t stream);
 cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain_work, int chain_blocks,
                                   const BatchWork* const* level_work, const int* level_blocks, int depth,
                                   int precision, size_t smem, cudaStream_t stream);

@@ -53,6 +53,17 @@ def usv(m: int, n: int, log10_kappa: float, seed: int) -> np.ndarray:
     return (U * s) @ V.T
 
 
+def usv_family(m: int, n: int, log10_kappas, seed: int):
+    """usv(m, n, k, seed) for every k in log10_kappas, drawing U and V once: the same rng draws
+    in the same order, so each matrix equals usv's bit for bit.  Yields the matrices one by one."""
+    rng = np.random.default_rng(seed)
+    U = _haar_columns(m, n, rng)
+    V = _haar_columns(n, n, rng)
+    for k in log10_kappas:
+        s = np.ones(1) if n == 1 else 10.0 ** (-float(k) * np.arange(n) / (n - 1))
+        yield (U * s) @ V.T
+
+
 def sparse_symmetric(m: int, seed: int, partners: int = 4):
     """Random sparse symmetric m x m matrix, about 2 * partners nonzeros per row.
 

@@ -35,6 +35,7 @@ TSQR_ROW_MAJOR, TSQR_COL_MAJOR = 0, 1
 EXPORTED = ("tsqr_workspace_size", "tsqr_factor", "tsqr_apply_qt", "tsqr_apply_q", "tsqr_form_q",
             "tsqr_status_poll", "tsqr_handle_info", "tsqr_destroy", "tsqr_status_string", "tsqr_last_error",
             "tsqr_factor_r_noalloc", "tsqr_noalloc_status_poll", "tsqr_batch_workspace_size", "tsqr_batch_create",
+            "tsqr_batch_workspace_size_plans", "tsqr_batch_create_plans",
             "tsqr_batch_factor", "tsqr_batch_form_q", "tsqr_batch_status_poll", "tsqr_batch_destroy", "tsqr_backward")
 
 
@@ -86,8 +87,12 @@ def load(path: str = LIB_PATH):
     lib.tsqr_noalloc_status_poll.argtypes = [vp, ctypes.POINTER(vp)]
     i32, pi64, pvp = ctypes.c_int32, ctypes.POINTER(i64), ctypes.POINTER(vp)
     lib.tsqr_batch_workspace_size.argtypes = [ctypes.c_int, i32, pi64, pi64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+    lib.tsqr_batch_workspace_size_plans.argtypes = [ctypes.c_int, i32, pi64, pi64, ctypes.POINTER(Opts),
+                                                    ctypes.POINTER(sz)]
     lib.tsqr_batch_create.argtypes = [ctypes.c_int, i32, pi64, pi64, pvp, pi64, pvp, pi64, pvp, pi64, vp, sz,
                                       ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.tsqr_batch_create_plans.argtypes = [ctypes.c_int, i32, pi64, pi64, pvp, pi64, pvp, pi64, pvp, pi64, vp, sz,
+                                            ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     lib.tsqr_batch_factor.argtypes = [vp, vp]
     lib.tsqr_batch_form_q.argtypes = [vp, vp]
     lib.tsqr_batch_status_poll.argtypes = [vp, vp]
@@ -201,6 +206,31 @@ def tsqr_batch_create(dtype, count, m, n, dA, lda, dR, ldr, dQ, ldq, dWork, work
                                     _arr(vp, dQ) if dQ is not None else None,
                                     _arr(ctypes.c_int64, ldq) if ldq is not None else None,
                                     dWork, work_bytes, _opts(opts), stream, ctypes.byref(h)))
+    return h
+
+
+def _opts_array(plans):
+    arr = (Opts * len(plans))()
+    for i, o in enumerate(plans):
+        arr[i] = o
+    return arr
+
+
+def tsqr_batch_workspace_size_plans(dtype, count, m, n, plans):
+    out = ctypes.c_size_t(0)
+    _check(load().tsqr_batch_workspace_size_plans(dtype, count, _arr(ctypes.c_int64, m), _arr(ctypes.c_int64, n),
+                                                  _opts_array(plans), ctypes.byref(out)))
+    return out.value
+
+
+def tsqr_batch_create_plans(dtype, count, m, n, dA, lda, dR, ldr, dQ, ldq, dWork, work_bytes, plans, stream):
+    h = ctypes.c_void_p()
+    vp = ctypes.c_void_p
+    _check(load().tsqr_batch_create_plans(dtype, count, _arr(ctypes.c_int64, m), _arr(ctypes.c_int64, n),
+                                          _arr(vp, dA), _arr(ctypes.c_int64, lda), _arr(vp, dR),
+                                          _arr(ctypes.c_int64, ldr), _arr(vp, dQ) if dQ is not None else None,
+                                          _arr(ctypes.c_int64, ldq) if ldq is not None else None,
+                                          dWork, work_bytes, _opts_array(plans), stream, ctypes.byref(h)))
     return h
 
 
@@ -331,7 +361,9 @@ class Batch:
     captured in a CUDA graph.
     """
 
-    def __init__(self, mats, want_q=True, leaf_h=0, chain=0, arity=0, precision=0):
+    def __init__(self, mats, want_q=True, leaf_h=0, chain=0, arity=0, precision=0, plans=None):
+        """plans: an Opts per matrix (its leaf height, arity and chain length; chain 0 takes the
+        batch's shared chain length), e.g. from autotune_batch; otherwise one plan for all."""
         import torch
 
         dt = mats[0].dtype
@@ -344,16 +376,24 @@ class Batch:
         self.n = [A.shape[1] for A in self.mats]
         count = len(self.mats)
         self.opts = Opts(leaf_h=leaf_h, chain=chain, arity=arity, precision=precision, inplace=0)
-        nbytes = tsqr_batch_workspace_size(self.code, count, self.m, self.n, self.opts)
+        self.plans = list(plans) if plans is not None else None
+        if self.plans is not None:
+            assert len(self.plans) == count
+            nbytes = tsqr_batch_workspace_size_plans(self.code, count, self.m, self.n, self.plans)
+        else:
+            nbytes = tsqr_batch_workspace_size(self.code, count, self.m, self.n, self.opts)
         self.work = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
         self.R = [torch.empty((k, k), dtype=dt, device=dev) for k in self.n]
         self.Q = [torch.empty((mm, k), dtype=dt, device=dev) for mm, k in zip(self.m, self.n)] \
             if want_q else None
-        self.handle = tsqr_batch_create(
-            self.code, count, self.m, self.n, [A.data_ptr() for A in self.mats], [A.stride(0) for A in self.mats],
-            [R.data_ptr() for R in self.R], [R.stride(0) for R in self.R],
-            [Q.data_ptr() for Q in self.Q] if want_q else None, [Q.stride(0) for Q in self.Q] if want_q else None,
-            self.work.data_ptr(), nbytes, self.opts, _stream())
+        args = (self.code, count, self.m, self.n, [A.data_ptr() for A in self.mats], [A.stride(0) for A in self.mats],
+                [R.data_ptr() for R in self.R], [R.stride(0) for R in self.R],
+                [Q.data_ptr() for Q in self.Q] if want_q else None, [Q.stride(0) for Q in self.Q] if want_q else None,
+                self.work.data_ptr(), nbytes)
+        if self.plans is not None:
+            self.handle = tsqr_batch_create_plans(*args, self.plans, _stream())
+        else:
+            self.handle = tsqr_batch_create(*args, self.opts, _stream())
 
     def factor(self):
         tsqr_batch_factor(self.handle, _stream())
@@ -447,6 +487,67 @@ def autotune(m, n, precision=0, reps=2, proxy_rows=1 << 18, path=None, dtype=Non
         with open(path, "w") as fh:
             json.dump({",".join(map(str, k)): v for k, v in _TUNE_CACHE.items()}, fh, indent=1)
     return best
+
+
+_BATCH_TUNE_CACHE = {}
+
+
+def padded_width(n):
+    np_ = 16
+    while np_ < n:
+        np_ *= 2
+    return np_
+
+
+def autotune_batch(mats, precision=0, leaf_hs=(64, 96, 128, 256, 512), arities=(2, 4), reps=2):
+    """Per-shape plans for a batch, tuned on the batch itself: for each padded width present
+    (16, 32, 64), one pass of coordinate descent over the leaf height and the tree arity of the
+    matrices of that width, the others held at their current choice, timing the whole batch's
+    factor + thin Q.  Returns (an Opts per matrix, {padded width: (leaf_h, arity)}); the choices
+    are cached by (padded widths present, precision, dtype)."""
+    import torch
+
+    code = TSQR_F32 if mats[0].dtype == torch.float32 else TSQR_F64
+    widths = sorted({padded_width(A.shape[1]) for A in mats})
+    key = (tuple(widths), int(precision), int(code))
+
+    def plans_for(choice):
+        return [Opts(leaf_h=choice[padded_width(A.shape[1])][0], arity=choice[padded_width(A.shape[1])][1],
+                     chain=0, precision=precision, inplace=0) for A in mats]
+
+    def time_plans(choice):
+        try:
+            b = Batch(mats, want_q=True, plans=plans_for(choice))
+        except TsqrError:
+            return float("inf")
+        ts = []
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.factor()
+            b.form_q()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        b.close()
+        return min(ts[1:])
+
+    if key not in _BATCH_TUNE_CACHE:
+        choice = {w: (0, 2) for w in widths}  # 0: the library's default leaf height
+        best = time_plans(choice)
+        for w in widths:
+            for h in leaf_hs:
+                if h < w:
+                    continue
+                for a in arities:
+                    trial = dict(choice)
+                    trial[w] = (h, a)
+                    t = time_plans(trial)
+                    if t < best:
+                        best, choice = t, trial
+        _BATCH_TUNE_CACHE[key] = choice
+    choice = _BATCH_TUNE_CACHE[key]
+    return plans_for(choice), dict(choice)
 
 
 # ---------------------------------------------------------------- differentiation

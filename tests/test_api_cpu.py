@@ -118,6 +118,24 @@ def test_batch_plans_and_errors(lib):
     assert ei.value.status == 2
 
 
+def test_batch_per_item_plans(lib):
+    """tsqr_batch_workspace_size_plans: a plan per matrix; the workspace follows each plan (shorter
+    leaves keep more T factors), mixed precisions and bad plans are refused with the item named."""
+    m, n = [20000, 5000, 3000], [64, 16, 50]
+    O = lib.Opts
+    base = lib.tsqr_batch_workspace_size_plans(lib.TSQR_F64, 3, m, n, [O(), O(), O()])
+    assert base == lib.tsqr_batch_workspace_size(lib.TSQR_F64, 3, m, n)
+    small_leaves = lib.tsqr_batch_workspace_size_plans(lib.TSQR_F64, 3, m, n,
+                                                       [O(leaf_h=64), O(leaf_h=64), O(leaf_h=64)])
+    assert small_leaves > base
+    with pytest.raises(lib.TsqrError) as ei:
+        lib.tsqr_batch_workspace_size_plans(lib.TSQR_F64, 3, m, n, [O(), O(precision=1), O()])
+    assert ei.value.status == 2
+    with pytest.raises(lib.TsqrError) as ei:
+        lib.tsqr_batch_workspace_size_plans(lib.TSQR_F64, 3, m, n, [O(), O(), O(leaf_h=20)])
+    assert ei.value.status == 1 and "item 2" in str(ei.value)
+
+
 def test_autotune_candidates_and_key(lib):
     c = lib.candidate_opts(1 << 20, 64)
     assert len(c) >= 6

@@ -58,3 +58,16 @@ def test_host_cpu_names_the_processor():
     h = _bench_module().host_cpu()
     assert isinstance(h["model"], str) and h["model"]
     assert h["cpu_count"] == os.cpu_count()
+
+
+def test_usv_family_equals_usv():
+    """The benchmark's conditioning grid draws U and V once for all kappa; each matrix must be the
+    one usv() draws for that kappa, bit for bit."""
+    import numpy as np
+
+    from paper_0809_2407_gb300 import inputs
+
+    ks = (0.0, 4.0, 12.0)
+    fam = inputs.usv_family(500, 12, ks, 31)
+    for k, A in zip(ks, fam):
+        assert np.array_equal(A, inputs.usv(500, 12, k, 31))

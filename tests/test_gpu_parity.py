@@ -112,6 +112,34 @@ def test_default_plan_shapes(T, m, n, prec):
     check_against_oracle(A_h, R, Q, precision=prec)
 
 
+BLOCKED_SHAPES = [(40000 + 13, 64, {}), (30000, 50, {}), (50000, 33, {}), (20000, 64, {"chain": 5}),
+                  (64 * 7 + 5, 64, {"chain": 8}), (8000, 40, {}), (100000 + 77, 64, {"chain": 40})]
+
+
+@pytest.mark.parametrize("m,n,opts", BLOCKED_SHAPES)
+def test_blocked_tensor_core_step_ozaki(T, m, n, opts):
+    """Precision mode 2 with 64-row leaves at padded width 64 runs the blocked flat-tree step: FP64
+    reflectors panel by panel, the panels' WY products and the Gram entries feeding T as Ozaki
+    tensor-core products.  R, Q and Q^T b against the oracle; R alone bitwise the full R."""
+    import torch
+
+    A_h = inputs.gaussian(m, n, inputs.seed_for(30, m + n))
+    f, R, Q = run(T, A_h, precision=2, leaf_h=64, **opts)
+    assert f.info().leaf_h == 64 and f.info().np == 64
+    check_against_oracle(A_h, R, Q, precision=2)
+    b_h = inputs.gaussian(m, 1, inputs.seed_for(31, m))
+    b = torch.from_numpy(b_h.copy()).cuda()
+    f.apply_qt(b)
+    torch.cuda.synchronize()
+    assert np.abs(b[:n].cpu().numpy() - oracle.thin_qt(A_h, b_h)[:n]).max() <= 1e-12 * np.linalg.norm(b_h)
+    fr = T.Factorization(torch.from_numpy(A_h).cuda(), precision=2, leaf_h=64, r_only=True, **opts)
+    torch.cuda.synchronize()
+    assert fr.status() == T.TSQR_OK
+    assert np.array_equal(fr.R.cpu().numpy(), R)
+    fr.close()
+    f.close()
+
+
 def test_short_last_leaf_is_merged(T):
     """A last leaf with fewer than n rows joins the previous chain instead of starting one."""
     A_h = inputs.gaussian(64 * 4 + 5, 32, 77)
@@ -217,10 +245,11 @@ def test_apply_column_counts(T, k):
 ])
 def test_apply_ozaki(T, m, n, k, opts):
     """Q^T B and Q B with the chains' WY products as Ozaki splits on the tensor cores (precision
-    modes 2 and 3 from 32 columns of B on).  Mode 2 factors in native FP64 exactly as mode 0
-    does, so its Q^T B and Q B must equal mode 0's FP64-pipe results over all m rows to the
-    accuracy of the split products (2^-50 relative to the rows and columns involved); mode 3 is
-    held to the oracle's thin part and the invariants Q^T A = [R; 0], Q Q^T B = B and
+    modes 2 and 3 from 32 columns of B on).  Where mode 2 factors in native FP64 exactly as mode
+    0 does (plans other than the blocked step's: leaf height other than 64), its Q^T B and Q B
+    must equal mode 0's FP64-pipe results over all m rows to the accuracy of the split products
+    (2^-50 relative to the rows and columns involved); otherwise, and in mode 3, Q^T B is held to
+    the oracle's thin part and to the invariants Q^T A = [R; 0], Q Q^T B = B and
     Q [I; 0] = thin Q."""
     import torch
 
@@ -240,7 +269,9 @@ def test_apply_ozaki(T, m, n, k, opts):
         assert f.status() == T.TSQR_OK
         QtB = B.cpu().numpy()
         assert np.abs(QtB[:n] - oracle.thin_qt(A_h, B_h)).max() <= 1e-10
-        if prec == 2:
+        info = f.info()
+        blocked = info.np == 64 and info.leaf_h == 64 and info.arity == 2
+        if prec == 2 and not blocked:
             assert torch.equal(R, f0.R)  # the same FP64 factorization
             assert (B - B0).abs().max().item() <= 1e-12 * B0.abs().max().item()
         Ad = A.clone()
@@ -546,6 +577,46 @@ def test_batched_uneven(T, precision):
     b.close()
 
 
+def test_batched_per_item_plans(T):
+    """A plan per matrix (leaf height, arity, chain length) in one persistent launch, FP64 and
+    double-float, and the plans autotune_batch picks on the batch itself: every matrix against
+    the oracle."""
+    import torch
+
+    rng = np.random.default_rng(41)
+    ms = [int(x) for x in np.exp(rng.uniform(np.log(500), np.log(60000), 12)).astype(int)]
+    ns = [int(x) for x in rng.choice([8, 16, 32, 50, 64], 12)]
+    ms = [max(m_, n_) for m_, n_ in zip(ms, ns)]
+    hs = [inputs.gaussian(m_, n_, 6000 + i) for i, (m_, n_) in enumerate(zip(ms, ns))]
+    mats = [torch.from_numpy(a).cuda() for a in hs]
+    choice = {16: (512, 4), 32: (128, 2), 64: (64, 8)}
+    for precision in (0, 1):
+        plans = [T.Opts(leaf_h=choice[T.padded_width(n_)][0], arity=choice[T.padded_width(n_)][1],
+                        chain=(3 if i % 3 == 0 else 0), precision=precision) for i, n_ in enumerate(ns)]
+        b = T.Batch(mats, precision=precision, plans=plans)
+        b.factor()
+        b.form_q()
+        torch.cuda.synchronize()
+        assert b.status() == T.TSQR_OK
+        for a, R, Q in zip(hs, b.R, b.Q):
+            check_against_oracle(a, R.cpu().numpy(), Q.cpu().numpy(), precision=precision)
+        b.close()
+    plans, picked = T.autotune_batch(mats, leaf_hs=(64, 256), arities=(2, 4), reps=1)
+    assert set(picked) == {T.padded_width(n_) for n_ in ns}
+    b = T.Batch(mats, plans=plans)
+    b.factor()
+    b.form_q()
+    torch.cuda.synchronize()
+    assert b.status() == T.TSQR_OK
+    for a, R, Q in zip(hs, b.R, b.Q):
+        check_against_oracle(a, R.cpu().numpy(), Q.cpu().numpy())
+    b.close()
+    # mixed precisions are refused before anything launches
+    bad = [T.Opts(precision=i % 2) for i in range(len(ns))]
+    with pytest.raises(T.TsqrError):
+        T.Batch(mats, plans=bad)
+
+
 def test_batched_cuda_graph(T):
     """tsqr_batch_factor / tsqr_batch_form_q captured once in a CUDA graph and replayed."""
     import torch
@@ -643,6 +714,26 @@ def test_f32_shapes(T, m, n, opts):
     f, R, Q = run32(T, A64, **opts)
     assert f.info().dtype == T.TSQR_F32
     check_f32(A32, R, Q)
+
+
+@pytest.mark.parametrize("m,n,opts", BLOCKED_SHAPES)
+def test_blocked_tensor_core_step_f32(T, m, n, opts):
+    """FP32 storage with 64-row leaves at padded width 64 runs the blocked flat-tree step: FP32
+    reflectors panel by panel, the panels' WY products and the Gram entries feeding T as bf16x3
+    tensor-core products.  R and Q against the oracle at the FP32 bar; R alone bitwise the full R."""
+    import torch
+
+    A64 = inputs.gaussian(m, n, inputs.seed_for(32, m + n))
+    A32 = A64.astype(np.float32).astype(np.float64)
+    f, R, Q = run32(T, A64, leaf_h=64, **opts)
+    assert f.info().leaf_h == 64 and f.info().np == 64
+    check_f32(A32, R, Q)
+    fr = T.Factorization(torch.from_numpy(A64.astype(np.float32)).cuda(), leaf_h=64, r_only=True, **opts)
+    torch.cuda.synchronize()
+    assert fr.status() == T.TSQR_OK
+    assert np.array_equal(fr.R.cpu().numpy().astype(np.float64), R)
+    fr.close()
+    f.close()
 
 
 @pytest.mark.parametrize("lda_extra,offset", [(1, 0), (0, 1), (5, 3)])

@@ -314,15 +314,14 @@ def _pins_pass(lib_path):
     import ctypes
     import oracle as O
 
-    saved = O._lib
+    saved = O._load()  # the serial build, whose argument types the mutant library takes
     try:
-        O._lib = None
         lib = ctypes.CDLL(lib_path)
         for nm in ("oracle_geqr2", "oracle_org2r", "oracle_apply_qt", "oracle_apply_q", "oracle_signs",
                    "oracle_qr", "oracle_backward_error", "oracle_orthogonality"):
-            getattr(lib, nm).argtypes = getattr(O._load(), nm).argtypes
-            getattr(lib, nm).restype = getattr(O._load(), nm).restype
-        O._lib = lib
+            getattr(lib, nm).argtypes = getattr(saved, nm).argtypes
+            getattr(lib, nm).restype = getattr(saved, nm).restype
+        O._libs["serial"] = lib
         try:
             A, Q0, R0 = householder_product_matrix(60, 6, 5)
             f = O.qr(A)
@@ -342,7 +341,7 @@ def _pins_pass(lib_path):
         except Exception:
             return False
     finally:
-        O._lib = saved
+        O._libs["serial"] = saved
 
 
 def test_oracle_mutants(oracle_mod):
@@ -406,3 +405,18 @@ def test_paper_p4_binary_and_flat_trees(oracle_mod):
     Q = np.vstack([leaf[2 * i + j]["Q"] @ Q1[i][j * n:(j + 1) * n] for i in range(2) for j in range(2)])
     assert np.abs(Q @ root["R"] - A).max() <= 1e-12 * np.abs(A).max()
     assert np.abs(Q - whole["Q"]).max() <= 1e-12
+
+
+def test_openmp_timing_build_is_bitwise_serial(oracle_mod):
+    """The oracle's -fopenmp build, used only to time it on all host cores, runs each column's
+    sums in the serial order, so its R, Q and reflectors are the serial build's bit for bit."""
+    oracle = oracle_mod
+    A = inputs.gaussian(3000, 24, 77)
+    ref = oracle.qr(A)
+    oracle.set_variant("openmp")
+    try:
+        par = oracle.qr(A)
+    finally:
+        oracle.set_variant("serial")
+    for k in ("R", "Q", "V", "tau", "D"):
+        assert np.array_equal(ref[k], par[k]), k
