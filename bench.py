@@ -320,9 +320,9 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     big = int(np.argmax(ms))
 
-    def graph_run(batch_mats):
+    def graph_run(batch_mats, plans=None):
         """Times the batch's factor + thin Q replayed from a CUDA graph; accuracy of the largest."""
-        b = tsqr.Batch(batch_mats)
+        b = tsqr.Batch(batch_mats, plans=plans)
         side = torch.cuda.Stream(dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):
@@ -354,6 +354,11 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
         return t, good, acc
 
     ms_batched, ok, (be, orth) = graph_run(mats)
+    # plans per padded width tuned on this batch (leaf height and arity; chains shared)
+    t_tune = time.perf_counter()
+    plans, picked = tsqr.autotune_batch(mats, leaf_hs=(64, 128, 256, 512), arities=(2, 4), reps=1)
+    t_tune = time.perf_counter() - t_tune
+    ms_tuned, ok_t, (be_t, orth_t) = graph_run(mats, plans)
     mats32 = [A.float() for A in mats]
     ms32, ok32, (be32, orth32) = graph_run(mats32)
     del mats32
@@ -387,7 +392,15 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
     return {"matrices": count, "elements": int(sum(int(m_) * int(n_) for m_, n_ in zip(ms, ns))),
             "workload": "m log-uniform in [1e4, 2^18], n in {8,16,32,64}, N(0,1), fp64, factor + thin Q",
             "value": fl / (ms_batched / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms_batched,
-            "launch": "one factor launch + one thin-Q launch per tree depth + one chain launch, CUDA graph",
+            "launch": "one persistent factor launch (resident blocks take chains longest first from a device "
+                      "queue) + one thin-Q launch per tree depth + one chain launch, CUDA graph; default plans",
+            "tuned": {"value": fl / (ms_tuned / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms_tuned,
+                      "speedup_vs_default_plans": ms_batched / ms_tuned, "status_ok": ok_t,
+                      "plans": {"np%d" % w: {"leaf_h": h or "default", "arity": a} for w, (h, a) in picked.items()},
+                      "tuning_seconds": t_tune,
+                      "how": "autotune_batch: per padded width, coordinate descent over leaf height {64, 128, 256, "
+                             "512} and arity {2, 4} timing this batch's factor + thin Q",
+                      "largest": {"backward_error": be_t, "orthogonality": orth_t}},
             "loop_value": fl / (ms_loop / 1e3) / 1e9, "loop_ms_per_step": ms_loop,
             "speedup_vs_loop": ms_loop / ms_batched, "status_ok": ok,
             "largest": {"m": int(ms[big]), "n": int(ns[big]), "backward_error": be, "orthogonality": orth},
