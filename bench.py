@@ -562,6 +562,41 @@ def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, war
     return out
 
 
+def run_tree_levels(tsqr, torch, dev, stream, sptr, n=64, levels=(4, 5, 6, 7, 8), reps=5):
+    """Time per level of the reduction tree: 2^L chains of one 64-row leaf each under a binary
+    tree of L levels (the leaves run as one wave, the levels one after another, each a single
+    structured node step per pair), factor time against L; the slope is the time per level."""
+    import numpy as np
+
+    pts = []
+    for L in levels:
+        m = 64 * (1 << L)
+        A = torch.from_numpy(np.random.default_rng(9).standard_normal((m, n))).to(dev)
+        R = torch.empty((n, n), dtype=torch.float64, device=dev)
+        o = tsqr.Opts(leaf_h=64, chain=1, arity=2)
+        nb = tsqr.tsqr_workspace_size(tsqr.TSQR_F64, m, n, o)
+        w = torch.empty(nb, dtype=torch.uint8, device=dev)
+        ts = []
+        for it in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = tsqr.tsqr_factor(tsqr.TSQR_F64, tsqr.TSQR_ROW_MAJOR, m, n, A.data_ptr(), n, R.data_ptr(), n,
+                                 w.data_ptr(), nb, o, sptr)
+            e1.record(stream)
+            tsqr.tsqr_destroy(h)
+            torch.cuda.synchronize()
+            if it >= 2:
+                ts.append(e0.elapsed_time(e1))
+        pts.append((L, min(ts)))
+        del A, R, w
+    x = np.array([p[0] for p in pts], dtype=float)
+    y = np.array([p[1] for p in pts])
+    slope = float(np.polyfit(x, y, 1)[0])
+    return {"ms_per_level": slope, "n": n, "points_ms": {"levels_%d" % L: t for L, t in pts},
+            "how": "factor of 2^L x 64 rows as 2^L one-leaf chains under a binary tree of L levels (FP64); "
+                   "least-squares slope of time against L"}
+
+
 COND_FORMS = (("fp64", 0, False), ("double_float", 1, False), ("ozaki_wy", 2, False), ("df_ozaki_wy", 3, False),
               ("fp32", 0, True))
 
@@ -712,6 +747,9 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 3],
                     help="arithmetic mode of the main line (0 native FP64; 1 and 2 are for profiling)")
     ap.add_argument("--fp32", action="store_true", help="main line in FP32 storage (for profiling)")
+    ap.add_argument("--leaf-h", type=int, default=0,
+                    help="leaf height of the main line (64 selects the blocked tensor-core factor step of "
+                         "precision 2 and FP32 storage; for profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -827,7 +865,7 @@ def main():
                 "launches": launches}
 
     pipes = measure_pipe_peaks()
-    main_mode = run_mode(args.precision, args.steps, args.warmup, True, f32=args.fp32)
+    main_mode = run_mode(args.precision, args.steps, args.warmup, True, f32=args.fp32, leaf_h=args.leaf_h)
     # end to end right after the main line, before the other sections fill host and device memory
     e2e = None
     if not args.no_e2e and not args.fp32:
@@ -985,6 +1023,10 @@ def main():
     if not args.no_shapes and world == 1:
         shapes = run_shapes(tsqr, torch, dev, stream, sptr, m)
 
+    tree_levels = None
+    if not args.no_shapes and world == 1:
+        tree_levels = run_tree_levels(tsqr, torch, dev, stream, sptr)
+
     conditioning = None
     if not args.no_conditioning and world == 1:
         conditioning = run_conditioning(tsqr, torch, dev, stream, sptr, m, n)
@@ -1013,7 +1055,7 @@ def main():
                "backward_error": be, "orthogonality": orth,
                "kernel_ms": {"factor": f_ms, "form_q": q_ms, "apply_qt": a_ms},
                "roofline": roofline, "precision_forms": forms, "apply_wide": apply_wide, "batched": batched,
-               "shapes": shapes, "conditioning": conditioning,
+               "shapes": shapes, "conditioning": conditioning, "tree_levels": tree_levels,
                "autograd": autograd, "r_alone": r_alone, "library_context": library, "cpu_baseline": cpu,
                "e2e": e2e,
                "gpu_launches": main_mode["launches"] * args.steps, "clocks": clocks}

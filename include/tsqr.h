@@ -87,7 +87,13 @@ typedef struct {
                         3 = double-float factorization, and Q^T B / Q B with fewer than 32
                             columns; the tensor-core products as in mode 2 (other shapes run
                             mode 1).
-                        Batches run mode 2 as 0 and mode 3 as 1. */
+                        With leaf_h = 64 at n in 33..64 and a binary tree, mode 2 factors by the
+                        blocked step: FP64 reflectors per 16-column panel, the panel's WY
+                        products and the Gram entries feeding T as Ozaki splits on the tensor
+                        cores (FP32 storage likewise, with bf16x3 terms).
+                        Batches factor mode 2 as 0 and mode 3 as 1, and form the thin Q of their
+                        matrices of n in 33..64 (leaf_h <= 128) with the tensor-core products;
+                        FP32-storage batches likewise with bf16x3 terms. */
   int32_t inplace;   /* nonzero: the leaf reflectors overwrite A (Sec. 4.2 storage) and A's
                         upper triangles hold intermediate R factors; zero: A is read only */
   int32_t r_only;    /* nonzero: compute R alone (the paper times R alone and Q with R apart,

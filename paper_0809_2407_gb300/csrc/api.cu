@@ -20,6 +20,13 @@ struct tsqr_batch_s {
   int count = 0, precision = 0;
   int total_chains = 0, max_depth = 0;
   int factor_blocks = 1;  // resident blocks of the persistent factor launch
+  // thin Q: chains on the FP64/FP32-pipe kernel, then chains whose WY products run on the tensor
+  // cores (tc: 0 none, 1 Ozaki, 2 Ozaki from double-float slots, 3 bf16x3)
+  const tsqr::BatchWork* d_formq_work = nullptr;
+  int formq_blocks = 0;
+  const tsqr::BatchWork* d_tc_work = nullptr;
+  int tc_blocks = 0, tc = 0;
+  size_t smem_tc = 0;
   size_t smem_factor = 0, smem_formq = 0;
   tsqr::BatchItem* d_items = nullptr;
   tsqr::BatchWork* d_chain_work = nullptr;
@@ -611,7 +618,9 @@ struct BatchPlan {
   std::vector<Plan> plans;
   std::vector<Layout> layouts;
   std::vector<size_t> item_off;
-  size_t items_off = 0, chain_work_off = 0, level_work_off = 0, counters_off = 0, status_off = 0, total = 0;
+  size_t items_off = 0, chain_work_off = 0, formq_work_off = 0, level_work_off = 0, counters_off = 0, status_off = 0,
+         total = 0;
+  int requested_precision = 0;  // before the Ozaki forms map to their factorization's arithmetic
   int total_chains = 0, max_depth = 0, level_items = 0;
   size_t counters_bytes = 0;
 };
@@ -631,8 +640,9 @@ tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n,
     else if (opts) o = *opts;
     if (o.inplace) return fail(TSQR_ERR_UNSUPPORTED, "batches keep A read-only (inplace is not supported)");
     if (o.r_only) return fail(TSQR_ERR_UNSUPPORTED, "batches keep Q (r_only is not supported)");
-    // the batched thin Q runs on the FP64-pipe or FP32-pipe kernels: the Ozaki forms run as their
-    // factorization's arithmetic
+    if (i == 0) bp->requested_precision = o.precision;
+    // the batched factorization runs the Ozaki forms in their factorization's arithmetic; their
+    // thin Q keeps the tensor-core products (items of padded width 64, leaf height <= 128)
     if (o.precision == tsqr::kPrecOzaki) o.precision = tsqr::kPrecF64;
     if (o.precision == tsqr::kPrecDFOzaki) o.precision = tsqr::kPrecDF;
     if (f32 && o.precision != 0)
@@ -681,6 +691,7 @@ tsqr_status_t make_batch_plan(int32_t count, const int64_t* m, const int64_t* n,
   bp->status_off = take(256);  // status word, then the persistent factor launch's work counter
   bp->items_off = take(sizeof(tsqr::BatchItem) * (size_t)count);
   bp->chain_work_off = take(sizeof(tsqr::BatchWork) * (size_t)bp->total_chains);
+  bp->formq_work_off = take(sizeof(tsqr::BatchWork) * (size_t)bp->total_chains);
   bp->level_work_off = take(sizeof(tsqr::BatchWork) * (size_t)(bp->level_items > 0 ? bp->level_items : 1));
   bp->counters_off = take(bp->counters_bytes);
   for (int i = 0; i < count; ++i) bp->item_off[i] = take(bp->layouts[i].total);
@@ -814,6 +825,27 @@ static tsqr_status_t batch_create(tsqr_dtype_t dtype, int32_t count, const int64
   };
   std::stable_sort(chain_work.begin(), chain_work.end(),
                    [&](const tsqr::BatchWork& a, const tsqr::BatchWork& c) { return chain_cost(a) > chain_cost(c); });
+  // thin-Q chain lists: the tensor-core kernel takes the items of padded width 64 and leaf height
+  // <= 128 when the batch asked for a tensor-core form (precision 2 or 3, or FP32 storage)
+  b->tc = f32 ? 3 : (bp.requested_precision == tsqr::kPrecOzaki ? 1 : (bp.requested_precision == tsqr::kPrecDFOzaki ? 2 : 0));
+  std::vector<tsqr::BatchWork> formq_list, tc_list;
+  for (const tsqr::BatchWork& wk : chain_work) {
+    const Plan& P = bp.plans[wk.item];
+    if (b->tc && P.np == 64 && P.h <= 128)
+      tc_list.push_back(wk);
+    else
+      formq_list.push_back(wk);
+  }
+  for (const tsqr::BatchWork& wk : tc_list) {
+    const Plan& P = bp.plans[wk.item];
+    b->smem_tc = std::max(b->smem_tc, b->tc == 3 ? tsqr::formq_bf16x3_smem_bytes(P) : tsqr::formq_ozaki_smem_bytes(P));
+  }
+  b->formq_blocks = (int)formq_list.size();
+  b->tc_blocks = (int)tc_list.size();
+  formq_list.insert(formq_list.end(), tc_list.begin(), tc_list.end());
+  tsqr::BatchWork* d_formq = reinterpret_cast<tsqr::BatchWork*>(w + bp.formq_work_off);
+  b->d_formq_work = d_formq;
+  b->d_tc_work = d_formq + b->formq_blocks;
   // tree steps of the batched thin Q, by distance d from each item's root
   std::vector<std::vector<tsqr::BatchWork>> levels(bp.max_depth);
   for (int i = 0; i < count; ++i) {
@@ -840,10 +872,15 @@ static tsqr_status_t batch_create(tsqr_dtype_t dtype, int32_t count, const int64
   if (e == cudaSuccess && !level_flat.empty())
     e = cudaMemcpyAsync(d_levels, level_flat.data(), sizeof(tsqr::BatchWork) * level_flat.size(),
                         cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_formq, formq_list.data(), sizeof(tsqr::BatchWork) * formq_list.size(),
+                        cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);  // the host arrays above are about to go away
   if (e == cudaSuccess) e = tsqr::prepare_factor_batched(b->precision, b->smem_factor);
   if (e == cudaSuccess) e = tsqr::factor_batched_blocks(b->precision, b->total_chains, b->smem_factor, &b->factor_blocks);
   if (e == cudaSuccess) e = tsqr::prepare_form_q_batched(b->precision, b->smem_formq);
+  if (e == cudaSuccess && b->tc_blocks > 0)
+    e = b->tc == 3 ? tsqr::prepare_formq_bf16x3_batched(b->smem_tc) : tsqr::prepare_formq_ozaki_batched(b->tc == 2, b->smem_tc);
   if (e != cudaSuccess) {
     delete b;
     return cuda_fail(e, "batch descriptor upload");
@@ -889,9 +926,12 @@ tsqr_status_t tsqr_batch_factor(tsqr_batch_t b, tsqr_stream_t stream) {
 tsqr_status_t tsqr_batch_form_q(tsqr_batch_t b, tsqr_stream_t stream) {
   if (!b) return fail(TSQR_ERR_INVALID_ARG, "batch is NULL");
   if (!b->has_q) return fail(TSQR_ERR_INVALID_ARG, "the batch was created without Q outputs");
-  cudaError_t e = tsqr::launch_form_q_batched(b->d_items, b->d_chain_work, b->total_chains, b->d_level_work.data(),
-                                              b->level_blocks.data(), b->max_depth, b->precision, b->smem_formq,
-                                              static_cast<cudaStream_t>(stream));
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = tsqr::launch_form_q_batched(b->d_items, b->d_formq_work, b->formq_blocks, b->d_level_work.data(),
+                                              b->level_blocks.data(), b->max_depth, b->precision, b->smem_formq, cs);
+  if (e == cudaSuccess && b->tc_blocks > 0)
+    e = b->tc == 3 ? tsqr::launch_formq_bf16x3_batched(b->d_items, b->d_tc_work, b->tc_blocks, b->smem_tc, cs)
+                   : tsqr::launch_formq_ozaki_batched(b->d_items, b->d_tc_work, b->tc_blocks, b->tc == 2, b->smem_tc, cs);
   if (e != cudaSuccess) return cuda_fail(e, "batched form_q launch");
   return TSQR_OK;
 }

@@ -385,6 +385,7 @@ static cudaError_t launch_form_q_batched_t(const BatchItem* items, const BatchWo
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if (chain_blocks == 0) return cudaSuccess;  // every chain runs on the tensor-core kernel
   formq_chain_batched_kernel<Ar><<<chain_blocks, kThreads, smem, stream>>>(items, chain_work);
   return cudaGetLastError();
 }
@@ -421,15 +422,14 @@ size_t formq_ozaki_smem_bytes(const Plan& P) {
 }
 
 
+// Chain g of one factorization (the body of formq_ozaki_kernel and of its batched form).
 template <bool kPairs>
-__global__ void __launch_bounds__(kOzT, 1)
-    formq_ozaki_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
-                       int64_t ldq, int box_rows) {
-  extern __shared__ char smem_raw[];
+__device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, const Plan& P, const Store& st,
+                                                  double* __restrict__ Q, int64_t ldq, int box_rows, int g,
+                                                  char* smem_raw) {
   OzSmem z = carve_ozaki(smem_raw, P.h);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int np = 64, n = P.n, h = P.h;
-  const int g = blockIdx.x;
   if (tid == 0) {
     for (int b = 0; b < 4; ++b) mbar_init(z.bars + b, 1);
     fence_mbar_init();
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(kOzT, 1)
         mbar_arrive_expect_tx(z.bars + 0, (uint32_t)h * np * 8);
         for (int pnl = 0; pnl < np / 16; ++pnl)
           for (int r = 0; r < h; r += box_rows)
-            tma_load_2d(z.Y.base + (size_t)pnl * h * 128 + (size_t)r * 128, &mapV, z.bars + 0, pnl * 16,
+            tma_load_2d(z.Y.base + (size_t)pnl * h * 128 + (size_t)r * 128, mapV_p, z.bars + 0, pnl * 16,
                         (int)(row0 + r));
       }
       // ---- C (B operand): output column j, k-th entry C[k][j]
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(kOzT, 1)
     } else {
       // ---- first leaf (V unit lower trapezoidal; the tile's rows 0..n-1 hold R above the
       //      diagonal): Q_rows = [C; 0] - V (T (V_top^T C)) as three Ozaki passes
-      if (!tile_load(z.Y, &mapV, z.bars, y_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
+      if (!tile_load(z.Y, mapV_p, z.bars, y_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
         alive = false;
         break;
       }
@@ -616,6 +616,42 @@ __global__ void __launch_bounds__(kOzT, 1)
   __syncthreads();
   oz::fence_after_sync();
   if (warp == 0) oz::tmem_dealloc(tmem, oz::kTmemCols);
+}
+
+template <bool kPairs>
+__global__ void __launch_bounds__(kOzT, 1)
+    formq_ozaki_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
+                       int64_t ldq, int box_rows) {
+  extern __shared__ char smem_raw[];
+  formq_ozaki_chain<kPairs>(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
+}
+
+// Batched: block b takes chain work[b].chain of item work[b].item (items whose thin Q runs on the
+// tensor cores: padded width 64, leaf height <= 128).
+template <bool kPairs>
+__global__ void __launch_bounds__(kOzT, 1)
+    formq_ozaki_batched_kernel(const BatchItem* __restrict__ items, const BatchWork* __restrict__ work) {
+  extern __shared__ char smem_raw[];
+  const BatchWork w = work[blockIdx.x];
+  const BatchItem& it = items[w.item];
+  formq_ozaki_chain<kPairs>(&it.mapV, it.plan, it.store, static_cast<double*>(it.Q), it.ldq, it.box_rows, w.chain,
+                            smem_raw);
+}
+
+cudaError_t prepare_formq_ozaki_batched(bool pairs, size_t smem) {
+  return pairs ? cudaFuncSetAttribute(formq_ozaki_batched_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)
+               : cudaFuncSetAttribute(formq_ozaki_batched_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem);
+}
+
+cudaError_t launch_formq_ozaki_batched(const BatchItem* items, const BatchWork* work, int blocks, bool pairs,
+                                       size_t smem, cudaStream_t stream) {
+  if (pairs)
+    formq_ozaki_batched_kernel<true><<<blocks, kOzT, smem, stream>>>(items, work);
+  else
+    formq_ozaki_batched_kernel<false><<<blocks, kOzT, smem, stream>>>(items, work);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------

@@ -55,6 +55,15 @@ cudaError_t launch_factor_batched(const BatchItem* items, const BatchWork* work,
 cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain_work, int chain_blocks,
                                   const BatchWork* const* level_work, const int* level_blocks, int depth,
                                   int precision, size_t smem, cudaStream_t stream);
+// Batched thin Q with the chains' WY products on the tensor cores, for the items of padded width
+// 64 and leaf height <= 128: Ozaki splits (FP64 storage; pairs: double-float slots) or bf16x3 terms
+// (FP32 storage); one block per chain in `work` (after the FP64- or FP32-pipe tree levels).
+cudaError_t prepare_formq_ozaki_batched(bool pairs, size_t smem);
+cudaError_t launch_formq_ozaki_batched(const BatchItem* items, const BatchWork* work, int blocks, bool pairs,
+                                       size_t smem, cudaStream_t stream);
+cudaError_t prepare_formq_bf16x3_batched(size_t smem);
+cudaError_t launch_formq_bf16x3_batched(const BatchItem* items, const BatchWork* work, int blocks, size_t smem,
+                                        cudaStream_t stream);
 cudaError_t launch_form_q(const CUtensorMap& mapV, const Plan& P, const Store& st, void* Q, int64_t ldq,
                           int box_rows, cudaStream_t stream);
 cudaError_t launch_apply_qt(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, void* B,

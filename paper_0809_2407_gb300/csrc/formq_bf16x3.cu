@@ -25,14 +25,13 @@ namespace {
 
 using namespace bf3;
 
-__global__ void __launch_bounds__(kT3, 1)
-    formq_bf16x3_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, float* __restrict__ Q,
-                        int64_t ldq, int box_rows) {
-  extern __shared__ char smem_raw[];
+// Chain g of one factorization (the body of formq_bf16x3_kernel and of its batched form).
+__device__ __forceinline__ void formq_bf16x3_chain(const CUtensorMap* mapV_p, const Plan& P, const Store& st,
+                                                   float* __restrict__ Q, int64_t ldq, int box_rows, int g,
+                                                   char* smem_raw) {
   Tc3Smem z = carve_tc3(smem_raw, P.h);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int np = 64, n = P.n, h = P.h;
-  const int g = blockIdx.x;
   if (tid == 0) {
     for (int b = 0; b < 3; ++b) mbar_init(z.bars + b, 1);
     fence_mbar_init();
@@ -71,7 +70,7 @@ __global__ void __launch_bounds__(kT3, 1)
         mbar_arrive_expect_tx(z.bars + 0, (uint32_t)h * np * 8);
         for (int pnl = 0; pnl < np / 16; ++pnl)
           for (int r = 0; r < h; r += box_rows)
-            tma_load_2d(z.Y.base + (size_t)pnl * h * 128 + (size_t)r * 128, &mapV, z.bars + 0, pnl * 16,
+            tma_load_2d(z.Y.base + (size_t)pnl * h * 128 + (size_t)r * 128, mapV_p, z.bars + 0, pnl * 16,
                         (int)(row0 + r));
       }
       // ---- M = T C on the FP32 pipe (T upper triangular).  M feeds C -= M, which carries the
@@ -119,7 +118,7 @@ __global__ void __launch_bounds__(kT3, 1)
       float* T = reinterpret_cast<float*>(z.a);  // the A terms are free here
       float* X = T + np * np;
       for (int i = tid; i < np * np; i += kT3) T[i] = Tg[i].hi;
-      if (!tile_load(z.Y, &mapV, z.bars, y_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
+      if (!tile_load(z.Y, mapV_p, z.bars, y_phase, np, row0, h, 0, box_rows, st.status, z.flag)) {
         alive = false;
         break;
       }
@@ -168,6 +167,21 @@ __global__ void __launch_bounds__(kT3, 1)
   if (warp == 0) oz::tmem_dealloc(tmem, kTmemCols3);
 }
 
+__global__ void __launch_bounds__(kT3, 1)
+    formq_bf16x3_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, float* __restrict__ Q,
+                        int64_t ldq, int box_rows) {
+  extern __shared__ char smem_raw[];
+  formq_bf16x3_chain(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
+}
+
+__global__ void __launch_bounds__(kT3, 1)
+    formq_bf16x3_batched_kernel(const BatchItem* __restrict__ items, const BatchWork* __restrict__ work) {
+  extern __shared__ char smem_raw[];
+  const BatchWork w = work[blockIdx.x];
+  const BatchItem& it = items[w.item];
+  formq_bf16x3_chain(&it.mapV, it.plan, it.store, static_cast<float*>(it.Q), it.ldq, it.box_rows, w.chain, smem_raw);
+}
+
 }  // namespace
 
 size_t formq_bf16x3_smem_bytes(const Plan& P) {
@@ -176,6 +190,16 @@ size_t formq_bf16x3_smem_bytes(const Plan& P) {
 }
 
 bool bf16x3_form_q_applies(const Plan& P) { return P.precision == kPrecF32 && P.np == 64 && P.h <= 128; }
+
+cudaError_t prepare_formq_bf16x3_batched(size_t smem) {
+  return cudaFuncSetAttribute(formq_bf16x3_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_formq_bf16x3_batched(const BatchItem* items, const BatchWork* work, int blocks, size_t smem,
+                                        cudaStream_t stream) {
+  formq_bf16x3_batched_kernel<<<blocks, kT3, smem, stream>>>(items, work);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_formq_bf16x3_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, float* Q, int64_t ldq,
                                        int box_rows, cudaStream_t stream) {

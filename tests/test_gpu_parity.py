@@ -556,9 +556,10 @@ def test_full_size_properties(T, prec):
     f.close()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_batched_uneven(T, precision):
-    """One launch for many matrices of uneven m and n (block Krylov / s-step batches)."""
+    """One launch for many matrices of uneven m and n (block Krylov / s-step batches); in modes 2
+    and 3 the thin Q of the matrices of n in 33..64 runs its WY products on the tensor cores."""
     import torch
 
     rng = np.random.default_rng(4)
@@ -589,7 +590,7 @@ def test_batched_per_item_plans(T):
     ms = [max(m_, n_) for m_, n_ in zip(ms, ns)]
     hs = [inputs.gaussian(m_, n_, 6000 + i) for i, (m_, n_) in enumerate(zip(ms, ns))]
     mats = [torch.from_numpy(a).cuda() for a in hs]
-    choice = {16: (512, 4), 32: (128, 2), 64: (64, 8)}
+    choice = {16: (512, 4), 32: (128, 2), 64: (128, 4)}
     for precision in (0, 1):
         plans = [T.Opts(leaf_h=choice[T.padded_width(n_)][0], arity=choice[T.padded_width(n_)][1],
                         chain=(3 if i % 3 == 0 else 0), precision=precision) for i, n_ in enumerate(ns)]
