@@ -562,10 +562,11 @@ def run_shapes(tsqr, torch, dev, stream, sptr, m, ns=(16, 32, 128), steps=3, war
     return out
 
 
-def run_tree_levels(tsqr, torch, dev, stream, sptr, n=64, levels=(4, 5, 6, 7, 8), reps=5):
+def run_tree_levels(tsqr, torch, dev, stream, sptr, n=64, levels=(3, 4, 5, 6, 7), reps=5):
     """Time per level of the reduction tree: 2^L chains of one 64-row leaf each under a binary
-    tree of L levels (the leaves run as one wave, the levels one after another, each a single
-    structured node step per pair), factor time against L; the slope is the time per level."""
+    tree of L levels (at most 128 chains, so the leaves run as one wave on the GPU's SMs; the
+    levels run one after another, each a structured node step per pair), factor time against L;
+    the slope is the time per level."""
     import numpy as np
 
     pts = []
