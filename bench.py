@@ -66,8 +66,9 @@ def load_peaks():
 
 
 # DRAM bytes (read + write) of one factor_kernel<ArithF64> launch, from an ncu capture at
-# m = 524288, n = 64 (700.4 MB), scaled by rows to m = 4194304: A is read once and V and T are
-# written once, so traffic grows in proportion to m.  Only valid for the kernel as captured.
+# m = 524288, n = 64 (700.4 MB, taken with the structured binary node step), scaled by rows to
+# m = 4194304: A is read once and V and T are written once, so traffic grows in proportion to m.
+# Only valid for the kernel as captured.
 FACTOR_F64_TRAFFIC = {(4194304, 64): 8 * 700.40e6}
 
 # FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s);
@@ -320,9 +321,9 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     big = int(np.argmax(ms))
 
-    def graph_run(batch_mats, plans=None):
+    def graph_run(batch_mats, plans=None, precision=0):
         """Times the batch's factor + thin Q replayed from a CUDA graph; accuracy of the largest."""
-        b = tsqr.Batch(batch_mats, plans=plans)
+        b = tsqr.Batch(batch_mats, plans=plans, precision=precision)
         side = torch.cuda.Stream(dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):
@@ -359,6 +360,13 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
     plans, picked = tsqr.autotune_batch(mats, leaf_hs=(64, 128, 256, 512), arities=(2, 4), reps=1)
     t_tune = time.perf_counter() - t_tune
     ms_tuned, ok_t, (be_t, orth_t) = graph_run(mats, plans)
+    # precision forms of the batch: the Ozaki forms' thin Q takes the tensor cores for n = 64
+    forms = {}
+    for nm, prec in (("double_float", 1), ("ozaki_wy", 2), ("df_ozaki_wy", 3)):
+        t_f, ok_f, (be_f, orth_f) = graph_run(mats, None, prec)
+        forms[nm] = {"precision": prec, "value": fl / (t_f / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": t_f,
+                     "speedup_vs_fp64_batched": ms_batched / t_f, "status_ok": ok_f,
+                     "largest": {"backward_error": be_f, "orthogonality": orth_f}}
     mats32 = [A.float() for A in mats]
     ms32, ok32, (be32, orth32) = graph_run(mats32)
     del mats32
@@ -401,6 +409,7 @@ def run_batched(tsqr, torch, dev, stream, sptr, args, count=512, seed=20084000):
                       "how": "autotune_batch: per padded width, coordinate descent over leaf height {64, 128, 256, "
                              "512} and arity {2, 4} timing this batch's factor + thin Q",
                       "largest": {"backward_error": be_t, "orthogonality": orth_t}},
+            "forms": forms,
             "loop_value": fl / (ms_loop / 1e3) / 1e9, "loop_ms_per_step": ms_loop,
             "speedup_vs_loop": ms_loop / ms_batched, "status_ok": ok,
             "largest": {"m": int(ms[big]), "n": int(ns[big]), "backward_error": be, "orthogonality": orth},

@@ -432,11 +432,16 @@ def test_panels_staged_and_inplace(T):
     check_against_oracle(A_h, R1, Q1)
 
 
-def test_node_structure_eq_fact_2rs(T):
-    """Tree-node reflectors: lower blocks upper triangular (eq. fact_2rs), T upper triangular."""
-    A_h = inputs.gaussian(2048, 16, 5)
-    f, R, Q = run(T, A_h, leaf_h=128, chain=1, arity=4)
+@pytest.mark.parametrize("m,n,h,arity", [(2048, 16, 128, 4), (2048, 16, 128, 2), (4096, 32, 128, 2),
+                                         (4096 + 64, 64, 64, 2), (6000, 50, 96, 2)])
+def test_node_structure_eq_fact_2rs(T, m, n, h, arity):
+    """Tree-node reflectors: lower blocks upper triangular (eq. fact_2rs), T upper triangular,
+    for k-ary nodes and for the structured binary node step; R and Q against the oracle."""
+    A_h = inputs.gaussian(m, n, 5)
+    f, R, Q = run(T, A_h, leaf_h=h, chain=1, arity=arity)
+    check_against_oracle(A_h, R, Q)
     info = f.info()
+    assert info.arity == arity and info.depth >= 3
     np_ = info.np
     Y = workspace_view(f, info.node_y, info.tree_nodes * (info.arity - 1) * np_ * np_)
     Y = Y.reshape(info.tree_nodes, info.arity - 1, np_, np_)
