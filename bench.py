@@ -907,7 +907,8 @@ def main():
     fp64_peak = pipes.get("fp64_tflops") or FP64_PEAK_TFLOPS
     roofline = {"bound": "alu", "kernel": dom + "_kernel", "achieved": achieved_tf, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak,
-                "traffic": FACTOR_F64_TRAFFIC.get((m, n)) if (dom == "factor" and args.precision == 0) else None,
+                "traffic": FACTOR_F64_TRAFFIC.get((m, n))
+                if (dom == "factor" and args.precision == 0 and not args.fp32 and args.leaf_h == 0) else None,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": ("FP64 pipe, measured in this run by the FMA-chain probe (%s); nominal 152 SMs x 2 "
                                 "DFMA/clk x 2.07 GHz = %.3f TFLOP/s" % (pipes.get("how"), FP64_PEAK_TFLOPS))

@@ -903,6 +903,45 @@ def test_degenerate_inputs(T, kind, prec):
         assert R[0, 0] == 0.0 and R[39, 39] == 0.0
 
 
+@pytest.mark.parametrize("kind", ["zero_matrix", "zero_first_last", "zero_middle", "duplicate_columns", "nan",
+                                  "scale_-600", "scale_600"])
+def test_blocked_step_degenerate_inputs(T, kind):
+    """The blocked tensor-core step (precision mode 2, 64-row leaves) on the degenerate cases of
+    the method: H = I reflectors, exact rank deficiency, NaN propagating without a fault, and
+    entries near the ends of the exponent range (the Ozaki products scale every operand row and
+    column by its own exponent)."""
+    m, n = 6000, 50
+    A_h = inputs.gaussian(m, n, inputs.seed_for(33, n))
+    if kind == "zero_matrix":
+        A_h[:] = 0.0
+    elif kind == "zero_first_last":
+        A_h[:, [0, n - 1]] = 0.0
+    elif kind == "zero_middle":
+        A_h[:, 20] = 0.0
+    elif kind == "duplicate_columns":
+        A_h[:, 5] = A_h[:, 3]
+        A_h[:, 40] = 2.0 * A_h[:, 17]
+    elif kind == "nan":
+        A_h[3333, 7] = np.nan
+    else:
+        A_h *= 2.0 ** int(kind.split("_")[1])
+    f, R, Q = run(T, A_h, precision=2, leaf_h=64, chain=5)
+    if kind == "nan":
+        assert np.isnan(R).any()
+        return
+    assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) >= 0.0)
+    assert oracle.orthogonality(Q) <= TOL_ORTH
+    if kind == "zero_matrix":
+        assert np.all(R == 0.0)
+        assert np.array_equal(Q[:n], np.eye(n)) and np.all(Q[n:] == 0.0)
+        return
+    assert oracle.backward_error(A_h, Q, R) <= TOL_BACK
+    if kind in ("zero_first_last", "scale_-600", "scale_600"):
+        ref = oracle.qr(A_h)
+        s = 2.0 ** -int(kind.split("_")[1]) if kind.startswith("scale") else 1.0
+        assert np.abs((R - ref["R"]) * s).max() <= 1e-10 * np.abs(ref["R"] * s).max()
+
+
 @pytest.mark.parametrize("scale_exp", [-600, -90, 90, 600])
 def test_extreme_scaling(T, scale_exp, prec):
     """Entries near the ends of the exponent range: the FP64 norms rescale by the largest
