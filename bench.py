@@ -98,6 +98,20 @@ def measure_pipe_peaks():
         out[name] = v.value if lib.tsqr_probe_fma_tflops(fp32, iters, ctypes.byref(v)) == 0 else None
     out["how"] = ("8 independent FMA chains per thread, 8 blocks x 256 threads per SM, CUDA events over the "
                   "second of two launches (about 0.1 s each)")
+    # FP64 with 1, 2, 4, 8 warps per SM: what a single warp can issue (the blocked factor's panel
+    # runs on one warp)
+    lib.tsqr_probe_fma_tflops_warps.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                                ctypes.POINTER(ctypes.c_double)]
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    byw = {"how": "one block of 32 x warps threads per SM, 8 independent FP64 FMA chains per thread; lanes per "
+                  "clock at the 2.07 GHz maximum SM clock"}
+    for w in (1, 2, 4, 8):
+        v = ctypes.c_double(0.0)
+        if lib.tsqr_probe_fma_tflops_warps(0, w, 20000 * 8 // w, ctypes.byref(v)) == 0:
+            byw["warps_%d" % w] = {"tflops": v.value, "fma_lanes_per_clock_per_sm": v.value * 1e12 / 2 / sms / 2.07e9}
+    out["fp64_by_warps_per_sm"] = byw
     return out
 
 

@@ -260,15 +260,10 @@ __device__ __forceinline__ void panel_column(const Tile& S, int c0, int jn, doub
     if (normal) {
       nrm = sqrt(full);
     } else {  // rescale by the largest magnitude (keeps NaN)
-      double mx = fabs(alpha);
-      const double m0 = fabs(x0), m1 = fabs(x1);
-      if (!(m0 <= mx)) mx = m0;
-      if (!(m1 <= mx)) mx = m1;
+      // NaN-propagating max, the same on every lane, so the branch below stays warp-uniform
+      double mx = max_nan(fabs(alpha), max_nan(fabs(x0), fabs(x1)));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double y = __shfl_xor_sync(0xffffffffu, mx, o);
-        if (!(y <= mx)) mx = y;
-      }
+      for (int o = 16; o > 0; o >>= 1) mx = max_nan(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if (mx == 0.0 || !(mx <= 1.7976931348623157e308)) {
         nrm = mx;
       } else {

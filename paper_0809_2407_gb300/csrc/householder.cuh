@@ -40,6 +40,11 @@ __device__ __forceinline__ bool skip_row(int kind, int r, int j, int np) {
 template <class Ar>
 __device__ inline void reflector_warp(const Tile& S, int kind, int N, int np, int j, typename Ar::E* sc);
 
+// max(a, b), NaN when either is NaN: unlike a comparison-and-select, the result does not depend
+// on the order of the operands, so every lane of a warp reduction ends with the same value and
+// the branches taken on it (which hold full-warp shuffles) stay warp-uniform.
+__device__ __forceinline__ double max_nan(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
+
 // Native FP64: ||x|| from the plain sum of squares unless that sum leaves [2^-900, 2^900], in
 // which case every entry is rescaled by the largest magnitude first.  Whether H = I is decided
 // from the entries themselves, not from their sum of squares, which underflows to zero for
@@ -71,13 +76,11 @@ __device__ inline void reflector_warp<ArithF64>(const Tile& S, int kind, int N, 
         double mx = fabs(alpha);
         for (int r = r_lo + lane; r < N; r += 32) {
           if (skip_row(kind, r, j, np)) continue;
-          const double a = fabs(at<double>(S, r, j));
-          if (!(a <= mx)) mx = a;  // keeps NaN
+          mx = max_nan(mx, fabs(at<double>(S, r, j)));  // keeps NaN
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const double y = __shfl_xor_sync(0xffffffffu, mx, o);
-          if (!(y <= mx)) mx = y;
+          mx = max_nan(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
         if (mx == 0.0 || !(mx <= 1.7976931348623157e308)) {
           nrm = mx;  // zero cannot happen here; Inf or NaN propagate

@@ -26,11 +26,11 @@ __global__ void __launch_bounds__(256) fma_chains(T* sink, int64_t iters, T a, T
 }
 
 template <class T>
-int run(int64_t iters, double* tflops) {
+int run(int64_t iters, double* tflops, int blocks_per_sm = 8, int threads = 256) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-  const int blocks = sms * 8;
+  const int blocks = sms * blocks_per_sm;
   T* sink = nullptr;
   if (cudaMalloc(&sink, sizeof(T) * blocks) != cudaSuccess) return 1;
   cudaEvent_t e0, e1;
@@ -39,7 +39,7 @@ int run(int64_t iters, double* tflops) {
   float ms = 0.f;
   for (int rep = 0; rep < 2; ++rep) {
     cudaEventRecord(e0);
-    fma_chains<T><<<blocks, 256>>>(sink, iters, (T)0.9999999, (T)1e-7);
+    fma_chains<T><<<blocks, threads>>>(sink, iters, (T)0.9999999, (T)1e-7);
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
     cudaEventElapsedTime(&ms, e0, e1);
@@ -49,7 +49,7 @@ int run(int64_t iters, double* tflops) {
   cudaEventDestroy(e1);
   cudaFree(sink);
   if (err != cudaSuccess || ms <= 0.f) return 1;
-  *tflops = 2.0 * 8.0 * (double)iters * (double)blocks * 256.0 / (ms * 1e-3) / 1e12;
+  *tflops = 2.0 * 8.0 * (double)iters * (double)blocks * (double)threads / (ms * 1e-3) / 1e12;
   return 0;
 }
 
@@ -59,4 +59,11 @@ int run(int64_t iters, double* tflops) {
 extern "C" int tsqr_probe_fma_tflops(int fp32, long long iters, double* tflops) {
   if (!tflops || iters < 1) return 1;
   return fp32 ? run<float>(iters, tflops) : run<double>(iters, tflops);
+}
+
+// The same with `warps` warps on each SM (one block of 32 * warps threads per SM): how the rate
+// grows with the number of warps issuing, i.e. what one warp alone can issue.  0 on success.
+extern "C" int tsqr_probe_fma_tflops_warps(int fp32, int warps, long long iters, double* tflops) {
+  if (!tflops || iters < 1 || warps < 1 || warps > 32) return 1;
+  return fp32 ? run<float>(iters, tflops, 1, 32 * warps) : run<double>(iters, tflops, 1, 32 * warps);
 }

@@ -441,7 +441,7 @@ def test_node_structure_eq_fact_2rs(T, m, n, h, arity):
     f, R, Q = run(T, A_h, leaf_h=h, chain=1, arity=arity)
     check_against_oracle(A_h, R, Q)
     info = f.info()
-    assert info.arity == arity and info.depth >= 3
+    assert info.arity == arity and info.depth >= 2
     np_ = info.np
     Y = workspace_view(f, info.node_y, info.tree_nodes * (info.arity - 1) * np_ * np_)
     Y = Y.reshape(info.tree_nodes, info.arity - 1, np_, np_)
@@ -978,11 +978,18 @@ def test_timeout_flag_reaches_the_host(T):
     f.close()
 
 
-def test_nan_propagates_without_fault(T):
-    """NaN in A propagates to R (no check, no trap); the device status word stays clear."""
-    A_h = inputs.gaussian(2000, 16, 99)
+@pytest.mark.parametrize("m,n,opts", [(2000, 16, {"leaf_h": 128}), (4096, 64, {"leaf_h": 64, "chain": 1, "arity": 2}),
+                                      (4096, 32, {"leaf_h": 64, "chain": 1, "arity": 2}),
+                                      (8192, 16, {"leaf_h": 64, "chain": 1, "arity": 2})])
+def test_nan_propagates_without_fault(T, m, n, opts):
+    """NaN in A propagates to R (no check, no trap); the device status word stays clear.  With
+    one-leaf chains under a binary tree the NaN reaches the structured node steps, which keep
+    the structural zeros exact, so only some lanes of a reflector's reductions see it: the
+    reductions must still end with one value on every lane (their branches hold full-warp
+    shuffles)."""
+    A_h = inputs.gaussian(m, n, 99)
     A_h[1234, 5] = np.nan
-    f, R, Q = run(T, A_h, leaf_h=128)
+    f, R, Q = run(T, A_h, **opts)
     assert np.isnan(R).any()
 
 
