@@ -115,29 +115,6 @@ __device__ __forceinline__ void load_groups(uint32_t taddr, uint32_t stride, lon
   }
 }
 
-// X * 2^k as FP64 with integer operations only (round to nearest even), so the conversion does
-// not occupy the FP64 pipe; X = 0 gives 0.  Falls back to scale_int outside the normal range.
-__device__ __forceinline__ double int_to_f64_scaled(long long X, int k) {
-  if (X == 0) return 0.0;
-  const unsigned long long sgn = (unsigned long long)X & 0x8000000000000000ull;
-  unsigned long long a = (X < 0) ? (unsigned long long)(-X) : (unsigned long long)X;
-  const int lz = __clzll((long long)a);  // a < 2^63, so lz >= 1
-  const int top = 63 - lz;                // a in [2^top, 2^(top+1))
-  const int E = top + k + 1023;           // biased exponent of the result
-  if (E < 1 || E > 2046) return oz::scale_int(X, k);
-  unsigned long long mant;
-  if (top <= 52) {
-    mant = a << (52 - top);
-  } else {
-    const int sh = top - 52;
-    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    mant = a >> sh;
-    if (rem > half || (rem == half && (mant & 1ull))) ++mant;  // may carry into 2^53
-  }
-  // mant in [2^52, 2^53]; adding the exponent field absorbs a carry to 2^53 correctly
-  const unsigned long long bits = sgn | (((unsigned long long)(E - 1) << 52) + mant);
-  return __longlong_as_double((long long)bits);
-}
 
 
 // T of the compact-WY form over columns [c0, c1), in place in the packed T_s, by blocked merges
@@ -370,7 +347,7 @@ __device__ __forceinline__ uint64_t bot_fixed(const Tile& S, int r, int c, int e
 // an Inf or NaN (exponent field 2047), which fixed point cannot carry.
 __device__ __forceinline__ double ozaki_value(long long X, int ea, int eb) {
   if (ea == 2047 || eb == 2047) return __longlong_as_double(0x7FF8000000000000LL);
-  return int_to_f64_scaled(X, ea + eb - 2100);
+  return oz::int_to_f64_scaled(X, ea + eb - 2100);
 }
 
 // Step 2: D = S_bot^T V_q (64 x 16, K = the 64 bottom rows) as one Ozaki product.  Rows c of D:

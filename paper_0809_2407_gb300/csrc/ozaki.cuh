@@ -150,6 +150,30 @@ __device__ __forceinline__ double scale_int(long long X, int k) {
   return scalbn(d, k);
 }
 
+// X * 2^k as FP64 with integer operations only (round to nearest even), so the conversion does
+// not occupy the FP64 pipe; X = 0 gives 0.  Falls back to scale_int outside the normal range.
+__device__ __forceinline__ double int_to_f64_scaled(long long X, int k) {
+  if (X == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)X & 0x8000000000000000ull;
+  unsigned long long a = (X < 0) ? (unsigned long long)(-X) : (unsigned long long)X;
+  const int lz = __clzll((long long)a);  // a < 2^63, so lz >= 1
+  const int top = 63 - lz;                // a in [2^top, 2^(top+1))
+  const int E = top + k + 1023;           // biased exponent of the result
+  if (E < 1 || E > 2046) return scale_int(X, k);
+  unsigned long long mant;
+  if (top <= 52) {
+    mant = a << (52 - top);
+  } else {
+    const int sh = top - 52;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    mant = a >> sh;
+    if (rem > half || (rem == half && (mant & 1ull))) ++mant;  // may carry into 2^53
+  }
+  // mant in [2^52, 2^53]; adding the exponent field absorbs a carry to 2^53 correctly
+  const unsigned long long bits = sgn | (((unsigned long long)(E - 1) << 52) + mant);
+  return __longlong_as_double((long long)bits);
+}
+
 // Bounded wait on an mbarrier phase (thread-level); false on timeout.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
   return mbar_wait_bounded(bar, parity, kWaitCycles);
