@@ -15,9 +15,13 @@
 //   * T is assembled after the leaf from the Gram entries g_pj = v_p^T v_j by the blocked
 //     Schreiber-Van Loan merge T = [T1, -T1 G12 T2; 0, T2], in parallel, instead of a
 //     column recurrence on the critical path of every reflector.
+// With kTc the Gram entries are not taken in the column loop at all but after it, as one
+// tensor-core product V^T V (gram_tc.cuh), so the loop's dot products cover only the columns
+// right of the pivot.
 #pragma once
 
 #include "householder.cuh"
+#include "gram_tc.cuh"
 
 namespace tsqr {
 
@@ -69,9 +73,13 @@ struct ChainScratch {
 // terms are products with exact zeros (in FP64 the results equal the dense step's bit for bit on
 // finite data), and the structural zeros stay exactly zero even when a reflector carries Inf or
 // NaN.  Every loop bound depends on j alone, never on data, and no barrier is skipped.
-template <class Ar, int NP, int H = ChainShape<NP>::H, bool kTri = false>
-__device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename Ar::E* T_s,
-                         const ChainScratch<Ar, NP>& w, bool want_t = true) {
+//
+// kTc: the Gram entries come from the tensor cores after the loop (tc; its stage is the T_s, red,
+// dvec and sc scratch, contiguous and free by then); R, the reflectors and tau are bitwise those
+// of the step without it.  False only if a wait on the tensor cores timed out.
+template <class Ar, int NP, int H = ChainShape<NP>::H, bool kTri = false, bool kTc = false>
+__device__ bool chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename Ar::E* T_s,
+                         const ChainScratch<Ar, NP>& w, bool want_t = true, const gram::GramTC* tc = nullptr) {
   using E = typename Ar::E;
   constexpr int NB = H / 8;            // row blocks of the bottom part
   constexpr int G = kThreads / NP;     // row groups of the dot products
@@ -83,6 +91,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
   const int rc = S.rows_cap;
   char* const bottom = S.base + (size_t)NP * 128;  // row NP starts block 0
   E* sc = w.sc;
+  const bool gram_loop = want_t && !kTc;  // Gram entries taken by the loop's dot products
 
   // bottom rows that can be nonzero in column c (all of them unless kTri)
   auto rows_of = [](int c) { return kTri ? (c + 1 < H ? c + 1 : H) : H; };
@@ -113,12 +122,12 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
     const E tau = sc[1];
     const bool active = !Ar::is_zero(sc[3]);
     if (tid == j) tau_s[j] = tau;
-    if (want_t && tid == j) T_s[tri_off(j, NP)] = tau;
+    if (gram_loop && tid == j) T_s[tri_off(j, NP)] = tau;
     if (active) {
       // ---- A: D_c = sum_r v_r a_rc over the bottom rows, every column c != j
       uint32_t oj[8];
       block_offsets(rc, j, oj);
-      if (cown < n && cown != j && (want_t || cown > j)) {
+      if (cown < n && cown != j && (gram_loop || cown > j)) {
         // four independent partial sums so consecutive multiply-adds do not wait on each other
         // on the FP32 pipe; FP64 keeps one: its pipe, not the latency, bounds the dots, and the
         // three adds that join four sums are FP64 instructions too
@@ -153,7 +162,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
           const E d = Ar::add(pr, D);
           pr = Ar::axpy(pr, tau, d);
           w.wvec[tid] = Ar::mul(tau, d);
-        } else if (want_t) {
+        } else if (gram_loop) {
           T_s[tri_off(tid, NP) + (j - tid)] = D;
         }
       }
@@ -200,7 +209,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
       __syncthreads();
     } else {
       // H_j = I: no update; Gram entries with column j are zero; build reflector j+1
-      if (want_t && tid < j) T_s[tri_off(tid, NP) + (j - tid)] = Ar::zero();
+      if (gram_loop && tid < j) T_s[tri_off(tid, NP) + (j - tid)] = Ar::zero();
       if (warp == 0 && j + 1 < n) {
         chain_reflector<Ar>(S, NP, H, j + 1, sc, w.invs);
         scale_column(j + 1);
@@ -209,6 +218,9 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
     }
   }
 
+  if constexpr (kTc) {
+    if (want_t && !gram::gram_ozaki<Ar, NP, H>(S, n, T_s, tau_s, w.X, *tc)) return false;
+  }
   // ---- T from the Gram entries by blocked merges (sizes b = 2^lb = 1, 2, 4, ... NP/2)
   for (int b = 1, lb = 0; want_t && b < n; b <<= 1, ++lb) {
     const int pairs = (n + 2 * b - 1) >> (lb + 1);
@@ -238,6 +250,7 @@ __device__ void chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
     }
     __syncthreads();
   }
+  return true;
 }
 
 }  // namespace tsqr

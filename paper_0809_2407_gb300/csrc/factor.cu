@@ -1,5 +1,7 @@
 // TSQR factorization kernels: leaves, flat chains and the tree over thread blocks, in one launch
-// (the schedule is in factor_chain.cuh), with the flat-tree step on the FP64 (or FP32) pipe.
+// (the schedule is in factor_chain.cuh), with the flat-tree step on the FP64 (or FP32) pipe.  In
+// the Ozaki forms (modes 2 and 3) the 64-column step takes the Gram entries of its T on the
+// tensor cores (gram_tc.cuh); everything else, and R bit for bit, is the plain step's.
 #include <algorithm>
 
 #include "factor_kernels.h"
@@ -9,19 +11,39 @@ namespace tsqr {
 
 size_t factor_smem_bytes(const Plan& P) {
   return 1024 + (size_t)P.rows_cap * P.np * 8 + (size_t)tri_size(P.np) * 8 + kThreads * 8 + P.np * 8 + 8 * 8 +
-         P.np * 8 + 2 * P.np * 8 + (size_t)P.np * P.np / 4 * 8 + 8 + 16;
+         P.np * 8 + 2 * P.np * 8 + (size_t)P.np * P.np / 4 * 8 + 16 + 16;
 }
 
-template <class Ar>
+// kTc: the chain steps take their Gram entries on the tensor cores; the block holds 256 TMEM
+// columns (two blocks per SM fit) for its lifetime.
+template <class Ar, bool kTc>
 __global__ void __launch_bounds__(kThreads, 2)
     factor_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, const Plan P,
                   const Store st, typename Ar::Out* __restrict__ R_out, int64_t ldr, int box_rows) {
   extern __shared__ char smem_raw[];
-  factor_chain<Ar>(&mapA, &mapV, P, st, R_out, ldr, box_rows, blockIdx.x, carve_factor<typename Ar::E>(smem_raw, P),
-                   [](const FactorSmem<typename Ar::E>& f, const Plan& p) {
-                     chain_step<Ar>(f, p);
-                     return true;
-                   });
+  using E = typename Ar::E;
+  const FactorSmem<E> f = carve_factor<E>(smem_raw, P);
+  if constexpr (!kTc) {
+    factor_chain<Ar>(&mapA, &mapV, P, st, R_out, ldr, box_rows, blockIdx.x, f,
+                     [](const FactorSmem<E>& ff, const Plan& p) { return chain_step<Ar>(ff, p); });
+  } else {
+    if (threadIdx.x < 32) oz::tmem_alloc(f.slot, gram::kTmemCols);
+    if (threadIdx.x == 0) {
+      mbar_init(f.mbar, 1);
+      fence_mbar_init();
+    }
+    oz::fence_before_sync();
+    __syncthreads();
+    oz::fence_after_sync();
+    const uint32_t tmem = *f.slot;
+    uint32_t phase = 0;
+    const gram::GramTC tc = gram_resources(f, &phase, tmem, st.status);
+    factor_chain<Ar>(&mapA, &mapV, P, st, R_out, ldr, box_rows, blockIdx.x, f,
+                     [&](const FactorSmem<E>& ff, const Plan& p) { return chain_step<Ar>(ff, p, &tc); });
+    oz::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) oz::tmem_dealloc(tmem, gram::kTmemCols);
+  }
 }
 
 // Many factorizations in one persistent launch: every block takes the next chain from the work
@@ -44,10 +66,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     const BatchItem& it = items[w.item];
     const FactorSmem<typename Ar::E> f = carve_factor<typename Ar::E>(smem_raw, it.plan);
     factor_chain<Ar>(&it.mapA, &it.mapV, it.plan, it.store, static_cast<typename Ar::Out*>(it.R), it.ldr,
-                     it.box_rows, w.chain, f, [](const FactorSmem<typename Ar::E>& ff, const Plan& p) {
-                       chain_step<Ar>(ff, p);
-                       return true;
-                     });
+                     it.box_rows, w.chain, f,
+                     [](const FactorSmem<typename Ar::E>& ff, const Plan& p) { return chain_step<Ar>(ff, p); });
     // a bounded wait that gave up may leave a copy in flight: take no further work
     __syncthreads();
     if (threadIdx.x == 0) k_s = *reinterpret_cast<volatile int*>(it.store.status) & kStatusTimeout;
@@ -118,17 +138,36 @@ cudaError_t launch_stage_widen_batched(const BatchItem* items, int count, cudaSt
   return cudaGetLastError();
 }
 
-template <class Ar>
+template <class Ar, bool kTc>
+static cudaError_t launch_factor_k(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
+                                   void* R_out, int64_t ldr, int box_rows, size_t smem, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(st.counters, 0, sizeof(int) * (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1), stream);
+  if (e != cudaSuccess) return e;
+  factor_kernel<Ar, kTc><<<P.chains, kThreads, smem, stream>>>(mapA, mapV, P, st,
+                                                               static_cast<typename Ar::Out*>(R_out), ldr, box_rows);
+  return cudaGetLastError();
+}
+
+// kTcForm: the precision form whose plans take the Gram entries on the tensor cores (where
+// gram_tc_applies and at most two blocks share an SM's 512 TMEM columns); -1 for none.
+template <class Ar, int kTcForm>
 static cudaError_t launch_factor_t(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                                    void* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
   const size_t smem = factor_smem_bytes(P);
-  cudaError_t e = cudaFuncSetAttribute(factor_kernel<Ar>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(factor_kernel<Ar, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(st.counters, 0, sizeof(int) * (size_t)(P.tree_nodes > 0 ? P.tree_nodes : 1), stream);
-  if (e != cudaSuccess) return e;
-  factor_kernel<Ar><<<P.chains, kThreads, smem, stream>>>(mapA, mapV, P, st, static_cast<typename Ar::Out*>(R_out),
-                                                          ldr, box_rows);
-  return cudaGetLastError();
+  if constexpr (kTcForm >= 0) {
+    if (P.precision == kTcForm && gram_tc_applies(P)) {
+      e = cudaFuncSetAttribute(factor_kernel<Ar, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_kernel<Ar, true>, kThreads, smem);
+      if (e != cudaSuccess) return e;
+      if (per_sm * (int)gram::kTmemCols <= 512)
+        return launch_factor_k<Ar, true>(mapA, mapV, P, st, R_out, ldr, box_rows, smem, stream);
+    }
+  }
+  return launch_factor_k<Ar, false>(mapA, mapV, P, st, R_out, ldr, box_rows, smem, stream);
 }
 
 // Copies A (m x n, leading dimension lda) into V (leading dimension ldv): the staging step for
@@ -205,9 +244,10 @@ cudaError_t launch_stage_transpose(const void* A, bool f32, int64_t lda, double*
 cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, const Plan& P, const Store& st,
                           void* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
   if (blocked_factor_applies(P)) return launch_factor_blocked(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
-  if (prec_df(P.precision)) return launch_factor_t<ArithDF>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
-  if (P.precision == kPrecF32) return launch_factor_t<ArithF32>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
-  return launch_factor_t<ArithF64>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
+  if (prec_df(P.precision))
+    return launch_factor_t<ArithDF, kPrecDFOzaki>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
+  if (P.precision == kPrecF32) return launch_factor_t<ArithF32, -1>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
+  return launch_factor_t<ArithF64, kPrecOzaki>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
 }
 
 }  // namespace tsqr

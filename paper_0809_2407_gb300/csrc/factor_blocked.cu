@@ -94,26 +94,6 @@ __device__ inline bool mma_wait(const Smem& z, uint32_t& phase, int* status, int
   return *flag == 0;
 }
 
-// The int64 recombination of the 8 weight groups of one accumulator column (ozaki.cuh): group
-// g (2..9) at TMEM column offset (g - 2) * stride.
-template <int kCols>
-__device__ __forceinline__ void load_groups(uint32_t taddr, uint32_t stride, long long acc[kCols]) {
-#pragma unroll
-  for (int c = 0; c < kCols; ++c) acc[c] = 0;
-#pragma unroll 1
-  for (int g = 2; g <= oz::kSlices + 1; ++g) {
-    uint32_t v[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                 : "r"(taddr + (uint32_t)(g - 2) * stride));
-    oz::tmem_wait_ld();
-#pragma unroll
-    for (int c = 0; c < kCols; ++c) {
-      const long long G = (long long)__float2int_rn(__uint_as_float(v[c]));
-      acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
-    }
-  }
-}
 
 
 
@@ -413,7 +393,7 @@ __device__ inline bool w_product(const Tile& S, const Smem& z, int q, double* T_
     const int c = 32 * (warp & 3) + lane;
     const int j0 = 8 * (warp >> 2);
     long long acc[8];
-    load_groups<8>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)j0, NB, acc);
+    oz::load_groups<8>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)j0, NB, acc);
     const int c1 = NB * (q + 1);
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
@@ -532,7 +512,7 @@ __device__ inline bool update_product(const Tile& S, const Smem& z, int q, uint3
       const int er = z.expU[r];
       for (int o = (warp >> 2) * (N / 2); o < (warp >> 2) * (N / 2) + N / 2; o += 8) {
         long long acc[8];
-        load_groups<8>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)o, 32, acc);
+        oz::load_groups<8>(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)o, 32, acc);
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) {
           const int c = c0 + o + jj;

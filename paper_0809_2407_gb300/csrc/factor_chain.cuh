@@ -24,8 +24,10 @@ template <class E>
 struct FactorSmem {
   Tile S;
   E *T_s, *red, *dvec, *sc, *tau_s, *wvec, *invs, *X;
-  uint64_t* bar;
+  uint64_t* bar;   // tile loads
+  uint64_t* mbar;  // tensor-core completion (the Gram entries on the tensor cores)
   int* flag;
+  uint32_t* slot;  // TMEM base address
 };
 
 template <class E>
@@ -42,18 +44,38 @@ __device__ inline FactorSmem<E> carve_factor(char* raw, const Plan& P) {
   f.invs = f.wvec + P.np;
   f.X = f.invs + P.np;
   f.bar = reinterpret_cast<uint64_t*>(f.X + P.np * P.np / 4);
-  f.flag = reinterpret_cast<int*>(f.bar + 1);
+  f.mbar = f.bar + 1;
+  f.flag = reinterpret_cast<int*>(f.bar + 2);
+  f.slot = reinterpret_cast<uint32_t*>(f.flag + 1);
   return f;
 }
 
+// Whether a plan's flat-tree steps can take their Gram entries on the tensor cores: the scheduled
+// step of 64 padded columns and 96-row leaves, with the Q factors kept.
+__host__ __device__ inline bool gram_tc_applies(const Plan& P) {
+  return P.np == 64 && P.h == ChainShape<64>::H && !P.r_only && P.rows_cap >= 64 + ChainShape<64>::H;
+}
+
+// The tensor-core Gram's resources inside a FactorSmem: the stage over T_s, red, dvec and sc
+// (contiguous in carve_factor and free after the column loop), the column exponents over wvec.
+template <class E>
+__device__ inline gram::GramTC gram_resources(const FactorSmem<E>& f, uint32_t* phase, uint32_t tmem, int* status) {
+  return gram::GramTC{reinterpret_cast<char*>(f.T_s), reinterpret_cast<int*>(f.wvec), f.mbar, phase, tmem, status,
+                      f.flag};
+}
+
 // The flat-tree step on the tile: the scheduled chain_qr for the default shapes, the generic
-// stacked_qr otherwise.
+// stacked_qr otherwise.  With tc (plans where gram_tc_applies) the 64-column step takes its Gram
+// entries on the tensor cores.  False only if a wait on the tensor cores timed out.
 template <class Ar>
-__device__ inline void chain_step(const FactorSmem<typename Ar::E>& f, const Plan& P) {
+__device__ inline bool chain_step(const FactorSmem<typename Ar::E>& f, const Plan& P,
+                                  const gram::GramTC* tc = nullptr) {
   const int np = P.np, n = P.n, h = P.h;
   const bool want_t = !P.r_only;
   if (np == 64 && h == ChainShape<64>::H) {
-    chain_qr<Ar, 64>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 64>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X}, want_t);
+    const ChainScratch<Ar, 64> w{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X};
+    if (tc != nullptr) return chain_qr<Ar, 64, ChainShape<64>::H, false, true>(f.S, n, f.tau_s, f.T_s, w, want_t, tc);
+    chain_qr<Ar, 64>(f.S, n, f.tau_s, f.T_s, w, want_t);
   } else if (np == 32 && h == ChainShape<32>::H) {
     chain_qr<Ar, 32>(f.S, n, f.tau_s, f.T_s, ChainScratch<Ar, 32>{f.red, f.dvec, f.wvec, f.invs, f.sc, f.X}, want_t);
   } else if (np == 16 && h == ChainShape<16>::H) {
@@ -61,6 +83,7 @@ __device__ inline void chain_step(const FactorSmem<typename Ar::E>& f, const Pla
   } else {
     stacked_qr<Ar>(f.S, CHAIN, np + h, np, n, f.tau_s, want_t ? f.T_s : nullptr, f.red, f.dvec, f.sc);
   }
+  return true;
 }
 
 // A binary tree node (q <= 2 children) by the scheduled chain step in its structured form

@@ -151,7 +151,9 @@ __device__ __forceinline__ double scale_int(long long X, int k) {
 }
 
 // X * 2^k as FP64 with integer operations only (round to nearest even), so the conversion does
-// not occupy the FP64 pipe; X = 0 gives 0.  Falls back to scale_int outside the normal range.
+// not occupy the FP64 pipe: for kernels bound by that pipe (the factorization's steps).  The
+// thin-Q and apply kernels, bound by the integer ALU, keep scale_int.  X = 0 gives 0.  Falls back
+// to scale_int outside the normal range.
 __device__ __forceinline__ double int_to_f64_scaled(long long X, int k) {
   if (X == 0) return 0.0;
   const unsigned long long sgn = (unsigned long long)X & 0x8000000000000000ull;
@@ -172,6 +174,27 @@ __device__ __forceinline__ double int_to_f64_scaled(long long X, int k) {
   // mant in [2^52, 2^53]; adding the exponent field absorbs a carry to 2^53 correctly
   const unsigned long long bits = sgn | (((unsigned long long)(E - 1) << 52) + mant);
   return __longlong_as_double((long long)bits);
+}
+
+// The int64 recombination X (this file's header) of the 8 weight groups of kCols accumulator
+// columns of this warp's 32 TMEM lanes: group g (2..9) at TMEM column offset (g - 2) * stride.
+template <int kCols>
+__device__ __forceinline__ void load_groups(uint32_t taddr, uint32_t stride, long long acc[kCols]) {
+#pragma unroll
+  for (int c = 0; c < kCols; ++c) acc[c] = 0;
+#pragma unroll 1
+  for (int g = 2; g <= oz::kSlices + 1; ++g) {
+    uint32_t v[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr + (uint32_t)(g - 2) * stride));
+    oz::tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) {
+      const long long G = (long long)__float2int_rn(__uint_as_float(v[c]));
+      acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
+    }
+  }
 }
 
 // Bounded wait on an mbarrier phase (thread-level); false on timeout.

@@ -211,7 +211,7 @@ __device__ inline void ozaki_epilogue(const OzSmem& z, uint32_t tmem, int rows, 
     if (i < rows) {
       const int ea = z.expA[i];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) out(i, c0 + c, oz::int_to_f64_scaled(acc[c], ea + z.expB[c0 + c] - 2100));
+      for (int c = 0; c < 16; ++c) out(i, c0 + c, oz::scale_int(acc[c], ea + z.expB[c0 + c] - 2100));
     }
   }
   oz::fence_before_sync();

@@ -453,6 +453,62 @@ def test_node_structure_eq_fact_2rs(T, m, n, h, arity):
     assert np.array_equal(np.diagonal(Tn, axis1=1, axis2=2), tau)
 
 
+def leaf_factors(f, info, precision):
+    """V (m x n), tau (leaves x np) and T (leaves x np x np) of a factorization as FP64, decoding
+    the double-float pairs of modes 1 and 3 (hi in the low word) into hi + lo."""
+    import torch
+
+    np_, leaves = info.np, info.leaves
+
+    def decode(ptr, count):
+        raw = workspace_view(f, ptr, count)
+        if precision in (1, 3):
+            pairs = raw.view(np.float32).reshape(-1, 2).astype(np.float64)
+            return pairs[:, 0] + pairs[:, 1]
+        return raw
+
+    torch.cuda.synchronize()
+    V = decode(info.v, info.m * info.ldv).reshape(info.m, info.ldv)[:, :info.n]
+    tau = decode(info.tau_leaf, leaves * np_).reshape(leaves, np_)
+    Tl = decode(info.t_leaf, leaves * np_ * np_).reshape(leaves, np_, np_)
+    return V, tau, Tl
+
+
+@pytest.mark.parametrize("n", [64, 50, 33])
+def test_gram_entries_on_tensor_cores(T, n):
+    """The Ozaki forms take the Gram entries v_p^T v_q of each flat-tree step's T on the tensor
+    cores.  For every step, T^-1 = diag(1/tau) + the strict upper part of V^T V (Sec. 3.2: the
+    compact-WY T of reflectors with tau = 2 / v^T v; the unit top parts are orthogonal, so V^T V
+    is the leaf rows' Gram), checked with numpy's FP64 Gram of the stored reflectors; in mode 2
+    R, V and tau are bitwise mode 0's and T agrees with mode 0's to the products' accuracy."""
+    import torch
+
+    h, chain, chains = 96, 4, 3
+    m = h * chain * chains
+    A_h = inputs.gaussian(m, n, inputs.seed_for(41, n))
+    A = torch.from_numpy(A_h).cuda()
+    got = {}
+    for prec in (0, 2, 3):
+        f = T.Factorization(A, precision=prec, leaf_h=h, chain=chain, arity=2)
+        info = f.info()
+        assert (info.np, info.leaf_h, info.chain, info.leaves) == (64, h, chain, chain * chains)
+        V, tau, Tl = leaf_factors(f, info, prec)
+        got[prec] = (f.R.cpu().numpy(), V, tau, Tl)
+        for leaf in range(info.leaves):
+            if leaf % chain == 0:
+                continue  # a chain's first leaf: plain Householder QR, T by its own recurrence
+            Vb = V[leaf * h:(leaf + 1) * h]
+            M = np.triu(Vb.T @ Vb, 1) + np.diag(1.0 / tau[leaf, :n])
+            Tn = Tl[leaf, :n, :n]
+            assert np.all(np.tril(Tl[leaf], -1) == 0.0) and np.all(Tl[leaf, n:] == 0.0)
+            assert np.abs(Tn @ M - np.eye(n)).max() <= (1e-12 if prec != 3 else 1e-9), (prec, leaf)
+        f.close()
+    R0, V0, tau0, T0 = got[0]
+    R2, V2, tau2, T2 = got[2]
+    assert np.array_equal(R2, R0) and np.array_equal(V2, V0) and np.array_equal(tau2, tau0)
+    assert np.abs(T2 - T0).max() <= 1e-13 * np.abs(T0).max()
+
+
 def workspace_view(f, ptr, count):
     """`count` doubles of the factorization's workspace starting at device pointer ptr."""
     import torch
