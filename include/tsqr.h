@@ -219,9 +219,9 @@ tsqr_status_t tsqr_batch_status_poll(tsqr_batch_t b, tsqr_stream_t stream);
 tsqr_status_t tsqr_batch_destroy(tsqr_batch_t b);
 
 /* R only, with no workspace and no allocation.  The paper has no counterpart: this entry point
- * exists for callers that cannot call cudaMalloc or hand the library a workspace, such as code
- * running while a stream is captured in global capture mode, code inside another runtime's
- * allocator or callbacks, or C hosts without a device allocator.
+ * exists for callers that cannot call cudaMalloc or hand the library a workspace: code inside
+ * another runtime's allocator or its callbacks (which must not re-enter an allocator), plugins
+ * whose host owns all device memory and gives them none, or C hosts without a device allocator.
  *   A  : device, m x n (m >= n >= 1), lda >= n and even, 16-byte aligned; read only.
  *   dR : device, n x n with ldr >= n; receives R with diag(R) >= 0, strict lower zeroed.
  * Same tree as tsqr_factor, except that the number of chains is capped so the scratch fits.

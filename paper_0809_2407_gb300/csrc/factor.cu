@@ -1,7 +1,10 @@
 // TSQR factorization kernels: leaves, flat chains and the tree over thread blocks, in one launch
 // (the schedule is in factor_chain.cuh), with the flat-tree step on the FP64 (or FP32) pipe.  In
-// the Ozaki forms (modes 2 and 3) the 64-column step takes the Gram entries of its T on the
-// tensor cores (gram_tc.cuh); everything else, and R bit for bit, is the plain step's.
+// the Ozaki WY form (mode 2) the 64-column step takes the Gram entries of its T on the tensor
+// cores (gram_tc.cuh); everything else, and R bit for bit, is the plain step's.  The double-float
+// step (modes 1 and 3) keeps them in its column loop: there the loop is bound by latency, not by
+// the FP32 pipe, so the extra dot products cost little and the serial tensor-core pass after the
+// loop cost more (factor at m = 2^22, n = 64: 39.6 ms with the loop's Gram, 46.7 ms without).
 #include <algorithm>
 
 #include "factor_kernels.h"
@@ -245,7 +248,7 @@ cudaError_t launch_factor(const CUtensorMap& mapA, const CUtensorMap& mapV, cons
                           void* R_out, int64_t ldr, int box_rows, cudaStream_t stream) {
   if (blocked_factor_applies(P)) return launch_factor_blocked(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
   if (prec_df(P.precision))
-    return launch_factor_t<ArithDF, kPrecDFOzaki>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
+    return launch_factor_t<ArithDF, -1>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
   if (P.precision == kPrecF32) return launch_factor_t<ArithF32, -1>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
   return launch_factor_t<ArithF64, kPrecOzaki>(mapA, mapV, P, st, R_out, ldr, box_rows, stream);
 }

@@ -1,9 +1,8 @@
 // tsqr_factor_r_noalloc: the R factor of TSQR for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc or hand over a workspace: code that runs while a stream
-// is being captured in global capture mode (where allocation calls are refused), code inside
-// another runtime's allocator or callbacks, or plain C hosts with no device allocator of their
-// own.  This entry point needs no workspace: the scratch the factorization uses between thread
+// Some callers cannot call cudaMalloc or hand over a workspace: code inside another runtime's
+// allocator or its callbacks (which must not re-enter an allocator), plugins whose host owns all
+// device memory and gives them none, or plain C hosts with no device allocator of their own.  This entry point needs no workspace: the scratch the factorization uses between thread
 // blocks (the chains' and tree nodes' R factors, the arrival counters and a status word) lives
 // in one file-scope __device__ array of kStaticScratchBytes, which every GPU that loads this
 // library holds until the process exits.  It computes only R (diag(R) >= 0); the implicit Q is

@@ -1,8 +1,9 @@
 // The Gram entries that the compact-WY T of a flat-tree step is built from, g_pq = v_p^T v_q
 // (p < q, over the leaf's rows; Sec. 3.2: T from the reflectors' inner products), taken on the
-// tensor cores as one Ozaki-split product V^T V, for the precision forms with FP64-level results
-// (Ozaki WY and double-float + Ozaki WY).  The reflectors themselves, tau, R and the merge that
-// turns the Gram entries into T stay on the FP64 (or double-float) path.
+// tensor cores as one Ozaki-split product V^T V, for the Ozaki WY form (FP64 storage, FP64-level
+// results).  The reflectors themselves, tau, R and the merge that turns the Gram entries into T
+// stay on the FP64 path.  The operand conversion also reads double-float pairs, but the
+// double-float forms keep the column loop's Gram entries (factor.cu says why).
 //
 // Reading: building T is native FP64 in the method's precision split, but its Gram entries are a
 // dense contraction of the reflectors, the same kind of product as the WY products, so they are

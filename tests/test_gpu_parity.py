@@ -476,8 +476,9 @@ def leaf_factors(f, info, precision):
 
 @pytest.mark.parametrize("n", [64, 50, 33])
 def test_gram_entries_on_tensor_cores(T, n):
-    """The Ozaki forms take the Gram entries v_p^T v_q of each flat-tree step's T on the tensor
-    cores.  For every step, T^-1 = diag(1/tau) + the strict upper part of V^T V (Sec. 3.2: the
+    """The Ozaki WY form (mode 2) takes the Gram entries v_p^T v_q of each flat-tree step's T on
+    the tensor cores; modes 0 and 3 take them in the column loop.  For every step, in every mode,
+    T^-1 = diag(1/tau) + the strict upper part of V^T V (Sec. 3.2: the
     compact-WY T of reflectors with tau = 2 / v^T v; the unit top parts are orthogonal, so V^T V
     is the leaf rows' Gram), checked with numpy's FP64 Gram of the stored reflectors; in mode 2
     R, V and tau are bitwise mode 0's and T agrees with mode 0's to the products' accuracy."""
