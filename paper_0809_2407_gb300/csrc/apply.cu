@@ -423,7 +423,11 @@ size_t formq_ozaki_smem_bytes(const Plan& P) {
 
 
 // Chain g of one factorization (the body of formq_ozaki_kernel and of its batched form).
-template <bool kPairs>
+// kDefer: the chain recurrence alone for the leaves that formq_leaf_deferred names: their
+// M = T C goes into the first n rows of the leaf's own rows of Q, and the product -V M that
+// replaces it is left to formq_ozaki_leaves_kernel; the reflector tile of those leaves is not
+// loaded here.
+template <bool kPairs, bool kDefer = false>
 __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, const Plan& P, const Store& st,
                                                   double* __restrict__ Q, int64_t ldq, int box_rows, int g,
                                                   char* smem_raw) {
@@ -450,23 +454,40 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
   }
   __syncthreads();
   const int64_t l0 = chain_first_leaf(P, g), l1 = chain_end_leaf(P, g);
+  // kDefer: a deferred leaf's T arrives in the Y buffer (which such a leaf does not use), issued
+  // while the previous leaf's products run; t_in_y says it is in flight
+  auto deferred_t = [&](int64_t leaf) { return kDefer && leaf > l0 && formq_leaf_deferred(P, leaf); };
+  bool t_in_y = false;
+  if (deferred_t(l1 - 1)) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(z.bars + 3, np * np * 8);
+      bulk_load(z.Y.base, st.t_leaf + (l1 - 1) * np * np, np * np * 8, z.bars + 3);
+    }
+    t_in_y = true;
+  }
   bool alive = true;
   for (int64_t leaf = l1 - 1; leaf >= l0 && alive; --leaf) {
     const int64_t row0 = leaf * h;
     const int rows_valid = (int)((P.m - row0 < h) ? (P.m - row0) : h);
     const double* Tg = st.t_leaf + leaf * np * np;
     if (leaf != l0) {
+      const bool defer = deferred_t(leaf);
+      const double* Ts = defer ? reinterpret_cast<const double*>(z.Y.base) : z.M;  // where T arrives
       // ---- both loads of the leaf start now: T into the M buffer, the reflector tile into Y
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
-        mbar_arrive_expect_tx(z.bars + 3, np * np * 8);
-        bulk_load(z.M, Tg, np * np * 8, z.bars + 3);
-        mbar_arrive_expect_tx(z.bars + 0, (uint32_t)h * np * 8);
-        for (int pnl = 0; pnl < np / 16; ++pnl)
-          for (int r = 0; r < h; r += box_rows)
-            tma_load_2d(z.Y.base + (size_t)pnl * h * 128 + (size_t)r * 128, mapV_p, z.bars + 0, pnl * 16,
-                        (int)(row0 + r));
+        if (!t_in_y) {
+          mbar_arrive_expect_tx(z.bars + 3, np * np * 8);
+          bulk_load(const_cast<double*>(Ts), Tg, np * np * 8, z.bars + 3);
+        }
+        if (!defer) {
+          mbar_arrive_expect_tx(z.bars + 0, (uint32_t)h * np * 8);
+          for (int pnl = 0; pnl < np / 16; ++pnl)
+            for (int r = 0; r < h; r += box_rows)
+              tma_load_2d(z.Y.base + (size_t)pnl * h * 128 + (size_t)r * 128, mapV_p, z.bars + 0, pnl * 16,
+                          (int)(row0 + r));
+        }
       }
       // ---- C (B operand): output column j, k-th entry C[k][j]
       ozaki_b_slices(z, [&](int j, int k) { return z.C[k * kOzLd + j]; });
@@ -483,11 +504,20 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
       long long* Tfix = reinterpret_cast<long long*>(z.M);
       for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
       __syncthreads();
-      for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], slot_bexp<kPairs>(z.M[idx]));
+      for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], slot_bexp<kPairs>(Ts[idx]));
       __syncthreads();
       for (int idx = tid; idx < np * np; idx += kOzT)
-        Tfix[idx] = (long long)slot_fixed<kPairs>(z.M[idx], z.expA[idx >> 6]);
+        Tfix[idx] = (long long)slot_fixed<kPairs>(Ts[idx], z.expA[idx >> 6]);
+      fence_proxy_async_smem();
       __syncthreads();
+      t_in_y = false;
+      if (defer && deferred_t(leaf - 1)) {  // the next leaf's T into the Y buffer, now read
+        if (tid == 0) {
+          mbar_arrive_expect_tx(z.bars + 3, np * np * 8);
+          bulk_load(z.Y.base, Tg - np * np, np * np * 8, z.bars + 3);
+        }
+        t_in_y = true;
+      }
       if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Tfix[r * 64 + k]; }, ph, st.status)) {
         alive = false;
         break;
@@ -497,6 +527,13 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
       for (int i = tid; i < np * np; i += kOzT) {
         const int o = (i / np) * kOzLd + i % np;
         z.C[o] -= z.M[o];
+      }
+      if (defer) {  // M (n x n) over the leaf's first n rows of Q, for the leaf products
+        for (int i = tid; i < n * n; i += kOzT) {
+          const int a = i / n, b = i % n;
+          Q[gidx(P, row0 + a, b, ldq)] = z.M[a * kOzLd + b];
+        }
+        continue;
       }
       // ---- M (B operand): output column j, k-th entry M[k][j]
       ozaki_b_slices(z, [&](int j, int k) { return z.M[k * kOzLd + j]; });
@@ -618,12 +655,12 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
   if (warp == 0) oz::tmem_dealloc(tmem, oz::kTmemCols);
 }
 
-template <bool kPairs>
+template <bool kPairs, bool kDefer>
 __global__ void __launch_bounds__(kOzT, 1)
     formq_ozaki_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
                        int64_t ldq, int box_rows) {
   extern __shared__ char smem_raw[];
-  formq_ozaki_chain<kPairs>(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
+  formq_ozaki_chain<kPairs, kDefer>(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
 }
 
 // Batched: block b takes chain work[b].chain of item work[b].item (items whose thin Q runs on the
@@ -1089,17 +1126,20 @@ static cudaError_t launch_form_q_ozaki(const CUtensorMap& mapV, const Plan& P, c
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  // the chain recurrence, leaving M = T C of the deferred leaves in Q; then their products
   const size_t smem = formq_ozaki_smem_bytes(P);
   if (pairs) {
-    e = cudaFuncSetAttribute(formq_ozaki_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(formq_ozaki_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    formq_ozaki_kernel<true><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+    formq_ozaki_kernel<true, true><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
   } else {
-    e = cudaFuncSetAttribute(formq_ozaki_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(formq_ozaki_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    formq_ozaki_kernel<false><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+    formq_ozaki_kernel<false, true><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
   }
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_formq_ozaki_leaves(P, st, Q, ldq, stream);
 }
 
 bool ozaki_form_q_applies(const Plan& P) {

@@ -11,6 +11,14 @@ size_t formq_smem_bytes(const Plan& P, bool allow_dbl = false);
 size_t apply_smem_bytes(const Plan& P, int kb);
 size_t formq_ozaki_smem_bytes(const Plan& P);
 bool ozaki_form_q_applies(const Plan& P);
+// Thin Q with Ozaki products: a leaf whose product -V M runs in formq_ozaki_leaves_kernel, apart
+// from its chain's recurrence (not the first leaf of its chain, and at least n rows).
+__host__ __device__ inline bool formq_leaf_deferred(const Plan& P, int64_t leaf) {
+  const bool first = (leaf % P.chain == 0) && (leaf / P.chain < P.chains);
+  return !first && P.m - leaf * P.h >= P.n;
+}
+// The products -V M of the deferred leaves (after the chain recurrence wrote their M into Q).
+cudaError_t launch_formq_ozaki_leaves(const Plan& P, const Store& st, double* Q, int64_t ldq, cudaStream_t stream);
 // Q^T B / Q B with the chains' WY products on the tensor cores (Ozaki splits in precision modes 2
 // and 3, bf16x3 terms in FP32 storage): np = 64, h <= 128, and at least this many columns of B
 // (narrower B stays on the FP64 / FP32 pipe)
