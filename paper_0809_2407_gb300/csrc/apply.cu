@@ -423,14 +423,12 @@ size_t formq_ozaki_smem_bytes(const Plan& P) {
 
 
 // Chain g of one factorization (the body of formq_ozaki_kernel and of its batched form).
-// kDefer: the chain recurrence alone for the leaves that formq_leaf_deferred names: their
-// M = T C goes into the first n rows of the leaf's own rows of Q, and the product -V M that
-// replaces it is left to formq_ozaki_leaves_kernel; the reflector tile of those leaves is not
-// loaded here.
-template <bool kPairs, bool kDefer = false>
+// first_only: only the chain's first leaf, with the block C entering it read from node_r[g] as
+// plain FP64 (written there by formq_ozaki_recur_kernel after the chain's other leaves).
+template <bool kPairs>
 __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, const Plan& P, const Store& st,
                                                   double* __restrict__ Q, int64_t ldq, int box_rows, int g,
-                                                  char* smem_raw) {
+                                                  char* smem_raw, bool first_only = false) {
   OzSmem z = carve_ozaki(smem_raw, P.h);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int np = 64, n = P.n, h = P.h;
@@ -446,48 +444,33 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
   const uint32_t tmem = *z.slot;
   uint32_t ph[2] = {0u, 0u};
   uint32_t y_phase = 0, t_phase = 0;
-  // C = this chain's block of Q_tree [D; 0]
+  // C = this chain's block of Q_tree [D; 0] (first_only: the block entering the first leaf)
   for (int i = tid; i < np * np; i += kOzT) {
     const int a = i / np, b = i % np;
-    z.C[a * kOzLd + b] = (P.depth == 0) ? ((a == b && a < n) ? __ldcg(st.signs + a) : 0.0)
-                                        : slot_val<kPairs>(__ldcg(st.node_r + (size_t)g * np * np + i));
+    const double* Cg = st.node_r + (size_t)g * np * np;
+    z.C[a * kOzLd + b] = first_only ? __ldcg(Cg + i)
+                         : (P.depth == 0) ? ((a == b && a < n) ? __ldcg(st.signs + a) : 0.0)
+                                          : slot_val<kPairs>(__ldcg(Cg + i));
   }
   __syncthreads();
-  const int64_t l0 = chain_first_leaf(P, g), l1 = chain_end_leaf(P, g);
-  // kDefer: a deferred leaf's T arrives in the Y buffer (which such a leaf does not use), issued
-  // while the previous leaf's products run; t_in_y says it is in flight
-  auto deferred_t = [&](int64_t leaf) { return kDefer && leaf > l0 && formq_leaf_deferred(P, leaf); };
-  bool t_in_y = false;
-  if (deferred_t(l1 - 1)) {
-    if (tid == 0) {
-      mbar_arrive_expect_tx(z.bars + 3, np * np * 8);
-      bulk_load(z.Y.base, st.t_leaf + (l1 - 1) * np * np, np * np * 8, z.bars + 3);
-    }
-    t_in_y = true;
-  }
+  const int64_t l0 = chain_first_leaf(P, g), l1 = first_only ? l0 + 1 : chain_end_leaf(P, g);
   bool alive = true;
   for (int64_t leaf = l1 - 1; leaf >= l0 && alive; --leaf) {
     const int64_t row0 = leaf * h;
     const int rows_valid = (int)((P.m - row0 < h) ? (P.m - row0) : h);
     const double* Tg = st.t_leaf + leaf * np * np;
     if (leaf != l0) {
-      const bool defer = deferred_t(leaf);
-      const double* Ts = defer ? reinterpret_cast<const double*>(z.Y.base) : z.M;  // where T arrives
       // ---- both loads of the leaf start now: T into the M buffer, the reflector tile into Y
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
-        if (!t_in_y) {
-          mbar_arrive_expect_tx(z.bars + 3, np * np * 8);
-          bulk_load(const_cast<double*>(Ts), Tg, np * np * 8, z.bars + 3);
-        }
-        if (!defer) {
-          mbar_arrive_expect_tx(z.bars + 0, (uint32_t)h * np * 8);
-          for (int pnl = 0; pnl < np / 16; ++pnl)
-            for (int r = 0; r < h; r += box_rows)
-              tma_load_2d(z.Y.base + (size_t)pnl * h * 128 + (size_t)r * 128, mapV_p, z.bars + 0, pnl * 16,
-                          (int)(row0 + r));
-        }
+        mbar_arrive_expect_tx(z.bars + 3, np * np * 8);
+        bulk_load(z.M, Tg, np * np * 8, z.bars + 3);
+        mbar_arrive_expect_tx(z.bars + 0, (uint32_t)h * np * 8);
+        for (int pnl = 0; pnl < np / 16; ++pnl)
+          for (int r = 0; r < h; r += box_rows)
+            tma_load_2d(z.Y.base + (size_t)pnl * h * 128 + (size_t)r * 128, mapV_p, z.bars + 0, pnl * 16,
+                        (int)(row0 + r));
       }
       // ---- C (B operand): output column j, k-th entry C[k][j]
       ozaki_b_slices(z, [&](int j, int k) { return z.C[k * kOzLd + j]; });
@@ -504,20 +487,11 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
       long long* Tfix = reinterpret_cast<long long*>(z.M);
       for (int r = tid; r < 128; r += kOzT) z.expA[r] = 0;
       __syncthreads();
-      for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], slot_bexp<kPairs>(Ts[idx]));
+      for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], slot_bexp<kPairs>(z.M[idx]));
       __syncthreads();
       for (int idx = tid; idx < np * np; idx += kOzT)
-        Tfix[idx] = (long long)slot_fixed<kPairs>(Ts[idx], z.expA[idx >> 6]);
-      fence_proxy_async_smem();
+        Tfix[idx] = (long long)slot_fixed<kPairs>(z.M[idx], z.expA[idx >> 6]);
       __syncthreads();
-      t_in_y = false;
-      if (defer && deferred_t(leaf - 1)) {  // the next leaf's T into the Y buffer, now read
-        if (tid == 0) {
-          mbar_arrive_expect_tx(z.bars + 3, np * np * 8);
-          bulk_load(z.Y.base, Tg - np * np, np * np * 8, z.bars + 3);
-        }
-        t_in_y = true;
-      }
       if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Tfix[r * 64 + k]; }, ph, st.status)) {
         alive = false;
         break;
@@ -527,13 +501,6 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
       for (int i = tid; i < np * np; i += kOzT) {
         const int o = (i / np) * kOzLd + i % np;
         z.C[o] -= z.M[o];
-      }
-      if (defer) {  // M (n x n) over the leaf's first n rows of Q, for the leaf products
-        for (int i = tid; i < n * n; i += kOzT) {
-          const int a = i / n, b = i % n;
-          Q[gidx(P, row0 + a, b, ldq)] = z.M[a * kOzLd + b];
-        }
-        continue;
       }
       // ---- M (B operand): output column j, k-th entry M[k][j]
       ozaki_b_slices(z, [&](int j, int k) { return z.M[k * kOzLd + j]; });
@@ -655,12 +622,16 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
   if (warp == 0) oz::tmem_dealloc(tmem, oz::kTmemCols);
 }
 
-template <bool kPairs, bool kDefer>
+// split: the chain's other leaves were taken by formq_ozaki_recur_kernel and the leaf products
+// kernel, so only its first leaf is left here (except a chain that holds a short last leaf,
+// which is taken whole, as without split).
+template <bool kPairs>
 __global__ void __launch_bounds__(kOzT, 1)
     formq_ozaki_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, double* __restrict__ Q,
-                       int64_t ldq, int box_rows) {
+                       int64_t ldq, int box_rows, bool split) {
   extern __shared__ char smem_raw[];
-  formq_ozaki_chain<kPairs, kDefer>(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
+  const int g = blockIdx.x;
+  formq_ozaki_chain<kPairs>(&mapV, P, st, Q, ldq, box_rows, g, smem_raw, split && !formq_chain_short(P, g));
 }
 
 // Batched: block b takes chain work[b].chain of item work[b].item (items whose thin Q runs on the
@@ -1126,16 +1097,19 @@ static cudaError_t launch_form_q_ozaki(const CUtensorMap& mapV, const Plan& P, c
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // the chain recurrence, leaving M = T C of the deferred leaves in Q; then their products
+  // the chains' recurrences (M = T C of every leaf but the first, into Q; the block entering the
+  // first leaf into node_r), then the first leaves, then the other leaves' products -V M
+  e = launch_formq_ozaki_recur(P, st, Q, ldq, stream);
+  if (e != cudaSuccess) return e;
   const size_t smem = formq_ozaki_smem_bytes(P);
   if (pairs) {
-    e = cudaFuncSetAttribute(formq_ozaki_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(formq_ozaki_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    formq_ozaki_kernel<true, true><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+    formq_ozaki_kernel<true><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows, true);
   } else {
-    e = cudaFuncSetAttribute(formq_ozaki_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(formq_ozaki_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    formq_ozaki_kernel<false, true><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
+    formq_ozaki_kernel<false><<<P.chains, kOzT, smem, stream>>>(mapV, P, st, Q, ldq, box_rows, true);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

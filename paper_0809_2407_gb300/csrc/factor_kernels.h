@@ -11,13 +11,22 @@ size_t formq_smem_bytes(const Plan& P, bool allow_dbl = false);
 size_t apply_smem_bytes(const Plan& P, int kb);
 size_t formq_ozaki_smem_bytes(const Plan& P);
 bool ozaki_form_q_applies(const Plan& P);
-// Thin Q with Ozaki products: a leaf whose product -V M runs in formq_ozaki_leaves_kernel, apart
-// from its chain's recurrence (not the first leaf of its chain, and at least n rows).
-__host__ __device__ inline bool formq_leaf_deferred(const Plan& P, int64_t leaf) {
-  const bool first = (leaf % P.chain == 0) && (leaf / P.chain < P.chains);
-  return !first && P.m - leaf * P.h >= P.n;
+// Thin Q with Ozaki products in three kernels (formq_ozaki_phases.cu): the chain recurrences,
+// the chains' first leaves, and the other leaves' products.  A chain that holds a short last leaf
+// (fewer than n rows, merged into the last chain) is taken whole by the first-leaf kernel.
+__host__ __device__ inline bool formq_chain_short(const Plan& P, int g) {
+  return g == P.chains - 1 && P.m - (P.leaves - 1) * P.h < P.n;
 }
-// The products -V M of the deferred leaves (after the chain recurrence wrote their M into Q).
+// A leaf whose product -V M runs in formq_ozaki_leaves_kernel: not the first of its chain, and
+// not in a chain taken whole.
+__host__ __device__ inline bool formq_leaf_deferred(const Plan& P, int64_t leaf) {
+  const int64_t g = leaf / P.chain < P.chains ? leaf / P.chain : P.chains - 1;
+  return leaf != chain_first_leaf(P, (int)g) && !formq_chain_short(P, (int)g);
+}
+// The recurrences: M = T C of every leaf but the first into that leaf's first n rows of Q, and
+// the block entering the first leaf into node_r[g] as plain FP64.
+cudaError_t launch_formq_ozaki_recur(const Plan& P, const Store& st, double* Q, int64_t ldq, cudaStream_t stream);
+// The products -V M of the deferred leaves, over the M that the recurrences left in Q.
 cudaError_t launch_formq_ozaki_leaves(const Plan& P, const Store& st, double* Q, int64_t ldq, cudaStream_t stream);
 // Q^T B / Q B with the chains' WY products on the tensor cores (Ozaki splits in precision modes 2
 // and 3, bf16x3 terms in FP32 storage): np = 64, h <= 128, and at least this many columns of B

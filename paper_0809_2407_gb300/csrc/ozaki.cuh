@@ -197,6 +197,33 @@ __device__ __forceinline__ void load_groups(uint32_t taddr, uint32_t stride, lon
   }
 }
 
+// load_groups with the loads of four groups in flight before each wait (32 registers for the
+// loaded values instead of 8): for epilogues whose loads would otherwise wait one by one.
+__device__ __forceinline__ void load_groups8_x4(uint32_t taddr, uint32_t stride, long long acc[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = 0;
+#pragma unroll
+  for (int g0 = 2; g0 <= oz::kSlices + 1; g0 += 4) {
+    uint32_t v[4][8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(v[u][0]), "=r"(v[u][1]), "=r"(v[u][2]), "=r"(v[u][3]), "=r"(v[u][4]), "=r"(v[u][5]),
+                     "=r"(v[u][6]), "=r"(v[u][7])
+                   : "r"(taddr + (uint32_t)(g0 + u - 2) * stride));
+    oz::tmem_wait_ld();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int g = g0 + u;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const long long G = (long long)__float2int_rn(__uint_as_float(v[u][c]));
+        acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
+      }
+    }
+  }
+}
+
 // Bounded wait on an mbarrier phase (thread-level); false on timeout.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
   return mbar_wait_bounded(bar, parity, kWaitCycles);
