@@ -364,7 +364,6 @@ __device__ inline bool w_product(const Tile& S, const Smem& z, int q, double* T_
     fx[u][0] = bot_fixed(S, r, c, e);
     fx[u][1] = bot_fixed(S, r + 1, c, e);
   }
-  const uint32_t idesc = oz::idesc_bf16(128, NB);
   for (int s = 1; s <= oz::kSlices; ++s) {
     if (s > 1 && !mma_wait(z, phase, status, flag)) return false;
 #pragma unroll
@@ -376,13 +375,15 @@ __device__ inline bool w_product(const Tile& S, const Smem& z, int q, double* T_
     __syncthreads();
     if (tid == 0) {
       oz::fence_after_sync();
+      // the B slices t = 1 .. 9 - s lie one after another, as do their groups s + t - 2 in TMEM:
+      // one MMA of N = 16 (9 - s) per K step
       const uint64_t adesc = oz::sw128_desc(smem_u32(abuf));
-      for (int t = 1; t <= oz::kSlices + 1 - s; ++t) {
-        const uint32_t d = tmem + (uint32_t)(s + t - 2) * NB;
-        const uint64_t bdesc = oz::sw128_desc(smem_u32(bsl + (t - 1) * 2048));
+      const uint32_t d = tmem + (uint32_t)(s - 1) * NB;
+      const uint64_t bdesc = oz::sw128_desc(smem_u32(bsl));
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (s > 1 || kk > 0) ? 1u : 0u);
-      }
+      for (int kk = 0; kk < 4; ++kk)
+        oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, oz::idesc_bf16(128, (uint32_t)(NB * (oz::kSlices + 1 - s))),
+                     (s > 1 || kk > 0) ? 1u : 0u);
       oz::mma_commit(z.mma_bar);
     }
   }

@@ -80,7 +80,6 @@ template <bool kLanesOnRows = false, class AFix>
 __device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows, AFix afix, uint32_t ph[2],
                                       int* status, bool accumulate = false) {
   const int tid = threadIdx.x;
-  const uint32_t idesc = oz::idesc_bf16(oz::kM, oz::kN);
   for (int s = 1; s <= oz::kSlices; ++s) {
     const int b = (s - 1) & 1;
     if (s >= 3) {
@@ -98,14 +97,18 @@ __device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows
     __syncthreads();
     if (tid == 0) {
       oz::fence_after_sync();
+      // the B slices t = 1 .. 9 - s lie one after another, as do their groups s + t - 2 in TMEM:
+      // one MMA takes up to four of them (N up to 256)
       const uint64_t adesc = oz::sw128_desc(smem_u32(abuf));
-      for (int t = 1; t <= oz::kSlices + 1 - s; ++t) {
-        const uint32_t d = tmem + (uint32_t)(s + t - 2) * 64u;
-        const uint64_t bdesc = oz::sw128_desc(smem_u32(z.bsl + (t - 1) * oz::kBSliceBytes));
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)  // K step of 16 bf16 = 32 bytes = 2 descriptor units
-          oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, idesc, (accumulate || s > 1 || kk > 0) ? 1u : 0u);
-      }
+      for (int kk = 0; kk < 4; ++kk)  // K step of 16 bf16 = 32 bytes = 2 descriptor units
+        for (int t0 = 1; t0 <= oz::kSlices + 1 - s; t0 += 4) {
+          const int nt = min(4, oz::kSlices + 2 - s - t0);
+          const uint32_t d = tmem + (uint32_t)(s + t0 - 2) * 64u;
+          const uint64_t bdesc = oz::sw128_desc(smem_u32(z.bsl + (t0 - 1) * oz::kBSliceBytes));
+          oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, oz::idesc_bf16(oz::kM, 64u * nt),
+                       (accumulate || s > 1 || kk > 0) ? 1u : 0u);
+        }
       oz::mma_commit(z.bars + 1 + b);
     }
   }
@@ -190,28 +193,18 @@ __device__ inline void ozaki_epilogue(const OzSmem& z, uint32_t tmem, int rows, 
   const int c0 = 16 * (warp >> 2);
   if (32 * sp < rows) {
     const uint32_t tb = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)c0;
-    long long acc[16];
+    const int ea = z.expA[i];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = 0;
-#pragma unroll 1
-    for (int g = 2; g <= oz::kSlices + 1; ++g) {
-      uint32_t v[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-            "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(tb + (uint32_t)(g - 2) * 64u));
-      oz::tmem_wait_ld();
+    for (int hf = 0; hf < 2; ++hf) {  // 8 columns at a time, four groups' loads per wait
+      long long acc[8];
+      oz::load_groups8_x4(tb + 8u * (uint32_t)hf, 64u, acc);
+      if (i < rows) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const long long G = (long long)__float2int_rn(__uint_as_float(v[c]));
-        acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
+        for (int c = 0; c < 8; ++c) {
+          const int j = c0 + 8 * hf + c;
+          out(i, j, oz::scale_int(acc[c], ea + z.expB[j] - 2100));
+        }
       }
-    }
-    if (i < rows) {
-      const int ea = z.expA[i];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) out(i, c0 + c, oz::scale_int(acc[c], ea + z.expB[c0 + c] - 2100));
     }
   }
   oz::fence_before_sync();
