@@ -36,18 +36,19 @@ namespace {
 // of columns j0 .. j0 + 7, j0 = 32 ((warp >> 1) & 1) + 8 (warp >> 2), and keeps C's entries there
 // in registers.  While the tensor cores work, every warp splits the next leaf's T (4 rows each)
 // into the other slice buffer, so a leaf costs one commit and T's splitting is off its path.
-constexpr uint32_t kTSliceBytes = 64 * 128;         // 64 operand rows of 128 bytes
-constexpr uint32_t kTBufBytes = 8 * kTSliceBytes;   // one leaf's 8 slices of T
-// C's slices as two halves of 32 output columns, the 8 slices of a half one after another
+constexpr uint32_t kTSliceBytes = 64 * 128;               // 64 operand rows of 128 bytes
+constexpr uint32_t kTBufBytes = oz::kDigits * kTSliceBytes;  // one leaf's 7 digit slices of T
+// C's slices as two halves of 32 output columns, the 8 slices of a half (the last one zero)
+// one after another
 constexpr uint32_t kCSliceBytes = 32 * 128;
-constexpr uint32_t kCHalfBytes = 8 * kCSliceBytes;
+constexpr uint32_t kCHalfBytes = oz::kDigitBSlices * kCSliceBytes;
 
 size_t recur_smem_bytes() {
   // 64 rows read before the first buffer, two T buffers, 64 rows read past the second, C's
   // slices, T row exponents (2 x 64), C column maxima of the two lane halves (2 x 64), barrier,
   // slot, flag
-  return 1024 + kTSliceBytes + 2 * (size_t)kTBufBytes + kTSliceBytes + 8 * (size_t)oz::kBSliceBytes + 4 * 64 * 4 +
-         8 + 8 + 8;
+  return 1024 + kTSliceBytes + 2 * (size_t)kTBufBytes + kTSliceBytes + 2 * (size_t)kCHalfBytes + 4 * 64 * 4 + 8 +
+         8 + 8;
 }
 
 template <bool kPairs>
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(kOzT, 1)
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   char* tbuf = base + kTSliceBytes;                       // 2 x kTBufBytes, 64 rows before and after
   char* bsl = tbuf + 2 * kTBufBytes + kTSliceBytes;       // C's 8 slices
-  int* expT = reinterpret_cast<int*>(bsl + 8 * oz::kBSliceBytes);  // [2][64]
+  int* expT = reinterpret_cast<int*>(bsl + 2 * kCHalfBytes);  // [2][64]
   int* expC2 = expT + 2 * 64;                                       // [2][64]
   uint64_t* bar = reinterpret_cast<uint64_t*>(expC2 + 2 * 64);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
@@ -75,6 +76,10 @@ __global__ void __launch_bounds__(kOzT, 1)
     fence_mbar_init();
     *flag = 0;
   }
+  for (int i2 = tid; i2 < 2 * (int)kCSliceBytes / 16; i2 += kOzT)  // the zero eighth slice of each half
+    *reinterpret_cast<uint4*>(bsl + (i2 / (kCSliceBytes / 16)) * kCHalfBytes + (oz::kDigitBSlices - 1) * kCSliceBytes +
+                              (i2 % (kCSliceBytes / 16)) * 16) = make_uint4(0, 0, 0, 0);
+  fence_proxy_async_smem();
   if (warp == 0) oz::tmem_alloc(slot, oz::kTmemCols);
   oz::fence_before_sync();
   __syncthreads();
@@ -96,11 +101,11 @@ __global__ void __launch_bounds__(kOzT, 1)
       const int r = warp + 16 * u;
       const int e = __reduce_max_sync(0xffffffffu, max(slot_bexp<kPairs>(traw[u].x), slot_bexp<kPairs>(traw[u].y)));
       if (lane == 0) expT[bb * 64 + r] = e;
-      const uint64_t f0 = slot_fixed<kPairs>(traw[u].x, e), f1 = slot_fixed<kPairs>(traw[u].y, e);
+      const uint64_t f0 = slot_biased54<kPairs>(traw[u].x, e), f1 = slot_biased54<kPairs>(traw[u].y, e);
       char* dst = tbuf + bb * kTBufBytes + oz::op_off(r, 2 * lane);
 #pragma unroll
-      for (int s = 1; s <= oz::kSlices; ++s)
-        *reinterpret_cast<uint32_t*>(dst + (s - 1) * kTSliceBytes) = slice_pair(f0, f1, s);
+      for (int s = 1; s <= oz::kDigits; ++s)
+        *reinterpret_cast<uint32_t*>(dst + (s - 1) * kTSliceBytes) = oz::digit_pair(f0, f1, s);
     }
   };
   // C's column exponent: the two lane halves of a column meet in shared memory
@@ -141,12 +146,12 @@ __global__ void __launch_bounds__(kOzT, 1)
         for (int q = 0; q < 4; ++q) {
           const int cq = odd ? 4 + q : q;
           const int ec = col_exp(cq);
-          const uint64_t f0 = oz::to_fixed(odd ? recv[q] : c[q], ec);
-          const uint64_t f1 = oz::to_fixed(odd ? c[4 + q] : recv[q], ec);
+          const uint64_t f0 = oz::to_biased54(odd ? recv[q] : c[q], ec);
+          const uint64_t f1 = oz::to_biased54(odd ? c[4 + q] : recv[q], ec);
           char* dst = bsl + half * kCHalfBytes + oz::op_off(j0 - 32 * half + cq, k0);
 #pragma unroll
-          for (int s = 1; s <= oz::kSlices; ++s)
-            *reinterpret_cast<uint32_t*>(dst + (s - 1) * kCSliceBytes) = slice_pair(f0, f1, s);
+          for (int s = 1; s <= oz::kDigits; ++s)
+            *reinterpret_cast<uint32_t*>(dst + (s - 1) * kCSliceBytes) = oz::digit_pair(f0, f1, s);
         }
       }
       fence_proxy_async_smem();
@@ -154,16 +159,16 @@ __global__ void __launch_bounds__(kOzT, 1)
       // ---- M = T C: two 32-column products of 36 slice pairs each, one commit
       if (tid == 0) {
         oz::fence_after_sync();
-        // A slice s meets C's slices t = 1 .. 9 - s of a half, which lie one after another in
-        // shared memory, as do their groups s + t - 2 in TMEM: one MMA (N = 32 (9 - s)) each
+        // digit slice s of T meets C's digit slices t = 1 .. digit_t_max(s) of a half, which lie
+        // one after another in shared memory, as do their groups s + t - 2 in TMEM: one MMA each
         for (int kk = 0; kk < 4; ++kk)  // K step of 16 bf16 = 32 bytes = 2 descriptor units
           for (int hh = 0; hh < 2; ++hh)
-            for (int s = 1; s <= oz::kSlices; ++s) {
+            for (int s = 1; s <= oz::kDigits; ++s) {
               const uint64_t adesc = oz::sw128_desc(
                   smem_u32(tbuf + b * kTBufBytes + (s - 1) * kTSliceBytes - (uint32_t)hh * kTSliceBytes));
               const uint32_t d = tmem + 256u * (uint32_t)hh + (uint32_t)(s - 1) * 32u;
               const uint64_t bdesc = oz::sw128_desc(smem_u32(bsl + (uint32_t)hh * kCHalfBytes));
-              oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, oz::idesc_bf16(oz::kM, 32u * (9 - s)),
+              oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, oz::idesc_bf16(oz::kM, 32u * oz::digit_t_max(s)),
                            (s > 1 || kk > 0) ? 1u : 0u);
             }
         oz::mma_commit(bar);
@@ -188,12 +193,13 @@ __global__ void __launch_bounds__(kOzT, 1)
       // ---- M back from TMEM (row i, columns j0..j0+7), C -= M, M into Q
       {
         long long acc[8];
-        oz::load_groups8_x4(tmem + ((uint32_t)(32 * q4) << 16) + 256u * (uint32_t)half + (uint32_t)(j0 - 32 * half), 32u, acc);
+        oz::load_digit_groups8(tmem + ((uint32_t)(32 * q4) << 16) + 256u * (uint32_t)half + (uint32_t)(j0 - 32 * half),
+                               32u, acc);
         const int ea = expT[b * 64 + i];
         double* dst = Q + gidx(P, row0 + i, 0, ldq);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const double mq = oz::scale_int(acc[q], ea + col_exp(q) - 2100);
+          const double mq = oz::int_to_f64_scaled(acc[q], ea + col_exp(q) - 2096);
           c[q] -= mq;
           if (i < n && j0 + q < n) dst[P.col_major ? (int64_t)(j0 + q) * ldq : j0 + q] = mq;
         }
@@ -226,7 +232,8 @@ constexpr int kRowsPerWarp = oz::kM / kWarps;  // 8: the 128 operand rows over t
 constexpr int kMPerThread = 64 * 32 / kOzT;    // 4 pairs (k, k + 1) of M entries per thread
 
 size_t leaves_smem_bytes() {
-  return 1024 + 8 * (size_t)oz::kASliceBytes + 8 * (size_t)oz::kBSliceBytes + 128 * 4 + 64 * 4 + 8 + 8 + 8;
+  return 1024 + oz::kDigits * (size_t)oz::kASliceBytes + oz::kDigitBSlices * (size_t)oz::kBSliceBytes + 128 * 4 +
+         64 * 4 + 8 + 8 + 8;
 }
 
 __device__ __forceinline__ int64_t next_deferred(const Plan& P, int64_t leaf) {
@@ -240,8 +247,8 @@ __global__ void __launch_bounds__(kOzT, 1)
   extern __shared__ char smem_raw[];
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   char* asl = base;
-  char* bsl = asl + 8 * oz::kASliceBytes;
-  int* expA = reinterpret_cast<int*>(bsl + 8 * oz::kBSliceBytes);
+  char* bsl = asl + oz::kDigits * oz::kASliceBytes;
+  int* expA = reinterpret_cast<int*>(bsl + oz::kDigitBSlices * oz::kBSliceBytes);
   int* expB = expA + 128;
   uint64_t* bar = reinterpret_cast<uint64_t*>(expB + 64);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
@@ -256,15 +263,15 @@ __global__ void __launch_bounds__(kOzT, 1)
     fence_mbar_init();
     *flag = 0;
   }
+  for (int i2 = tid; i2 < (int)oz::kBSliceBytes / 16; i2 += kOzT)  // the zero eighth B slice
+    *reinterpret_cast<uint4*>(bsl + (oz::kDigitBSlices - 1) * oz::kBSliceBytes + i2 * 16) = make_uint4(0, 0, 0, 0);
+  fence_proxy_async_smem();
   if (warp == 0) oz::tmem_alloc(slot, oz::kTmemCols);
   oz::fence_before_sync();
   __syncthreads();
   oz::fence_after_sync();
   const uint32_t tmem = *slot;
   uint32_t phase = 0;
-  OzSmem z{};  // the epilogue reads the exponents only
-  z.expA = expA;
-  z.expB = expB;
 
   // one leaf's operands in registers: rows warp + kWarps u of V (columns 2 lane, 2 lane + 1), and
   // M entries (k, j), (k + 1, j) with j = tid % 64, k = 2 (tid / 64 + 8 u)
@@ -305,11 +312,11 @@ __global__ void __launch_bounds__(kOzT, 1)
       const int r = warp + kWarps * u;
       const int e = __reduce_max_sync(0xffffffffu, max(slot_bexp<kPairs>(vr[u].x), slot_bexp<kPairs>(vr[u].y)));
       if (lane == 0) expA[r] = e;
-      const uint64_t f0 = slot_fixed<kPairs>(vr[u].x, e), f1 = slot_fixed<kPairs>(vr[u].y, e);
+      const uint64_t f0 = slot_biased54<kPairs>(vr[u].x, e), f1 = slot_biased54<kPairs>(vr[u].y, e);
       const uint32_t off = oz::op_off(r, 2 * lane);
 #pragma unroll
-      for (int s = 1; s <= oz::kSlices; ++s)
-        *reinterpret_cast<uint32_t*>(asl + (s - 1) * oz::kASliceBytes + off) = slice_pair(f0, f1, s);
+      for (int s = 1; s <= oz::kDigits; ++s)
+        *reinterpret_cast<uint32_t*>(asl + (s - 1) * oz::kASliceBytes + off) = oz::digit_pair(f0, f1, s);
     }
     __syncthreads();
     // ---- B: M's column exponents, then its slices (output column j, K = M's rows)
@@ -325,11 +332,11 @@ __global__ void __launch_bounds__(kOzT, 1)
 #pragma unroll
       for (int u = 0; u < kMPerThread; ++u) {
         const int k = 2 * ((tid >> 6) + 8 * u);
-        const uint64_t f0 = oz::to_fixed(mr[u].x, e), f1 = oz::to_fixed(mr[u].y, e);
+        const uint64_t f0 = oz::to_biased54(mr[u].x, e), f1 = oz::to_biased54(mr[u].y, e);
         const uint32_t off = oz::op_off(j_own, k);
 #pragma unroll
-        for (int s = 1; s <= oz::kSlices; ++s)
-          *reinterpret_cast<uint32_t*>(bsl + (s - 1) * oz::kBSliceBytes + off) = slice_pair(f0, f1, s);
+        for (int s = 1; s <= oz::kDigits; ++s)
+          *reinterpret_cast<uint32_t*>(bsl + (s - 1) * oz::kBSliceBytes + off) = oz::digit_pair(f0, f1, s);
       }
     }
     fence_proxy_async_smem();
@@ -337,14 +344,14 @@ __global__ void __launch_bounds__(kOzT, 1)
     // ---- the 36 slice products, one commit
     if (tid == 0) {
       oz::fence_after_sync();
-      // A slice s meets B slices t = 1 .. 9 - s, which lie one after another in shared memory and
-      // whose groups s + t - 2 lie one after another in TMEM: one MMA takes up to four of them
-      // (N up to 256), so a product is 12 MMAs per K step instead of 36
+      // digit slice s of A meets B's slices t = 1 .. digit_t_max(s), which lie one after another
+      // in shared memory and whose groups s + t - 2 lie one after another in TMEM: one MMA takes up
+      // to four of them (N up to 256), so a product is 11 MMAs per K step instead of 34
       for (int kk = 0; kk < 4; ++kk)  // K step of 16 bf16 = 32 bytes = 2 descriptor units
-        for (int s = 1; s <= oz::kSlices; ++s) {
+        for (int s = 1; s <= oz::kDigits; ++s) {
           const uint64_t adesc = oz::sw128_desc(smem_u32(asl + (s - 1) * oz::kASliceBytes));
-          for (int t0 = 1; t0 <= oz::kSlices + 1 - s; t0 += 4) {
-            const int nt = min(4, oz::kSlices + 2 - s - t0);
+          for (int t0 = 1; t0 <= oz::digit_t_max(s); t0 += 4) {
+            const int nt = min(4, oz::digit_t_max(s) + 1 - t0);
             const uint32_t d = tmem + (uint32_t)(s + t0 - 2) * 64u;
             const uint64_t bdesc = oz::sw128_desc(smem_u32(bsl + (t0 - 1) * oz::kBSliceBytes));
             oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, oz::idesc_bf16(oz::kM, 64u * nt),
@@ -369,9 +376,47 @@ __global__ void __launch_bounds__(kOzT, 1)
       break;
     }
     // ---- -V M over the leaf's rows (M was read into registers before this leaf started)
-    ozaki_epilogue(z, tmem, rv, [&](int i, int j, double v) {
-      if (j < n) Q[gidx(P, row0 + i, j, ldq)] = -v;
-    });
+    {
+      // warp w reads TMEM lanes 32 (w & 3).. (rows) and columns 16 (w >> 2).., 8 at a time, into
+      // a 128 x 64 FP64 tile over the A slices (dead until the next leaf), in 16-byte units whose
+      // index within a row is XORed with (row & 7); then every warp writes whole rows to Q
+      double* tile = reinterpret_cast<double*>(asl);
+      const int sp = warp & 3, i = 32 * sp + lane, c0 = 16 * (warp >> 2);
+      if (32 * sp < rv) {
+        const uint32_t tb = tmem + ((uint32_t)(32 * sp) << 16) + (uint32_t)c0;
+        const int ea = expA[i];
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          long long X[8];
+          oz::load_digit_groups8(tb + 8u * (uint32_t)hf, 64u, X);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = c0 + 8 * hf + 2 * u;
+            const int unit = (j >> 1) ^ (i & 7);
+            *reinterpret_cast<double2*>(tile + i * 64 + 2 * unit) =
+                make_double2(-oz::int_to_f64_scaled(X[2 * u], ea + expB[j] - 2096),
+                             -oz::int_to_f64_scaled(X[2 * u + 1], ea + expB[j + 1] - 2096));
+          }
+        }
+      }
+      oz::fence_before_sync();
+      __syncthreads();
+      oz::fence_after_sync();
+      const int j = 2 * lane;
+      for (int r = warp; r < rv; r += kWarps) {
+        const double2 v = *reinterpret_cast<const double2*>(tile + r * 64 + 2 * (lane ^ (r & 7)));
+        if (j < n) {
+          double* q = Q + gidx(P, row0 + r, j, ldq);
+          if (!P.col_major && j + 1 < n && (reinterpret_cast<uintptr_t>(q) & 15) == 0) {
+            *reinterpret_cast<double2*>(q) = v;
+          } else {
+            q[0] = v.x;
+            if (j + 1 < n) Q[gidx(P, row0 + r, j + 1, ldq)] = v.y;
+          }
+        }
+      }
+      __syncthreads();  // the tile is read before the next leaf's A slices go over it
+    }
     leaf = next;
   }
   // a block that gave up: one more bounded wait for the MMAs in flight before TMEM is freed

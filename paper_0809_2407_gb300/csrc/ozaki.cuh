@@ -224,6 +224,89 @@ __device__ __forceinline__ void load_groups8_x4(uint32_t taddr, uint32_t stride,
   }
 }
 
+// ---- balanced base-256 digits ------------------------------------------------------------------
+// A second form of the split, for the thin Q's recurrence and leaf-product kernels.  The value is
+// written in 54-bit fixed point against its row/column's largest biased exponent emax,
+// m = v 2^(1076 - emax) rounded to nearest (|m| < 2^54), and m + 0x0080808080808080 (0x80 in each
+// of bytes 0..6, which keeps the sum in [0, 2^56)) is read byte by byte: byte j minus 128 is the
+// digit of weight 2^(8 j), in [-128, 127], so m = sum_j d_j 2^(8 j) exactly.  Digit s = 1..7 is
+// byte 7 - s (most significant first).  A digit is exact in bf16 (at most 8 significant bits), a
+// product of two is at most 2^14 in magnitude, and the pairs of one weight g = s + t <= 9 (at most
+// 8 of them) summed over K = 64 stay below 2^23: exact FP32 TMEM groups.  The 34 pairs with
+// s + t <= 9 leave an error of about 2^-51 relative to |A| |B| (the 7-bit form's 36 pairs: 2^-49);
+// the digits need no sign handling, and one byte permute and one FP32 add make each of them.
+constexpr int kDigits = 7;
+constexpr int kDigitGroups = 8;  // weights g = 2 .. 9
+constexpr unsigned long long kDigitBias = 0x0080808080808080ull;
+
+// The B operand carries an eighth digit slice of zeros, so that the first A slice meets
+// t = 1 .. 8 and its MMAs (which start every accumulation) write all 8 groups; A slice s meets
+// B slices t = 1 .. digit_t_max(s) = 9 - s.
+constexpr int kDigitBSlices = 8;
+__host__ __device__ constexpr int digit_t_max(int s) { return 9 - s; }
+
+// Biased 54-bit fixed point of an FP64 value against emax (biased exponent, >= the value's).
+__device__ __forceinline__ uint64_t to_biased54(double v, int emax) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return kDigitBias;
+  const uint64_t mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // |v| = mant 2^(E - 1075)
+  const int d = E + 1 - emax;                                      // <= 1: mag < 2^54
+  const uint64_t mag = (d >= 0) ? (mant << d) : ((-d < 64) ? ((mant + (1ull << (-d - 1))) >> (-d)) : 0ull);
+  return (b >> 63) ? kDigitBias - mag : kDigitBias + mag;
+}
+// The same for a double-float value (hi, lo) in an 8-byte slot (hi in the low word): each part in
+// fixed point against emax (the exponent bound of bexp_pair), summed.
+__device__ __forceinline__ long long fixed54_f32(uint32_t b, int emax) {
+  const int E = (int)((b >> 23) & 0xFF);
+  if (E == 0) return 0;
+  const uint64_t m = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);  // |f| = m 2^(E - 150)
+  const int sh = E - emax + 926;                               // 2^(1076 - emax) scaling: <= 30
+  const uint64_t mag = (sh >= 0) ? (m << sh) : ((-sh < 64) ? ((m + (1ull << (-sh - 1))) >> (-sh)) : 0ull);
+  return (b & 0x80000000u) ? -(long long)mag : (long long)mag;
+}
+__device__ __forceinline__ uint64_t to_biased54_pair(double raw, int emax) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(raw);
+  return kDigitBias + (uint64_t)(fixed54_f32((uint32_t)u, emax) + fixed54_f32((uint32_t)(u >> 32), emax));
+}
+// bf16 bits of digit s (1-based) of two biased fixed-point values, packed low | high.
+__device__ __forceinline__ uint32_t digit_pair(uint64_t m0, uint64_t m1, int s) {
+  const int byte = 7 - s;
+  const uint32_t w0 = (byte >= 4) ? (uint32_t)(m0 >> 32) : (uint32_t)m0;
+  const uint32_t w1 = (byte >= 4) ? (uint32_t)(m1 >> 32) : (uint32_t)m1;
+  const uint32_t sel = 0x7540u | (uint32_t)(byte & 3);  // [the byte, 0, 0, 0x4B]: 2^23 + byte
+  const float f0 = __fsub_rn(__uint_as_float(__byte_perm(w0, 0x4B000000u, sel)), 8388736.f);
+  const float f1 = __fsub_rn(__uint_as_float(__byte_perm(w1, 0x4B000000u, sel)), 8388736.f);
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+// The 8 weight groups G_2..G_9 (exact integers in FP32) of 8 accumulator columns of this warp's
+// 32 TMEM lanes (group g at column offset (g - 2) stride), four groups' loads in flight per wait,
+// recombined per column into X = sum_{g <= 7} G_g 2^(8 (7 - g)) + floor((G_8 2^8 + G_9) / 2^16)
+// (|X| < 2^62; the product is X 2^(eA + eB - 2096)).  Pairs of groups meet in int32 first
+// (|G_g 2^8 + G_{g+1}| < 2^31).
+__device__ __forceinline__ void load_digit_groups8(uint32_t taddr, uint32_t stride, long long X[8]) {
+  int p[4][8];
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint32_t v[4][8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(v[u][0]), "=r"(v[u][1]), "=r"(v[u][2]), "=r"(v[u][3]), "=r"(v[u][4]), "=r"(v[u][5]),
+                     "=r"(v[u][6]), "=r"(v[u][7])
+                   : "r"(taddr + (uint32_t)(4 * half + u) * stride));
+    tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      p[2 * half][c] = __float2int_rn(__uint_as_float(v[0][c])) * 256 + __float2int_rn(__uint_as_float(v[1][c]));
+      p[2 * half + 1][c] = __float2int_rn(__uint_as_float(v[2][c])) * 256 + __float2int_rn(__uint_as_float(v[3][c]));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    X[c] = ((long long)p[0][c] << 32) + ((long long)p[1][c] << 16) + (long long)p[2][c] + (long long)(p[3][c] >> 16);
+}
+
 // Bounded wait on an mbarrier phase (thread-level); false on timeout.
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
   return mbar_wait_bounded(bar, parity, kWaitCycles);

@@ -242,5 +242,11 @@ __device__ __forceinline__ uint64_t slot_fixed(double raw, int emax) {
   if constexpr (kPairs) return oz::to_fixed_pair(raw, emax);
   else return oz::to_fixed(raw, emax);
 }
+// The biased 54-bit fixed point of a slot, for the digit form of the split (ozaki.cuh).
+template <bool kPairs>
+__device__ __forceinline__ uint64_t slot_biased54(double raw, int emax) {
+  if constexpr (kPairs) return oz::to_biased54_pair(raw, emax);
+  else return oz::to_biased54(raw, emax);
+}
 
 }  // namespace tsqr
