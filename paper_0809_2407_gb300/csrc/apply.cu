@@ -404,10 +404,12 @@ cudaError_t launch_form_q_batched(const BatchItem* items, const BatchWork* chain
 }
 
 // ------------------------------------------------------------------------------------------
-// Thin Q with the compact-WY products on the tensor cores (precision mode 2).
+// Thin Q with the compact-WY products on the tensor cores (precision modes 2 and 3): the whole
+// chain in one block, as the batched thin Q runs it, and, for a single factorization, the chains'
+// first leaves after formq_ozaki_phases.cu has taken the rest.
 //
-// Per chain leaf: M = T C and Q_rows = -Y M, each an Ozaki-split FP64 product (ozaki.cuh) of
-// 8 x 8 bf16 slice pairs on tcgen05 with exact FP32 accumulators in TMEM; C -= M in FP64.
+// Per chain leaf: M = T C and Q_rows = -Y M, each an Ozaki-split FP64 product (ozaki.cuh, digit
+// form) on tcgen05 with exact FP32 accumulators in TMEM; C -= M in FP64.
 // The leaf's T arrives by a bulk copy and its reflector tile by TMA, both issued when the leaf
 // starts so that they overlap the T C product.  The first leaf of a chain (V unit lower
 // trapezoidal) takes three passes: X = V_top^T C, M = T X, Q_rows = [C; 0] - V M.  Needs
@@ -490,7 +492,7 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
       for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], slot_bexp<kPairs>(z.M[idx]));
       __syncthreads();
       for (int idx = tid; idx < np * np; idx += kOzT)
-        Tfix[idx] = (long long)slot_fixed<kPairs>(z.M[idx], z.expA[idx >> 6]);
+        Tfix[idx] = (long long)slot_biased54<kPairs>(z.M[idx], z.expA[idx >> 6]);
       __syncthreads();
       if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Tfix[r * 64 + k]; }, ph, st.status)) {
         alive = false;
@@ -521,7 +523,7 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
       __syncthreads();
       for (int idx = tid; idx < h * np; idx += kOzT) {
         double* p = z.Y.ptr(idx >> 6, idx & 63);
-        *reinterpret_cast<uint64_t*>(p) = slot_fixed<kPairs>(*p, z.expA[idx >> 6]);
+        *reinterpret_cast<uint64_t*>(p) = slot_biased54<kPairs>(*p, z.expA[idx >> 6]);
       }
       __syncthreads();
       if (!ozaki_mma_pass(z, tmem, h, [&](int r, int k) { return *reinterpret_cast<const uint64_t*>(z.Y.ptr(r, k)); },
@@ -563,7 +565,7 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
       __syncthreads();
       for (int idx = tid; idx < np * np; idx += kOzT) {
         const int a = idx >> 6, r = idx & 63;
-        Afix[idx] = (long long)oz::to_fixed(r < n ? vval(r, a) : 0.0, z.expA[a]);
+        Afix[idx] = (long long)oz::to_biased54(r < n ? vval(r, a) : 0.0, z.expA[a]);
       }
       __syncthreads();
       if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Afix[r * 64 + k]; }, ph, st.status)) {
@@ -578,7 +580,7 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
       __syncthreads();
       for (int idx = tid; idx < np * np; idx += kOzT) warp_max_into(&z.expA[idx >> 6], oz::bexp(z.M[idx]));
       __syncthreads();
-      for (int idx = tid; idx < np * np; idx += kOzT) Afix[idx] = (long long)oz::to_fixed(z.M[idx], z.expA[idx >> 6]);
+      for (int idx = tid; idx < np * np; idx += kOzT) Afix[idx] = (long long)oz::to_biased54(z.M[idx], z.expA[idx >> 6]);
       __syncthreads();
       if (!ozaki_mma_pass(z, tmem, np, [&](int r, int k) { return (uint64_t)Afix[r * 64 + k]; }, ph, st.status)) {
         alive = false;
@@ -595,7 +597,7 @@ __device__ __forceinline__ void formq_ozaki_chain(const CUtensorMap* mapV_p, con
       for (int idx = tid; idx < h * np; idx += kOzT) {
         const int r = idx >> 6, a = idx & 63;
         const double v = vval(r, a);  // reads only element (r, a), which it then replaces
-        *reinterpret_cast<uint64_t*>(z.Y.ptr(r, a)) = oz::to_fixed(v, z.expA[r]);
+        *reinterpret_cast<uint64_t*>(z.Y.ptr(r, a)) = oz::to_biased54(v, z.expA[r]);
       }
       __syncthreads();
       if (!ozaki_mma_pass(z, tmem, h, [&](int r, int k) { return *reinterpret_cast<const uint64_t*>(z.Y.ptr(r, k)); },

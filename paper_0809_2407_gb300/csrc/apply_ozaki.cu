@@ -6,10 +6,10 @@
 //   W = C + Y^T B_leaf      (first leaf: W = V^T B_leaf)
 //   M = T^T W  (Q^T)  or  M = T W  (Q)
 //   C -= M,  B_leaf -= Y M  (first leaf: B_leaf -= V M)
-// Each product is an Ozaki-split FP64 product (ozaki.cuh) of 8 x 8 bf16 slices on tcgen05 with
-// exact FP32 group sums in TMEM.  W's inner dimension is the leaf height h (up to 128): it is
-// taken in parts of at most 64 rows, each against its own exponents and epilogued into an FP64
-// partial sum, so every group sum stays below 2^23 as in the thin-Q kernel.  M is computed as
+// Each product is an Ozaki-split FP64 product (ozaki.cuh, digit form: 7 balanced base-256 digits,
+// 34 digit pairs on tcgen05) with exact FP32 group sums in TMEM.  W's inner dimension is the leaf
+// height h (up to 128): it is taken in parts of at most 64 rows, each against its own exponents
+// and epilogued into an FP64 partial sum, so every group sum stays below 2^23 as in the thin Q.  M is computed as
 // its transpose, with W^T (kept transposed from the epilogue on) as the A operand, so that T's
 // slices come from one bulk copy.  B is read
 // and written in the caller's layout; the reflector tile arrives by TMA and is loaded twice per
@@ -108,25 +108,23 @@ __global__ void __launch_bounds__(kOzT, 1)
       // B operand: output column b, k-th entry B_leaf[r0 + k][b] (coalesced along b)
       for (int idx = tid; idx < 64 * 32; idx += kOzT) {
         const int b = idx & 63, k = (idx >> 6) * 2;
-        const uint64_t f0 = (r0 + k < r1) ? oz::to_fixed(bget(r0 + k, b), z.expB[b]) : 0ull;
-        const uint64_t f1 = (r0 + k + 1 < r1) ? oz::to_fixed(bget(r0 + k + 1, b), z.expB[b]) : 0ull;
-#pragma unroll
-        for (int s = 1; s <= oz::kSlices; ++s)
-          *reinterpret_cast<uint32_t*>(z.bsl + (s - 1) * oz::kBSliceBytes + oz::op_off(b, k)) = slice_pair(f0, f1, s);
+        const uint64_t f0 = (r0 + k < r1) ? oz::to_biased54(bget(r0 + k, b), z.expB[b]) : oz::kDigitBias;
+        const uint64_t f1 = (r0 + k + 1 < r1) ? oz::to_biased54(bget(r0 + k + 1, b), z.expB[b]) : oz::kDigitBias;
+        put_b_digits(z, oz::op_off(b, k), f0, f1);
       }
       // A operand V^T: this part of the tile in fixed point against the column maxima, in place
       // (the tile is loaded again for the update)
       for (int idx = tid; idx < (r1 - r0) * 64; idx += kOzT) {
         const int r = r0 + (idx >> 6), a = idx & 63;
         const double v = vget(r, a);  // reads only element (r, a), which it then replaces
-        *reinterpret_cast<uint64_t*>(z.Y.ptr(r, a)) = oz::to_fixed(v, z.expA[a]);
+        *reinterpret_cast<uint64_t*>(z.Y.ptr(r, a)) = oz::to_biased54(v, z.expA[a]);
       }
       fence_proxy_async_smem();
       __syncthreads();
       if (!ozaki_mma_pass<true>(  // lanes on a: the tile's row r0 + k is contiguous along a
               z, tmem, 64,
               [&](int a, int k) {
-                return (r0 + k < r1) ? *reinterpret_cast<const uint64_t*>(z.Y.ptr(r0 + k, a)) : 0ull;
+                return (r0 + k < r1) ? *reinterpret_cast<const uint64_t*>(z.Y.ptr(r0 + k, a)) : oz::kDigitBias;
               },
               ph, st.status)) {
         alive = false;
@@ -155,7 +153,7 @@ __global__ void __launch_bounds__(kOzT, 1)
     __syncthreads();
     for (int idx = tid; idx < np * np; idx += kOzT) {
       double* p = X + (idx >> 6) * kOzLd + (idx & 63);
-      *reinterpret_cast<uint64_t*>(p) = oz::to_fixed(*p, z.expA[idx >> 6]);
+      *reinterpret_cast<uint64_t*>(p) = oz::to_biased54(*p, z.expA[idx >> 6]);
     }
     {
       const bool ok = oz_wait_all(z, z.bars + 3, t_phase, st.status);
@@ -199,7 +197,7 @@ __global__ void __launch_bounds__(kOzT, 1)
     for (int idx = tid; idx < h * np; idx += kOzT) {
       const int r = idx >> 6, a = idx & 63;
       const double v = vget(r, a);
-      *reinterpret_cast<uint64_t*>(z.Y.ptr(r, a)) = oz::to_fixed(v, z.expA[r]);
+      *reinterpret_cast<uint64_t*>(z.Y.ptr(r, a)) = oz::to_biased54(v, z.expA[r]);
     }
     fence_proxy_async_smem();
     __syncthreads();

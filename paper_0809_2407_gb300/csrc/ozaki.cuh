@@ -1,21 +1,27 @@
 // FP64 products on the tensor cores by error-free splitting (the scheme of Ozaki, Ogita, Oishi
-// and Rump), for the compact-WY products of TSQR's thin-Q formation.
+// and Rump), for the compact-WY products of TSQR.
 //
 // Each FP64 operand row (A) or column (B) is written in fixed point against its largest
-// exponent: v = sign * mag * 2^(E_max - 1078) with mag < 2^56.  mag is cut into 8 slices of
-// 7 bits, c_1 (most significant) .. c_8, each an integer in [0, 127] held exactly in bf16 with
-// the sign of v.  Slice products c_s^A c_t^B are below 2^14; summed over K = 64 they stay below
-// 2^20, and the pairs of equal weight s + t = g (at most 8 of them) below 2^23, so one FP32
-// tensor-core accumulator per weight group g = 2..9 holds its sum exactly.  The epilogue
-// recombines the eight exact group sums in 64-bit integers,
-//   X = sum_{g<=8} G_g 2^(7(8-g)) + floor(G_9 / 2^7)   (|X| < 2^63),
-// and the FP64 product is X * 2^(E_A + E_B - 2100).  Pairs with s + t > 9 are left out: the
-// result is accurate to about 2^-50 relative to |A| |B| (row and column maxima), close to the
-// rounding of a native FP64 dot product of length 64.
+// exponent and cut into pieces that bf16 holds exactly; the piece products of one weight sum
+// exactly in one FP32 tensor-core accumulator (a "group"), and an int64 epilogue recombines the
+// groups.  Two forms are used:
+//   - the digit form (the thin Q, Q^T B and Q B): 7 balanced base-256 digits of a 54-bit fixed
+//     point rounded to nearest, 34 digit pairs in 8 groups; about 2^-51 relative to |A| |B|
+//     (row and column maxima).  Its helpers are under "balanced base-256 digits" below.
+//   - the 7-bit form (the factorization's Gram entries and its blocked step): v = sign * mag *
+//     2^(E_max - 1078) with mag < 2^56, cut into 8 slices of 7 bits c_1 (most significant) ..
+//     c_8, each in [0, 127] with the sign of v.  Slice products are below 2^14; summed over
+//     K = 64 below 2^20, and the pairs of equal weight s + t = g (at most 8) below 2^23, so one
+//     accumulator per weight group g = 2..9 holds its sum exactly.  The epilogue recombines
+//       X = sum_{g<=8} G_g 2^(7(8-g)) + floor(G_9 / 2^7)   (|X| < 2^63),
+//     and the product is X * 2^(E_A + E_B - 2100); the 36 pairs with s + t <= 9 give about
+//     2^-49 relative to |A| |B| (magnitudes are truncated toward zero).
 //
-// tcgen05 use: one thread issues kind::f16 MMAs (bf16 in, FP32 out, M = 128, N = 64, K = 16)
-// from 128-byte-swizzled K-major shared-memory operands; the eight group accumulators take all
-// 512 TMEM columns of the SM, so the kernel runs one block per SM.  Completion is signalled by
+// tcgen05 use: one thread issues kind::f16 MMAs (bf16 in, FP32 out, M = 128, K = 16) from
+// 128-byte-swizzled K-major shared-memory operands; the eight group accumulators of a 64-column
+// product take all 512 TMEM columns of the SM, so those kernels run one block per SM.  The B
+// pieces that one A piece meets lie one after another in shared memory, as do their groups in
+// TMEM, so one MMA of N up to 256 takes several of them.  Completion is signalled by
 // tcgen05.commit on an mbarrier; every wait on it is bounded.
 #pragma once
 
@@ -193,33 +199,6 @@ __device__ __forceinline__ void load_groups(uint32_t taddr, uint32_t stride, lon
     for (int c = 0; c < kCols; ++c) {
       const long long G = (long long)__float2int_rn(__uint_as_float(v[c]));
       acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
-    }
-  }
-}
-
-// load_groups with the loads of four groups in flight before each wait (32 registers for the
-// loaded values instead of 8): for epilogues whose loads would otherwise wait one by one.
-__device__ __forceinline__ void load_groups8_x4(uint32_t taddr, uint32_t stride, long long acc[8]) {
-#pragma unroll
-  for (int c = 0; c < 8; ++c) acc[c] = 0;
-#pragma unroll
-  for (int g0 = 2; g0 <= oz::kSlices + 1; g0 += 4) {
-    uint32_t v[4][8];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(v[u][0]), "=r"(v[u][1]), "=r"(v[u][2]), "=r"(v[u][3]), "=r"(v[u][4]), "=r"(v[u][5]),
-                     "=r"(v[u][6]), "=r"(v[u][7])
-                   : "r"(taddr + (uint32_t)(g0 + u - 2) * stride));
-    oz::tmem_wait_ld();
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int g = g0 + u;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const long long G = (long long)__float2int_rn(__uint_as_float(v[u][c]));
-        acc[c] += (g <= oz::kSlices) ? G * (1ll << (7 * (oz::kSlices - g))) : (G >> 7);
-      }
     }
   }
 }

@@ -1,7 +1,8 @@
 // Shared pieces of the kernels that run compact-WY products on the tensor cores as Ozaki splits
-// (ozaki.cuh): the shared-memory layout of a 512-thread block, the slicing of operands into bf16
-// slices, one 8 x 8 slice product into the eight TMEM group accumulators, and the int64 epilogue.
+// (ozaki.cuh): the shared-memory layout of a 512-thread block, the digit slices of the operands,
+// one product of 34 digit pairs into the eight TMEM group accumulators, and the int64 epilogue.
 // Used by the thin-Q kernel (apply.cu) and by the Q^T B / Q B chain kernel (apply_ozaki.cu).
+// slice_pair (the 7-bit form) serves the factorization's Gram entries and blocked step.
 #pragma once
 
 #include "arith.cuh"
@@ -70,17 +71,16 @@ __device__ inline bool oz_wait_all(const OzSmem& z, uint64_t* bar, uint32_t pari
   return *z.flag == 0;
 }
 
-// One Ozaki product D (128 x 64) = A (a_rows x 64) B (64 x 64) into the 8 TMEM groups.  The B
-// slices must be in z.bsl and rows a_rows..127 of both A buffers zero; afix(r, k) gives the
-// fixed-point A entries.  With accumulate, the groups keep their sums (a product over a longer
-// K in 64-deep parts, every part against the same exponents).  kLanesOnRows puts the lanes of a
-// warp on consecutive rows r (for an afix source laid out with r contiguous); otherwise on
-// consecutive k.  All threads call.  False on timeout.
+// One Ozaki product D (128 x 64) = A (a_rows x 64) B (64 x 64) in the digit form of the split
+// (ozaki.cuh) into the 8 TMEM groups.  The B digit slices (and the eighth, zero) must be in z.bsl
+// and rows a_rows..127 of both A buffers zero; afix(r, k) gives the biased fixed-point A entries
+// (to_biased54).  kLanesOnRows puts the lanes of a warp on consecutive rows r (for an afix source
+// laid out with r contiguous); otherwise on consecutive k.  All threads call.  False on timeout.
 template <bool kLanesOnRows = false, class AFix>
 __device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows, AFix afix, uint32_t ph[2],
-                                      int* status, bool accumulate = false) {
+                                      int* status) {
   const int tid = threadIdx.x;
-  for (int s = 1; s <= oz::kSlices; ++s) {
+  for (int s = 1; s <= oz::kDigits; ++s) {
     const int b = (s - 1) & 1;
     if (s >= 3) {
       const bool ok = oz_wait_all(z, z.bars + 1 + b, ph[b], status);
@@ -91,23 +91,23 @@ __device__ inline bool ozaki_mma_pass(const OzSmem& z, uint32_t tmem, int a_rows
     for (int idx = tid; idx < a_rows * 32; idx += kOzT) {  // two k per thread: one 32-bit store
       const int r = kLanesOnRows ? idx % a_rows : idx >> 5;
       const int k = kLanesOnRows ? (idx / a_rows) * 2 : (idx & 31) * 2;
-      *reinterpret_cast<uint32_t*>(abuf + oz::op_off(r, k)) = slice_pair(afix(r, k), afix(r, k + 1), s);
+      *reinterpret_cast<uint32_t*>(abuf + oz::op_off(r, k)) = oz::digit_pair(afix(r, k), afix(r, k + 1), s);
     }
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       oz::fence_after_sync();
-      // the B slices t = 1 .. 9 - s lie one after another, as do their groups s + t - 2 in TMEM:
-      // one MMA takes up to four of them (N up to 256)
+      // the B slices t = 1 .. digit_t_max(s) lie one after another, as do their groups s + t - 2
+      // in TMEM: one MMA takes up to four of them (N up to 256)
       const uint64_t adesc = oz::sw128_desc(smem_u32(abuf));
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)  // K step of 16 bf16 = 32 bytes = 2 descriptor units
-        for (int t0 = 1; t0 <= oz::kSlices + 1 - s; t0 += 4) {
-          const int nt = min(4, oz::kSlices + 2 - s - t0);
+        for (int t0 = 1; t0 <= oz::digit_t_max(s); t0 += 4) {
+          const int nt = min(4, oz::digit_t_max(s) + 1 - t0);
           const uint32_t d = tmem + (uint32_t)(s + t0 - 2) * 64u;
           const uint64_t bdesc = oz::sw128_desc(smem_u32(z.bsl + (t0 - 1) * oz::kBSliceBytes));
           oz::mma_bf16(d, adesc + 2 * kk, bdesc + 2 * kk, oz::idesc_bf16(oz::kM, 64u * nt),
-                       (accumulate || s > 1 || kk > 0) ? 1u : 0u);
+                       (s > 1 || kk > 0) ? 1u : 0u);
         }
       oz::mma_commit(z.bars + 1 + b);
     }
@@ -129,18 +129,22 @@ __device__ inline void ozaki_zero_a_rows(const OzSmem& z, int r0, int r1) {
   }
 }
 
-// B slices of the 64 x 64 matrix whose output column j and k-th entry is bval(j, k), against the
-// column exponents in z.expB.  All threads call; ends with a barrier.
+// The 7 digit slices of a B operand entry pair and the eighth, zero slice.
+__device__ __forceinline__ void put_b_digits(const OzSmem& z, uint32_t off, uint64_t m0, uint64_t m1) {
+#pragma unroll
+  for (int s = 1; s <= oz::kDigits; ++s)
+    *reinterpret_cast<uint32_t*>(z.bsl + (s - 1) * oz::kBSliceBytes + off) = oz::digit_pair(m0, m1, s);
+  *reinterpret_cast<uint32_t*>(z.bsl + (oz::kDigitBSlices - 1) * oz::kBSliceBytes + off) = 0u;
+}
+
+// B digit slices of the 64 x 64 matrix whose output column j and k-th entry is bval(j, k),
+// against the column exponents in z.expB.  All threads call; ends with a barrier.
 template <class BVal>
 __device__ inline void ozaki_b_fill(const OzSmem& z, BVal bval) {
   const int tid = threadIdx.x;
   for (int idx = tid; idx < 64 * 32; idx += kOzT) {
     const int j = idx >> 5, k = (idx & 31) * 2;
-    const uint64_t f0 = oz::to_fixed(bval(j, k), z.expB[j]);
-    const uint64_t f1 = oz::to_fixed(bval(j, k + 1), z.expB[j]);
-#pragma unroll
-    for (int s = 1; s <= oz::kSlices; ++s)
-      *reinterpret_cast<uint32_t*>(z.bsl + (s - 1) * oz::kBSliceBytes + oz::op_off(j, k)) = slice_pair(f0, f1, s);
+    put_b_digits(z, oz::op_off(j, k), oz::to_biased54(bval(j, k), z.expB[j]), oz::to_biased54(bval(j, k + 1), z.expB[j]));
   }
   fence_proxy_async_smem();
   __syncthreads();
@@ -173,11 +177,7 @@ __device__ inline void ozaki_b_slices_jmajor(const OzSmem& z, BVal bval) {
   __syncthreads();
   for (int idx = tid; idx < 64 * 32; idx += kOzT) {
     const int j = idx & 63, k = (idx >> 6) * 2;
-    const uint64_t f0 = oz::to_fixed(bval(j, k), z.expB[j]);
-    const uint64_t f1 = oz::to_fixed(bval(j, k + 1), z.expB[j]);
-#pragma unroll
-    for (int s = 1; s <= oz::kSlices; ++s)
-      *reinterpret_cast<uint32_t*>(z.bsl + (s - 1) * oz::kBSliceBytes + oz::op_off(j, k)) = slice_pair(f0, f1, s);
+    put_b_digits(z, oz::op_off(j, k), oz::to_biased54(bval(j, k), z.expB[j]), oz::to_biased54(bval(j, k + 1), z.expB[j]));
   }
   fence_proxy_async_smem();
   __syncthreads();
@@ -197,12 +197,12 @@ __device__ inline void ozaki_epilogue(const OzSmem& z, uint32_t tmem, int rows, 
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf) {  // 8 columns at a time, four groups' loads per wait
       long long acc[8];
-      oz::load_groups8_x4(tb + 8u * (uint32_t)hf, 64u, acc);
+      oz::load_digit_groups8(tb + 8u * (uint32_t)hf, 64u, acc);
       if (i < rows) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int j = c0 + 8 * hf + c;
-          out(i, j, oz::scale_int(acc[c], ea + z.expB[j] - 2100));
+          out(i, j, oz::scale_int(acc[c], ea + z.expB[j] - 2096));
         }
       }
     }
@@ -236,11 +236,6 @@ template <bool kPairs>
 __device__ __forceinline__ int slot_bexp(double raw) {
   if constexpr (kPairs) return oz::bexp_pair(raw);
   else return oz::bexp(raw);
-}
-template <bool kPairs>
-__device__ __forceinline__ uint64_t slot_fixed(double raw, int emax) {
-  if constexpr (kPairs) return oz::to_fixed_pair(raw, emax);
-  else return oz::to_fixed(raw, emax);
 }
 // The biased 54-bit fixed point of a slot, for the digit form of the split (ozaki.cuh).
 template <bool kPairs>
