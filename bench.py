@@ -75,9 +75,10 @@ FACTOR_F64_TRAFFIC = {(4194304, 64): 8 * 700.40e6}
 # the fallback when the live probe below cannot run.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-# Thin-Q tensor-core products per useful FP64 multiply-add: the Ozaki split runs 36 bf16 slice
-# products, bf16x3 six term products (on the chains' Y M; the FP32 form's T C stays on the FP32 pipe).
-OZAKI_PRODUCTS, BF16X3_PRODUCTS = 36, 6
+# Thin-Q tensor-core products per useful FP64 multiply-add: the Ozaki split runs 34 bf16 digit
+# products (7 balanced base-256 digits, pairs of weight <= 9), bf16x3 six term products (on the
+# chains' Y M; the FP32 form's T C stays on the FP32 pipe).
+OZAKI_PRODUCTS, BF16X3_PRODUCTS = 34, 6
 
 
 def measure_pipe_peaks():
