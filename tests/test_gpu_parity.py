@@ -140,6 +140,41 @@ def test_blocked_tensor_core_step_ozaki(T, m, n, opts):
     f.close()
 
 
+OZAKI_PHASE_SHAPES = [
+    (96 * 40 + 50, 64, {"chain": 1}),   # every leaf starts a chain: no leaf products kernel work
+    (96 * 40 + 50, 64, {"chain": 41}),  # one chain, no tree: the recurrence starts from the signs
+    (96 * 41 + 20, 64, {"chain": 5}),   # a short last leaf joins the last chain, taken whole
+    (96 * 37 + 70, 33, {"chain": 4}),   # odd n, ragged last leaf of at least n rows
+    (96 * 300 + 1, 64, {}),             # the default plan; a one-row last leaf
+]
+
+
+@pytest.mark.parametrize("m,n,opts", OZAKI_PHASE_SHAPES)
+@pytest.mark.parametrize("precision", [2, 3], ids=["ozaki", "df_ozaki"])
+def test_ozaki_thin_q_phases(T, m, n, opts, precision):
+    """The tensor-core thin Q of modes 2 and 3 runs as the chains' recurrences (M = T C into
+    each later leaf's rows of Q), the chains' first leaves, and the other leaves' products -V M.
+    Q against the oracle elementwise and against the FP64-pipe thin Q of the same factorization's
+    arithmetic (mode 0 for mode 2, mode 1 for mode 3), in row- and column-major layout."""
+    import torch
+
+    A_h = inputs.gaussian(m, n, inputs.seed_for(43, m + n))
+    f, R, Q = run(T, A_h, precision=precision, **opts)
+    check_against_oracle(A_h, R, Q, precision=precision)
+    _, R0, Q0 = run(T, A_h, precision=precision - 2, **opts)
+    assert np.array_equal(R, R0)  # the factorization is the same; only the thin Q's products differ
+    assert np.abs(Q - Q0).max() <= 1e-13
+    # column-major: the same Q, bitwise
+    A_col = torch.from_numpy(np.ascontiguousarray(A_h.T)).cuda().t()
+    fc = T.Factorization(A_col, precision=precision, **opts)
+    Qc = fc.form_q()
+    torch.cuda.synchronize()
+    assert fc.status() == T.TSQR_OK and Qc.stride(0) == 1
+    assert np.array_equal(Qc.cpu().numpy(), Q)
+    fc.close()
+    f.close()
+
+
 def test_short_last_leaf_is_merged(T):
     """A last leaf with fewer than n rows joins the previous chain instead of starting one."""
     A_h = inputs.gaussian(64 * 4 + 5, 32, 77)
