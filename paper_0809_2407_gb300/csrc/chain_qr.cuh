@@ -124,10 +124,32 @@ __device__ bool chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
     if (tid == j) tau_s[j] = tau;
     if (gram_loop && tid == j) T_s[tri_off(j, NP)] = tau;
     if (active) {
-      // ---- A: D_c = sum_r v_r a_rc over the bottom rows, every column c != j
+      // ---- A: D_c = sum_r v_r a_rc over the bottom rows, every column c != j (without the
+      //      loop's Gram entries only c > j).  Native FP64 without the Gram entries packs those
+      //      a = n - 1 - j columns and their G row groups onto the first G a threads, so whole
+      //      warps fall idle as j grows and the FP64 pipe, which charges a warp instruction
+      //      whatever its active lanes, is spared; each partial sum covers the same rows in the
+      //      same order, so the results do not change.  The FP32-pipe arithmetics keep the fixed
+      //      mapping (their loop is bound by latency, and the packing measured slower there).
       uint32_t oj[8];
       block_offsets(rc, j, oj);
-      if (cown < n && cown != j && (gram_loop || cown > j)) {
+      int ca = cown, ga = gown;
+      uint32_t op[8];
+      bool act;
+      if (gram_loop || Ar::kPrecision != 0) {
+        act = cown < n && cown != j && (gram_loop || cown > j);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) op[t] = oc[t];
+      } else {
+        const int a = n - 1 - j;
+        act = tid < G * a;
+        if (act) {
+          ca = j + 1 + tid % a;
+          ga = tid / a;
+        }
+        block_offsets(rc, ca, op);
+      }
+      if (act) {
         // four independent partial sums so consecutive multiply-adds do not wait on each other
         // on the FP32 pipe; FP64 keeps one: its pipe, not the latency, bounds the dots, and the
         // three adds that join four sums are FP64 instructions too
@@ -135,19 +157,19 @@ __device__ bool chain_qr(const Tile& S, int n, typename Ar::E* tau_s, typename A
         E acc[4] = {Ar::zero(), Ar::zero(), Ar::zero(), Ar::zero()};
 #pragma unroll
         for (int bb = 0; bb < NBG; ++bb) {
-          if (kTri && gown + bb * G > (j >> 3)) continue;  // rows past j: exact zeros in v_j
-          const char* pb = bottom + (size_t)(gown + bb * G) * 1024;
+          if (kTri && ga + bb * G > (j >> 3)) continue;  // rows past j: exact zeros in v_j
+          const char* pb = bottom + (size_t)(ga + bb * G) * 1024;
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
             const E x = *reinterpret_cast<const E*>(pb + oj[t]);
-            const E a = *reinterpret_cast<const E*>(pb + oc[t]);
+            const E a = *reinterpret_cast<const E*>(pb + op[t]);
             Ar::fma_acc(acc[t % kAcc], x, a);
           }
         }
         if constexpr (kAcc == 1)
-          w.red[gown * NP + cown] = Ar::fin(acc[0]);
+          w.red[ga * NP + ca] = Ar::fin(acc[0]);
         else
-          w.red[gown * NP + cown] = Ar::add(Ar::add(acc[0], acc[1]), Ar::add(acc[2], acc[3]));
+          w.red[ga * NP + ca] = Ar::add(Ar::add(acc[0], acc[1]), Ar::add(acc[2], acc[3]));
       }
       __syncthreads();
       // ---- B: d_c = S(j,c) + D_c (c > j): pivot-row update and the update weight tau d_c;
