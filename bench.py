@@ -66,10 +66,10 @@ def load_peaks():
 
 
 # DRAM bytes (read + write) of one factor_kernel<ArithF64> launch, from an ncu capture at
-# m = 524288, n = 64 (700.4 MB, taken with the structured binary node step), scaled by rows to
-# m = 4194304: A is read once and V and T are written once, so traffic grows in proportion to m.
-# Only valid for the kernel as captured.
-FACTOR_F64_TRAFFIC = {(4194304, 64): 8 * 700.40e6}
+# m = 524288, n = 64 (699.4 MB: 269.0 MB read, 430.3 MB written; taken after the chain step's
+# packed dot products), scaled by rows to m = 4194304: A is read once and V and T are written
+# once, so traffic grows in proportion to m.  Only valid for the kernel as captured.
+FACTOR_F64_TRAFFIC = {(4194304, 64): 8 * 699.37e6}
 
 # FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s);
 # the fallback when the live probe below cannot run.

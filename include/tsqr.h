@@ -79,11 +79,13 @@ typedef struct {
                             the FP32 pipe.  Magnitudes of A's and B's nonzero entries should lie
                             in about [2^-100, 2^100]; the stored factors (and A, with inplace)
                             then hold (hi, lo) FP32 pairs in each 8-byte slot.
-                        2 = Ozaki WY: native FP64 reflectors, T and tree; the compact-WY
-                            products of the thin Q (T C, Y M) and of Q^T B / Q B with at least 32
-                            columns of B (Y^T B, W^T T, Y M) as Ozaki splits (8 slices of 7 bits
-                            in bf16, exact FP32 group sums) on the tensor cores (n in 33..64,
-                            leaf_h <= 128; other shapes and narrower B run mode 0).
+                        2 = Ozaki WY: native FP64 reflectors, T recurrence and tree; the
+                            compact-WY products of the thin Q (T C, Y M) and of Q^T B / Q B with
+                            at least 32 columns of B (Y^T B, W^T T, Y M) as Ozaki splits (7
+                            balanced base-256 digits in bf16, exact FP32 group sums) on the
+                            tensor cores, and the flat-tree steps' Gram entries feeding T likewise
+                            (n in 33..64, leaf_h <= 128; other shapes and narrower B run mode 0).
+                            R and the reflectors are bitwise mode 0's.
                         3 = double-float factorization, and Q^T B / Q B with fewer than 32
                             columns; the tensor-core products as in mode 2 (other shapes run
                             mode 1).
