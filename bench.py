@@ -945,19 +945,21 @@ def main():
         ozm = run_mode(2, args.steps, min(args.warmup, 3), False)
         o_ms = ozm["ms"] / args.steps
         forms["ozaki_wy"] = {
-            "precision": 2, "dtype": "f64+bf16x8-split", "value": per_step * world / (o_ms / 1e3) / 1e9,
+            "precision": 2, "dtype": "f64+bf16x7-digit-split", "value": per_step * world / (o_ms / 1e3) / 1e9,
             "unit": "GFLOP/s", "ms_per_step": o_ms, "speedup_vs_f64": ms_step / o_ms,
             "kernel_ms": {k: statistics.mean(v) for k, v in ozm["ev"].items()},
             "backward_error": ozm["be"], "orthogonality": ozm["orth"],
-            "note": "native FP64 factor; thin-Q products T*C and Y*M on tcgen05 tensor cores as Ozaki splits"}
+            "note": "native FP64 reflectors, T merges and tree; the factor's Gram entries and the thin-Q products "
+                    "T*C and Y*M on tcgen05 tensor cores as Ozaki splits (7 balanced base-256 digits)"}
         dzm = run_mode(3, args.steps, min(args.warmup, 3), False)
         dz_ms = dzm["ms"] / args.steps
         forms["df_ozaki_wy"] = {
-            "precision": 3, "dtype": "f32x2+bf16x8-split", "value": per_step * world / (dz_ms / 1e3) / 1e9,
+            "precision": 3, "dtype": "f32x2+bf16x7-digit-split", "value": per_step * world / (dz_ms / 1e3) / 1e9,
             "unit": "GFLOP/s", "ms_per_step": dz_ms, "speedup_vs_f64": ms_step / dz_ms,
             "kernel_ms": {k: statistics.mean(v) for k, v in dzm["ev"].items()},
             "backward_error": dzm["be"], "orthogonality": dzm["orth"],
-            "note": "double-float factor and Q^T b; thin-Q WY products as Ozaki splits on tcgen05"}
+            "note": "double-float factor and Q^T b; thin-Q WY products as Ozaki splits (7 balanced base-256 "
+                    "digits) on tcgen05"}
         f3 = run_mode(0, args.steps, min(args.warmup, 3), False, f32=True)
         s_ms = f3["ms"] / args.steps
         forms["fp32"] = {
@@ -976,7 +978,7 @@ def main():
                  "reflectors, panel WY products and Gram entries as bf16x3 terms on tcgen05; thin Q as fp32")):
             r = run_mode(prec, args.steps, min(args.warmup, 3), False, f32=f32, leaf_h=64)
             r_ms = r["ms"] / args.steps
-            forms[nm] = {"precision": prec, "leaf_h": 64, "dtype": "f32" if f32 else "f64+bf16x8-split",
+            forms[nm] = {"precision": prec, "leaf_h": 64, "dtype": "f32" if f32 else "f64+bf16x8-slice-split",
                          "value": per_step * world / (r_ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": r_ms,
                          "speedup_vs_f64": ms_step / r_ms,
                          "kernel_ms": {k: statistics.mean(v) for k, v in r["ev"].items()},
