@@ -41,6 +41,11 @@ bool bf16x3_apply_applies(const Plan& P, int64_t k);
 cudaError_t launch_apply_bf16x3_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, int64_t k, float* B,
                                        int64_t ldb, int box_rows, bool trans, cudaStream_t stream);
 bool bf16x3_form_q_applies(const Plan& P);
+// FP32 storage, as the Ozaki thin Q above (formq_f32_phases.cu): the chains' recurrences M = T C
+// on the FP32 pipe (M into each later leaf's rows of Q, the block entering the first leaf into
+// node_r), and the other leaves' products -Y M as bf16x3 terms on the tensor cores.
+cudaError_t launch_formq_f32_recur(const Plan& P, const Store& st, float* Q, int64_t ldq, cudaStream_t stream);
+cudaError_t launch_formq_bf16x3_leaves(const Plan& P, const Store& st, float* Q, int64_t ldq, cudaStream_t stream);
 // chains of an FP32-storage thin Q with bf16x3 tensor-core WY products (after the tree levels)
 cudaError_t launch_formq_bf16x3_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, float* Q, int64_t ldq,
                                        int box_rows, cudaStream_t stream);

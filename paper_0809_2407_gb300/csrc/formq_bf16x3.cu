@@ -26,9 +26,11 @@ namespace {
 using namespace bf3;
 
 // Chain g of one factorization (the body of formq_bf16x3_kernel and of its batched form).
+// first_only: only the chain's first leaf, with the block C entering it read from node_r[g]
+// (written there by formq_f32_recur_kernel after the chain's other leaves), also without a tree.
 __device__ __forceinline__ void formq_bf16x3_chain(const CUtensorMap* mapV_p, const Plan& P, const Store& st,
                                                    float* __restrict__ Q, int64_t ldq, int box_rows, int g,
-                                                   char* smem_raw) {
+                                                   char* smem_raw, bool first_only = false) {
   Tc3Smem z = carve_tc3(smem_raw, P.h);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int np = 64, n = P.n, h = P.h;
@@ -47,14 +49,14 @@ __device__ __forceinline__ void formq_bf16x3_chain(const CUtensorMap* mapV_p, co
   const f32x2* blocks = reinterpret_cast<const f32x2*>(st.node_r);
   for (int i = tid; i < np * np; i += kT3) {
     const int a = i >> 6, b = i & 63;
-    z.C[a * kLd + b] = (P.depth == 0) ? ((a == b && a < n) ? (float)__ldcg(st.signs + a) : 0.f)
-                                      : blocks[(size_t)g * np * np + i].hi;
+    z.C[a * kLd + b] = (P.depth == 0 && !first_only) ? ((a == b && a < n) ? (float)__ldcg(st.signs + a) : 0.f)
+                                                     : blocks[(size_t)g * np * np + i].hi;
   }
   __syncthreads();
   // rows h..127 of the A terms stay zero (the MMA reads 128 rows; only the first leaf, which is
   // processed last, reuses the buffers as scratch)
   if (h < 128) zero_a_rows(z.a, h);
-  const int64_t l0 = chain_first_leaf(P, g), l1 = chain_end_leaf(P, g);
+  const int64_t l0 = chain_first_leaf(P, g), l1 = first_only ? l0 + 1 : chain_end_leaf(P, g);
   bool alive = true;
   for (int64_t leaf = l1 - 1; leaf >= l0 && alive; --leaf) {
     const int64_t row0 = leaf * h;
@@ -167,11 +169,15 @@ __device__ __forceinline__ void formq_bf16x3_chain(const CUtensorMap* mapV_p, co
   if (warp == 0) oz::tmem_dealloc(tmem, kTmemCols3);
 }
 
+// split: the chain's other leaves were taken by the recurrence and leaf-product kernels
+// (formq_f32_phases.cu), so only its first leaf is left here (a chain that holds a short last
+// leaf is taken whole).
 __global__ void __launch_bounds__(kT3, 1)
     formq_bf16x3_kernel(const __grid_constant__ CUtensorMap mapV, const Plan P, const Store st, float* __restrict__ Q,
-                        int64_t ldq, int box_rows) {
+                        int64_t ldq, int box_rows, bool split) {
   extern __shared__ char smem_raw[];
-  formq_bf16x3_chain(&mapV, P, st, Q, ldq, box_rows, blockIdx.x, smem_raw);
+  const int g = blockIdx.x;
+  formq_bf16x3_chain(&mapV, P, st, Q, ldq, box_rows, g, smem_raw, split && !formq_chain_short(P, g));
 }
 
 __global__ void __launch_bounds__(kT3, 1)
@@ -203,11 +209,17 @@ cudaError_t launch_formq_bf16x3_batched(const BatchItem* items, const BatchWork*
 
 cudaError_t launch_formq_bf16x3_chains(const CUtensorMap& mapV, const Plan& P, const Store& st, float* Q, int64_t ldq,
                                        int box_rows, cudaStream_t stream) {
-  const size_t smem = formq_bf16x3_smem_bytes(P);
-  cudaError_t e = cudaFuncSetAttribute(formq_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the chains' recurrences (M = T C of every leaf but the first, into Q; the block entering the
+  // first leaf into node_r), then the first leaves, then the other leaves' products -Y M
+  cudaError_t e = launch_formq_f32_recur(P, st, Q, ldq, stream);
   if (e != cudaSuccess) return e;
-  formq_bf16x3_kernel<<<P.chains, kT3, smem, stream>>>(mapV, P, st, Q, ldq, box_rows);
-  return cudaGetLastError();
+  const size_t smem = formq_bf16x3_smem_bytes(P);
+  e = cudaFuncSetAttribute(formq_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  formq_bf16x3_kernel<<<P.chains, kT3, smem, stream>>>(mapV, P, st, Q, ldq, box_rows, true);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_formq_bf16x3_leaves(P, st, Q, ldq, stream);
 }
 
 }  // namespace tsqr

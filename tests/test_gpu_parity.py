@@ -800,6 +800,27 @@ def check_f32(A32, R, Q, unique=True):
         assert np.abs(Q - ref["Q"]).max() <= bound
 
 
+@pytest.mark.parametrize("m,n,opts", OZAKI_PHASE_SHAPES)
+def test_f32_thin_q_phases(T, m, n, opts):
+    """FP32 storage at padded width 64 forms the thin Q as the chains' recurrences (M = T C on the
+    FP32 pipe, into each later leaf's rows of Q), the chains' first leaves, and the other leaves'
+    products -Y M as bf16x3 tensor-core terms.  Q against the oracle's QR of the float32 input,
+    and the column-major layout bitwise the same."""
+    import torch
+
+    A32 = inputs.gaussian(m, n, inputs.seed_for(44, m + n)).astype(np.float32).astype(np.float64)
+    f, R, Q = run32(T, A32, **opts)
+    check_f32(A32, R, Q)
+    A_col = torch.from_numpy(np.ascontiguousarray(A32.T.astype(np.float32))).cuda().t()
+    fc = T.Factorization(A_col, **opts)
+    Qc = fc.form_q()
+    torch.cuda.synchronize()
+    assert fc.status() == T.TSQR_OK and Qc.stride(0) == 1
+    assert np.array_equal(Qc.cpu().numpy().astype(np.float64), Q)
+    fc.close()
+    f.close()
+
+
 @pytest.mark.parametrize("m,n,opts", [(4096, 16, {"leaf_h": 256, "chain": 1, "arity": 2}),
                                       (3000, 24, {"leaf_h": 128, "chain": 3, "arity": 3}),
                                       (40000 + 13, 64, {}), (30000, 50, {}), (100000 + 3, 16, {}),
