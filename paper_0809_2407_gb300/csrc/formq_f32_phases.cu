@@ -140,18 +140,19 @@ __global__ void __launch_bounds__(kRT, 2)
 // value in its low half; warp w takes rows w + 8 u, two columns per lane), M from the leaf's rows
 // of Q; both are split into bf16 terms in shared memory; the three MMAs per K step (A term s
 // against B terms 0 .. 2 - s) go out in one commit; the next leaf's rows and M load into
-// registers while they run; the epilogue writes -Y M over M.
+// registers while they run; the epilogue writes -Y M over M.  A row-major Q leaves through a
+// shared tile in whole rows (a TMEM lane holds one row, so direct stores would touch a sector per
+// lane); a column-major Q is written straight from the lanes, which are then consecutive.
 constexpr int kLT = 256;
 constexpr int kLWarps = kLT / 32;
 constexpr int kLRows = 128 / kLWarps;  // 16 operand rows per warp (h <= 128)
 constexpr int kLM = 64 * 32 / kLT;     // 8 pairs (k, k + 1) of M entries per thread
 constexpr uint32_t kLTmem = 256;       // 3 regions of 64 columns
+constexpr int kStLd = 68;              // row stride of the output tile (floats; rows 16-byte aligned)
 
-// 72 KB in use; the request is padded to 100 KB so that at most two blocks (512 TMEM columns)
-// share an SM.
+// 107 KB: two blocks (512 TMEM columns) share an SM, a third does not fit.
 size_t bf16x3_leaves_smem_bytes() {
-  const size_t used = 1024 + 3 * (size_t)bf3::kTermA + 3 * (size_t)bf3::kTermB + 8 + 8 + 8;
-  return used > 100 * 1024 ? used : 100 * 1024;
+  return 1024 + 3 * (size_t)bf3::kTermA + 3 * (size_t)bf3::kTermB + 128 * kStLd * 4 + 8 + 8 + 8;
 }
 
 __device__ __forceinline__ int64_t next_deferred_f32(const Plan& P, int64_t leaf) {
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(kLT, 2)
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   char* za = base;                  // 3 A terms, 128 operand rows each
   char* zb = za + 3 * bf3::kTermA;  // 3 B terms, 64 operand rows each
-  uint64_t* bar = reinterpret_cast<uint64_t*>(zb + 3 * bf3::kTermB);
+  float* stage = reinterpret_cast<float*>(zb + 3 * bf3::kTermB);  // -Y M, 128 x kStLd
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stage + 128 * kStLd);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
   int* flag = reinterpret_cast<int*>(slot + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -283,15 +285,41 @@ __global__ void __launch_bounds__(kLT, 2)
         for (int c = 0; c < 32; ++c) acc[c] = __fadd_rn(acc[c], __uint_as_float(v[c]));
         oz::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);  // sum_s A_s B_0
         oz::tmem_wait_ld();
-        if (i < rv) {
+        if (P.col_major) {
+          if (i < rv) {
 #pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (c0 + c < n) Q[gidx(P, row0 + i, c0 + c, ldq)] = -__fadd_rn(acc[c], __uint_as_float(v[c]));
+            for (int c = 0; c < 32; ++c)
+              if (c0 + c < n) Q[gidx(P, row0 + i, c0 + c, ldq)] = -__fadd_rn(acc[c], __uint_as_float(v[c]));
+          }
+        } else {
+          float4* srow = reinterpret_cast<float4*>(stage + i * kStLd + c0);
+#pragma unroll
+          for (int c = 0; c < 32; c += 4)
+            srow[c / 4] = make_float4(-__fadd_rn(acc[c], __uint_as_float(v[c])),
+                                      -__fadd_rn(acc[c + 1], __uint_as_float(v[c + 1])),
+                                      -__fadd_rn(acc[c + 2], __uint_as_float(v[c + 2])),
+                                      -__fadd_rn(acc[c + 3], __uint_as_float(v[c + 3])));
         }
       }
       oz::fence_before_sync();
       __syncthreads();
       oz::fence_after_sync();
+    }
+    // ---- a row-major Q in whole rows; the tile is next written after the next leaf's barrier
+    if (!P.col_major) {
+      float* qrow0 = Q + row0 * ldq;
+      if (n == 64 && (ldq & 3) == 0 && (reinterpret_cast<uintptr_t>(Q) & 15) == 0) {
+        for (int e = tid; e < rv * 16; e += kLT) {
+          const int r = e >> 4, c4 = e & 15;
+          __stcg(reinterpret_cast<float4*>(qrow0 + r * ldq) + c4,
+                 *reinterpret_cast<const float4*>(stage + r * kStLd + 4 * c4));
+        }
+      } else {
+        for (int e = tid; e < rv * 64; e += kLT) {
+          const int r = e >> 6, c = e & 63;
+          if (c < n) __stcg(qrow0 + r * ldq + c, stage[r * kStLd + c]);
+        }
+      }
     }
     leaf = next;
   }
