@@ -862,6 +862,14 @@ def main():
         tsqr.tsqr_destroy(h)
         P, d = info.panels, info.depth
         launches = (P > 1) + P + (P - 1) + P * (d + 1) + (P - 1) * (d + 1) + P
+        if P == 1:
+            # FP32 storage widens A into the staging slots first; the tensor-core thin Q (modes 2
+            # and 3, FP32 storage; padded width 64, leaves of at most 128 rows) runs its chains as
+            # three launches: recurrences, first leaves, leaf products (none when every leaf
+            # starts a chain)
+            launches += int(f32)
+            if (precision in (2, 3) or f32) and info.np == 64 and info.leaf_h <= 128:
+                launches += 2 if info.leaves > info.chains else 1
         torch.cuda.synchronize()
         if dist:
             dist.barrier()

@@ -2,10 +2,11 @@
 //
 // Some callers cannot call cudaMalloc or hand over a workspace: code inside another runtime's
 // allocator or its callbacks (which must not re-enter an allocator), plugins whose host owns all
-// device memory and gives them none, or plain C hosts with no device allocator of their own.  This entry point needs no workspace: the scratch the factorization uses between thread
-// blocks (the chains' and tree nodes' R factors, the arrival counters and a status word) lives
-// in one file-scope __device__ array of kStaticScratchBytes, which every GPU that loads this
-// library holds until the process exits.  It computes only R (diag(R) >= 0); the implicit Q is
+// device memory and gives them none, or plain C hosts with no device allocator of their own.
+// This entry point needs no workspace: the scratch the factorization uses between thread blocks
+// (the chains' and tree nodes' R factors, the arrival counters and a status word) lives in one
+// file-scope __device__ array of kStaticScratchBytes, which every GPU that loads this library
+// holds until the process exits.  It computes only R (diag(R) >= 0); the implicit Q is
 // not kept, so the leaf reflectors and T factors are never written.
 //
 // The array's address is taken once per device with cudaGetSymbolAddress, on the first call
