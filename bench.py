@@ -51,6 +51,23 @@ def max_over_ranks(x, dist, device):
     return t.item()
 
 
+def launches_per_step(panels, depth, precision, f32, np_, leaf_h, leaves, chains):
+    """Kernels of one step (factor, thin Q, Q^T b with one column): the factorization, one thin-Q
+    launch per tree level plus the chain launch, and one Q^T b launch; with P > 1 panels (n > 64)
+    also the staging copy, the trailing updates and the earlier panels' Q applied to the later
+    column blocks.  For one panel: FP32 storage first widens A into the staging slots, and the
+    tensor-core thin Q (modes 2 and 3, FP32 storage; padded width 64, leaves of at most 128 rows)
+    runs its chains as three launches: recurrences, first leaves and leaf products (the last is
+    skipped when every leaf starts a chain).  With P > 1 the count is the FP64 schedule's."""
+    P, d = panels, depth
+    n_launch = (P > 1) + P + (P - 1) + P * (d + 1) + (P - 1) * (d + 1) + P
+    if P == 1:
+        n_launch += int(f32)
+        if (precision in (2, 3) or f32) and np_ == 64 and leaf_h <= 128:
+            n_launch += 2 if leaves > chains else 1
+    return n_launch
+
+
 def job_value(units_per_step_per_rank, world, ms_per_step):
     """Whole-job throughput: every rank processes the same units per step (weak scaling), and the
     job's step time is the slowest rank's."""
@@ -853,23 +870,12 @@ def main():
 
         for _ in range(warmup):
             step(False)
-        # kernels of one step: the factorization, one thin-Q launch per tree level plus the chain
-        # launch, and one Q^T b launch; with P > 1 panels (n > 64) also the staging copy, the
-        # trailing updates and the earlier panels' Q applied to the later column blocks
         h = tsqr.tsqr_factor(code, tsqr.TSQR_ROW_MAJOR, m, n, A_.data_ptr(), n, R_.data_ptr(), n,
                              work.data_ptr(), nbytes, opts, sptr)
         info = tsqr.tsqr_handle_info(h)
         tsqr.tsqr_destroy(h)
-        P, d = info.panels, info.depth
-        launches = (P > 1) + P + (P - 1) + P * (d + 1) + (P - 1) * (d + 1) + P
-        if P == 1:
-            # FP32 storage widens A into the staging slots first; the tensor-core thin Q (modes 2
-            # and 3, FP32 storage; padded width 64, leaves of at most 128 rows) runs its chains as
-            # three launches: recurrences, first leaves, leaf products (none when every leaf
-            # starts a chain)
-            launches += int(f32)
-            if (precision in (2, 3) or f32) and info.np == 64 and info.leaf_h <= 128:
-                launches += 2 if info.leaves > info.chains else 1
+        launches = launches_per_step(info.panels, info.depth, precision, f32, info.np, info.leaf_h, info.leaves,
+                                     info.chains)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()

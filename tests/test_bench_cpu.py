@@ -71,3 +71,20 @@ def test_usv_family_equals_usv():
     fam = inputs.usv_family(500, 12, ks, 31)
     for k, A in zip(ks, fam):
         assert np.array_equal(A, inputs.usv(500, 12, k, 31))
+
+
+def test_launches_per_step_matches_the_launch_lists():
+    """gpu_launches counts the kernels of a step as the committed ncu launch lists show them at
+    m = 2^22, n = 64 (leaf height 96, 43691 leaves, 304 chains, 9 tree levels): FP64 12 (factor,
+    9 tree levels, thin-Q chains, Q^T b), the Ozaki form 14 (three thin-Q chain kernels), FP32
+    storage 15 (also the widening of A)."""
+    bench = _bench_module()
+    full = dict(np_=64, leaf_h=96, leaves=43691, chains=304)
+    assert bench.launches_per_step(1, 9, 0, False, **full) == 12
+    assert bench.launches_per_step(1, 9, 1, False, **full) == 12
+    assert bench.launches_per_step(1, 9, 2, False, **full) == 14
+    assert bench.launches_per_step(1, 9, 3, False, **full) == 14
+    assert bench.launches_per_step(1, 9, 0, True, **full) == 15
+    # every leaf starts a chain: no leaf-products launch; padded width 32: the one chain kernel
+    assert bench.launches_per_step(1, 4, 2, False, np_=64, leaf_h=96, leaves=16, chains=16) == 8
+    assert bench.launches_per_step(1, 9, 2, False, np_=32, leaf_h=256, leaves=16384, chains=304) == 12
